@@ -1,0 +1,406 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check is a closed-form
+moment, an exact invariant, a textbook solution, a symmetry, or a value the
+paper prints (``tests/golden/paper_values.json``).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_08666_gb300 import media
+
+E = np.array([[0, 1, 0, -1, 0, 1, -1, -1, 1], [0, 0, 1, 0, -1, 1, 1, -1, -1]], dtype=float)
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+def nu_of_tau(tau):
+    return (tau - 0.5) / 3.0
+
+
+# --- Eq. 2 and Eq. 11: moments fixed by construction -------------------------
+
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (0.7, 0.05, -0.03), (0.027, -0.1, 0.08)])
+def test_feq_moments(rho, ux, uy):
+    f = oracle.feq(rho, ux, uy)
+    assert f.sum() == pytest.approx(rho, rel=1e-15, abs=1e-16)
+    assert E @ f == pytest.approx([rho * ux, rho * uy], abs=1e-16)
+    # second moment: rho (cs^2 I + u u)
+    pi = np.einsum("ai,bi,i->ab", E, E, f)
+    want = rho * (np.eye(2) / 3.0 + np.outer([ux, uy], [ux, uy]))
+    assert np.allclose(pi, want, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("ux,uy,fx,fy", [(0.0, 0.0, 1e-3, 0.0), (0.04, -0.02, 2e-4, -5e-4),
+                                         (-0.1, 0.07, -3e-3, 1e-3)])
+def test_source_moments_and_tensor_form(ux, uy, fx, fy):
+    s = oracle.source(ux, uy, fx, fy)
+    assert abs(s.sum()) < 1e-17
+    assert E @ s == pytest.approx([fx, fy], abs=1e-17)
+    # second moment of the forcing term equals u F + F u (Eq. 10 design)
+    pi = np.einsum("ai,bi,i->ab", E, E, s)
+    u, F = np.array([ux, uy]), np.array([fx, fy])
+    assert np.allclose(pi, np.outer(u, F) + np.outer(F, u), atol=1e-17)
+    # Eq. 10 (tensor form) written independently of Eq. 11
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    cs2 = 1 / 3
+    for i in range(9):
+        e = E[:, i]
+        q = np.outer(e, e) - cs2 * np.eye(2)
+        t10 = w[i] * (e @ F / cs2 + np.sum(q * (np.outer(u, F) + np.outer(F, u))) / (2 * cs2 ** 2))
+        assert s[i] == pytest.approx(t10, abs=1e-17)
+
+
+def test_pressure_eos_ordered_pairs():
+    # Eq. 14 at equal densities of 1/2: P = cs^2 * 1 + cs^2/2 * G * 2 * 1/4
+    assert oracle.pressure(3.5, 0.5, 0.5) == pytest.approx(1 / 3 + 3.5 / 12, rel=1e-15)
+    assert oracle.pressure(3.5, 1.0, 0.0) == pytest.approx(1 / 3, rel=1e-15)
+
+
+def test_tau_nu_reading_matches_printed_pairs():
+    for tau, nu in GOLD["tau_nu_pairs"]["value"]:
+        assert nu_of_tau(tau) == pytest.approx(nu, rel=1e-12)
+    t = GOLD["viscosity_ratio_tau"]["value"]["M25"]
+    assert nu_of_tau(t[0]) / nu_of_tau(t[1]) == pytest.approx(25.0, rel=1e-12)
+
+
+# --- invariants of the full update --------------------------------------------
+
+def _periodic(n, m, **kw):
+    solid = np.zeros((m, n), np.uint8)
+    return oracle.Oracle(solid, np.zeros((m, n), np.float32), periodic_y=True, **kw)
+
+
+def test_uniform_rest_state_is_fixed_point():
+    o = _periodic(12, 10, nu1=1 / 6, nu2=0.04)
+    o.init(np.full((10, 12), 0.6), np.full((10, 12), 0.4))
+    f0 = o.f.copy()
+    o.step(20)
+    # fixed point up to the rounding of sum_i w_i rho
+    assert np.max(np.abs(o.f - f0)) < 1e-15
+
+
+def _closed_droplet_box(xi_val, nu1, nu2, n=40, m=32):
+    solid = np.zeros((m, n), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    yy, xx = np.mgrid[0:m, 0:n]
+    solid[((xx - 30) ** 2 + (yy - 16) ** 2) <= 16] = 1     # a grain
+    xi = media.uniform_xi(solid, xi_val)
+    rho1, rho2 = media.droplet_densities(n, m, 12, 9, 6, solid=solid)
+    o = oracle.Oracle(solid, xi, nu1=nu1, nu2=nu2)
+    o.init(rho1, rho2)
+    return o
+
+
+@pytest.mark.parametrize("xi_val,tau1,tau2", [(0.0, 1.0, 1.0), (-0.4, 3.5, 0.62), (0.5, 0.62, 3.5)])
+def test_mass_conserved_in_closed_box(xi_val, tau1, tau2):
+    o = _closed_droplet_box(xi_val, nu_of_tau(tau1), nu_of_tau(tau2))
+    d0 = o.diagnostics()
+    o.step(1500)
+    d1 = o.diagnostics()
+    assert abs(d1["mass1"] / d0["mass1"] - 1) < 1e-12
+    assert abs(d1["mass2"] / d0["mass2"] - 1) < 1e-12
+
+
+def test_total_momentum_gain_equals_body_force():
+    """Interaction forces cancel pairwise in a periodic box, so with the
+    half-force velocity shift the total momentum grows by g * total mass per
+    step exactly (a wrong sign, a dropped forcing term or the unshifted
+    velocity breaks this)."""
+    n = m = 24
+    g = (1e-5, -4e-6)
+    rho1, rho2 = media.droplet_densities(n, m, 12, 12, 6)
+    o = _periodic(n, m, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), gx=g[0], gy=g[1])
+    o.init(rho1, rho2)
+    o.step(30)   # let the interface develop non-trivial forces
+    mom = lambda f: np.einsum("ai,cixy->a", E, f)
+    for _ in range(5):
+        p0 = mom(o.f)
+        mass = o.f.sum()
+        o.step(1)
+        gain = mom(o.f) - p0
+        assert gain == pytest.approx([g[0] * mass, g[1] * mass], rel=1e-9, abs=1e-15)
+    # the unshifted reading gains only (1 - 1/(2 tau)) F and fails the balance
+    o2 = _periodic(n, m, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), gx=g[0], gy=g[1],
+                   vel_shift=False)
+    o2.init(rho1, rho2)
+    o2.step(30)
+    p0, mass = mom(o2.f), o2.f.sum()
+    o2.step(1)
+    assert abs((mom(o2.f) - p0)[0] - g[0] * mass) > 1e-3 * abs(g[0] * mass)
+
+
+def test_component_swap_symmetry_bitwise():
+    """At equal viscosities, swapping the components and xi -> -xi swaps the
+    solution exactly."""
+    n, m = 32, 24
+    solid = np.zeros((m, n), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    solid[8:14, 20:26] = 1
+    xi = media.uniform_xi(solid, 0.35)
+    rho1, rho2 = media.droplet_densities(n, m, 10, 10, 5, solid=solid)
+    a = oracle.Oracle(solid, xi, nu1=0.1, nu2=0.1)
+    b = oracle.Oracle(solid, -xi, nu1=0.1, nu2=0.1)
+    a.init(rho1, rho2)
+    b.init(rho2, rho1)
+    a.step(200)
+    b.step(200)
+    assert np.array_equal(a.f[0], b.f[1]) and np.array_equal(a.f[1], b.f[0])
+
+
+def test_y_mirror_symmetry():
+    n, m = 30, 26
+    solid = np.zeros((m, n), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    solid[9:17, 14:20] = 1          # symmetric about y = 12.5
+    xi = media.uniform_xi(solid, -0.3)
+    rho1, rho2 = media.drainage_densities(solid)
+    o = oracle.Oracle(solid, xi, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01,
+                      rho_out2=1.0)
+    o.init(rho1, rho2)
+    o.step(300)
+    mirror = [0, 1, 4, 3, 2, 8, 7, 6, 5]          # e_y -> -e_y
+    fm = o.f[:, mirror, ::-1, :]
+    assert np.max(np.abs(fm - o.f)) < 1e-13
+
+
+# --- boundary treatments (Sec. 2.3) ---------------------------------------------
+
+def _open_channel(n=20, m=16, seed=3):
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((m, n), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    solid[6:9, 8:11] = 1
+    xi = media.uniform_xi(solid, -0.4)
+    rho1 = (0.027 + 0.9 * rng.random((m, n))) * (solid == 0)
+    rho2 = (0.027 + 0.9 * rng.random((m, n))) * (solid == 0)
+    o = oracle.Oracle(solid, xi, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), rho_in1=1.02,
+                      rho_out2=0.98)
+    o.init(rho1, rho2)
+    o.step(3)
+    return o
+
+
+def test_zou_he_prescribes_density_and_zero_tangential_velocity():
+    o = _open_channel()
+    fpost = o.f.copy()
+    fs = o.stream_bc()
+    fluid_in = np.nonzero(o.solid[:, 0] == 0)[0]
+    fluid_out = np.nonzero(o.solid[:, -1] == 0)[0]
+    assert np.allclose(fs[0, :, fluid_in, 0].sum(axis=1), 1.02, rtol=0, atol=1e-15)
+    assert np.allclose(fs[1, :, fluid_out, -1].sum(axis=1), 0.98, rtol=0, atol=1e-15)
+    ey = E[1]
+    assert np.allclose(fs[0, :, fluid_in, 0] @ ey, 0.0, atol=1e-16)
+    assert np.allclose(fs[1, :, fluid_out, -1] @ ey, 0.0, atol=1e-16)
+    # Eq. 28: component 2 at the inlet keeps its own post-collision f_{1,5,8}
+    for i in (1, 5, 8):
+        assert np.array_equal(fs[1, i, fluid_in, 0], fpost[1, i, fluid_in, 0])
+    # Eq. 26: component 1 at the outlet takes its initial f_{3,6,7}
+    for k, i in enumerate((3, 6, 7)):
+        assert np.array_equal(fs[0, i, fluid_out, -1], o.d5[k, fluid_out])
+    # the interior is pure streaming: f_1 at (x, y) came from (x-1, y)
+    y = fluid_in[len(fluid_in) // 2]
+    assert fs[0, 1, y, 5] == fpost[0, 1, y, 4]
+
+
+def test_bounce_back_reflects_own_population():
+    o = _open_channel()
+    fpost = o.f.copy()
+    fs = o.stream_bc()
+    # node (5, 2) sits on the bottom wall: direction 2 (from below) bounces back
+    assert fs[0, 2, 2, 5] == fpost[0, 4, 2, 5]
+    assert fs[1, 5, 2, 5] == fpost[1, 7, 2, 5]
+    assert fs[1, 6, 2, 5] == fpost[1, 8, 2, 5]
+
+
+def test_boundary_mirror_gives_no_x_interaction_force():
+    o = _open_channel()
+    rho, _, _ = o.moments(o.stream_bc())
+    psi = o.ivsd(rho)
+    fx, fy = o.forces(rho, psi)
+    scale = np.abs(fx).max()
+    for x in (0, -1):
+        fluid = o.solid[:, x] == 0
+        assert np.max(np.abs(fx[:, fluid, x])) < 1e-15 * max(scale, 1.0) + 1e-17
+        assert np.max(np.abs(fy[:, fluid, x])) > 0       # y force is untouched
+
+
+def test_ivsd_uniform_neighbourhood():
+    o = _open_channel()
+    rho0 = 0.73
+    rho = np.stack([np.full((o.ny, o.nx), rho0)] * 2) * (o.solid == 0)
+    psi = o.ivsd(rho)
+    adj = np.zeros_like(o.solid, dtype=bool)
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            adj |= np.roll(np.roll(o.solid == 0, dy, 0), dx, 1)
+    sel = (o.solid == 1) & adj
+    sel[:, 0] = sel[:, -1] = False     # rolled wrap is not a neighbour there
+    assert np.allclose(psi[0][sel], (1 - 0.4) * rho0, rtol=1e-14)
+    assert np.allclose(psi[1][sel], (1 + 0.4) * rho0, rtol=1e-14)
+
+
+# --- textbook flows --------------------------------------------------------------
+
+def test_single_phase_poiseuille_exact_at_magic_tau():
+    """Component 2 absent: a body-force driven channel between half-way
+    bounce-back walls reproduces the parabola exactly at (tau-1/2)^2 = 3/16."""
+    n, m = 4, 18
+    solid = np.zeros((m, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    nu, g = nu_of_tau(tau), 1e-6
+    o = oracle.Oracle(solid, np.zeros((m, n), np.float32), nu1=nu, nu2=0.1, gx=g)
+    o.init(np.ones((m, n)) * (solid == 0), np.zeros((m, n)))
+    o.step(8000)
+    y = np.arange(m, dtype=float)
+    lo, hi = 0.5, m - 1.5
+    u_exact = g / (2 * nu) * (y - lo) * (hi - y)
+    ux = o.ux[1:-1, 2]
+    assert np.max(np.abs(ux - u_exact[1:-1])) < 1e-10 * u_exact.max()
+    assert np.array_equal(o.f[1], np.zeros_like(o.f[1]))
+
+
+@pytest.mark.slow
+def test_two_layer_poiseuille():
+    """Stratified layers with viscosity ratio 10, driven by a body force,
+    against the continuum solution of d/dy(mu du/dy) = -rho g for the
+    dynamic viscosity that Eq. 6 implies, mu = rho1 nu1 + rho2 nu2, on the
+    diffuse density profile (2 %).  The sharp-interface parabola is 16 % off
+    at this width: the diffuse interface carries the viscosity contrast."""
+    n, m = 4, 42
+    solid = np.zeros((m, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    nu1, nu2, g = nu_of_tau(1.7), nu_of_tau(0.62), 2e-7
+    h = 20.5
+    rho1, rho2 = media.layered_densities(m, n, h, solid=solid)
+    o = oracle.Oracle(solid, np.zeros((m, n), np.float32), nu1=nu1, nu2=nu2, gx=g, gy=0.0)
+    o.init(rho1, rho2)
+    o.step(50000)
+    dens = o.density()[:, :, 1]
+    ux = o.ux[:, 1]
+    # finite-volume solution on nodes 1..m-2, walls half-way (u = 0 there)
+    mu = dens[0] * nu1 + dens[1] * nu2
+    rho = dens[0] + dens[1]
+    J = np.arange(1, m - 1)
+    A = np.zeros((len(J), len(J)))
+    for k, j in enumerate(J):
+        for nb, kk in ((j + 1, k + 1), (j - 1, k - 1)):
+            if 1 <= nb <= m - 2:
+                face = 0.5 * (mu[j] + mu[nb])
+                A[k, kk] += face
+                A[k, k] -= face
+            else:
+                A[k, k] -= 2 * mu[j]
+    u_cont = np.linalg.solve(A, -rho[J] * g)
+    assert np.max(np.abs(ux[J] - u_cont)) < 0.02 * u_cont.max()
+
+
+# --- values printed in the paper --------------------------------------------------
+
+def _laplace_runs(tau1, tau2, radii=(9, 12, 16), n=64, steps=5000):
+    out = []
+    for r0 in radii:
+        rho1, rho2 = media.droplet_densities(n, n, n / 2, n / 2, r0)
+        o = _periodic(n, n, nu1=nu_of_tau(tau1), nu2=nu_of_tau(tau2))
+        o.init(rho1, rho2)
+        o.step(steps)
+        rho = o.density()
+        P = o.pressure_field()
+        thr = 0.5 * (rho[0].max() + rho[0].min())
+        R = math.sqrt((rho[0] > thr).sum() / math.pi)
+        out.append((1.0 / R, P[n // 2, n // 2] - P[0, 0], rho[0].min(), rho[1].min()))
+    return np.array(out)
+
+
+@pytest.mark.slow
+def test_laplace_law_surface_tension_and_minority_density():
+    res = _laplace_runs(1.0, 1.0)
+    k, b = np.polyfit(res[:, 0], res[:, 1], 1)
+    fit = np.polyval([k, b], res[:, 0])
+    r2 = 1 - np.sum((res[:, 1] - fit) ** 2) / np.sum((res[:, 1] - res[:, 1].mean()) ** 2)
+    assert r2 > 0.999
+    assert k == pytest.approx(GOLD["surface_tension_G3p5"]["value"], rel=0.10)
+    # dissolved minority density at G = 3.5
+    assert res[:, 2].mean() == pytest.approx(GOLD["minority_density_G3p5"]["value"], rel=0.08)
+
+
+@pytest.mark.slow
+def test_surface_tension_independent_of_viscosity_ratio():
+    g = []
+    for t1, t2 in (GOLD["viscosity_ratio_tau"]["value"]["M25"],
+                   GOLD["viscosity_ratio_tau"]["value"]["M1/25"], [1.0, 1.0]):
+        res = _laplace_runs(t1, t2, radii=(10, 16), steps=5000)
+        g.append((res[0, 1] - res[1, 1]) / (res[0, 0] - res[1, 0]))
+    assert max(g) / min(g) - 1 < 0.05
+
+
+def test_miscibility_below_threshold():
+    """Well below the printed threshold the components mix: a droplet at
+    G = 1.5 dissolves."""
+    n = 32
+    rho1, rho2 = media.droplet_densities(n, n, n / 2, n / 2, 8)
+    o = _periodic(n, n, nu1=1 / 6, nu2=1 / 6, g_coh=1.5)
+    o.init(rho1, rho2)
+    o.step(3000)
+    rho = o.density()
+    assert rho[0].max() - rho[0].min() < 0.05
+    assert GOLD["miscibility_threshold_G"]["value"] > 1.5
+
+
+def _sessile_angle(xi_val, n=120, m=60, r0=20, steps=12000):
+    """Contact angle of a droplet of component 1 on the bottom wall,
+    measured through component 2 (Sec. 3.3): circle through the interface
+    points found by linear interpolation, the wall at the half-way position."""
+    solid = np.zeros((m, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    xi = media.uniform_xi(solid, xi_val)
+    rho1, rho2 = media.droplet_densities(n, m, n / 2, 0.5, r0, solid=solid)
+    o = oracle.Oracle(solid, xi, nu1=1 / 6, nu2=1 / 6)
+    o.init(rho1, rho2)
+    o.step(steps)
+    rho = o.density()
+    phi = rho[0] - rho[1]
+    # interface points: zero crossings of phi along rows and columns
+    pts = []
+    for y in range(1, m - 1):
+        row = phi[y]
+        for x in range(n - 1):
+            if row[x] * row[x + 1] < 0:
+                pts.append((x + row[x] / (row[x] - row[x + 1]), y))
+    for x in range(n):
+        col = phi[:, x]
+        for y in range(1, m - 2):
+            if col[y] * col[y + 1] < 0:
+                pts.append((x, y + col[y] / (col[y] - col[y + 1])))
+    pts = np.array([p for p in pts if p[1] >= 5.5])   # away from the wall
+    # least-squares circle x^2 + y^2 + D x + E y + F = 0
+    A = np.c_[pts[:, 0], pts[:, 1], np.ones(len(pts))]
+    rhs = -(pts[:, 0] ** 2 + pts[:, 1] ** 2)
+    D, Ecoef, F = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    yc = -Ecoef / 2
+    R = math.sqrt(D * D / 4 + Ecoef * Ecoef / 4 - F)
+    wall = 0.5
+    # angle inside the droplet at the wall line, then through component 2
+    cos_in = -(yc - wall) / R
+    theta_drop = math.degrees(math.acos(max(-1.0, min(1.0, cos_in))))
+    return 180.0 - theta_drop
+
+
+@pytest.mark.slow
+def test_contact_angle_neutral_and_symmetric():
+    t0 = _sessile_angle(0.0)
+    assert t0 == pytest.approx(90.0, abs=2.0)
+    tp, tm = _sessile_angle(0.3), _sessile_angle(-0.3)
+    assert tp + tm == pytest.approx(180.0, abs=1.0)
+    pairs = dict((round(a, 2), b) for a, b in GOLD["xi_theta_pairs"]["value"])
+    assert tm == pytest.approx(pairs[-0.3], abs=8.0)
+    assert tp == pytest.approx(pairs[0.3], abs=8.0)
