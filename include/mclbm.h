@@ -1,0 +1,207 @@
+/*
+ * mclbm.h - C ABI of the GB300 two-component pseudopotential lattice
+ * Boltzmann library (improved multicomponent Shan-Chen model of Sedahmed,
+ * Coelho and Warda, arXiv:2111.08666).
+ *
+ * The library advances a two-component D2Q9 lattice over a 2-D porous
+ * medium: component densities and pseudopotentials, inter-component cohesion
+ * (Eq. 13) and improved-virtual-solid-density adhesion (Eqs. 15-17), the
+ * modified explicit-forcing BGK collision with a system relaxation time
+ * (Eqs. 1, 2, 6, 8, 11), streaming with half-way bounce-back, and the Set-3
+ * inlet/outlet pressure boundaries (Sec. 2.3, Eqs. 18-28).
+ *
+ * Conventions shared by every call:
+ *  - Lattice arrays are row-major [ny][nx]; x is the flow direction, the
+ *    inlet is column x = 0 and the outlet column x = nx-1.  Populations are
+ *    [2][9][ny][nx]: component (0 = component 1, 1 = component 2), direction
+ *    i of Sec. 2.1 (e_0..e_8 = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+ *    (-1,-1) (1,-1)), row, column.
+ *  - Lattice units throughout (dx = dt = 1, c_s^2 = 1/3).
+ *  - Every call returns MCLBM_OK (0) or a negative error code; on error
+ *    mclbm_last_error() gives a message (thread-local, valid until the next
+ *    failing call on the same thread).  No call throws or aborts.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  Buffers
+ *    the library fills may be host memory (pageable or pinned) or device
+ *    memory; the library tells them apart with cudaPointerGetAttributes.
+ *  - Work is enqueued on the lattice's CUDA stream.  mclbm_step returns
+ *    before the GPU finishes; the read-outs synchronise that stream.
+ *  - The library owns all device memory of a lattice and frees it in
+ *    mclbm_destroy.  A lattice must not be used from two threads at once.
+ */
+#ifndef MCLBM_H
+#define MCLBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define MCLBM_OK 0
+#define MCLBM_ERR_ARG (-1)      /* invalid argument (null, size, range) */
+#define MCLBM_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define MCLBM_ERR_DIVERGED (-3) /* non-finite or negative density detected */
+#define MCLBM_ERR_TIMEOUT (-4)  /* a bounded device-side wait ran out */
+#define MCLBM_ERR_STATE (-5)    /* call not valid in the lattice's state */
+#define MCLBM_ERR_NOMEM (-6)    /* device or host allocation failed */
+
+/* Storage precision of the populations.  FP64 and FP32 store f_i; the
+ * deviation variants store f_i - w_i (reference density 1) in FP32, FP16 or
+ * BF16 and compute in FP32.  Global reductions are FP64 in every variant. */
+typedef enum {
+    MCLBM_FP64 = 0,
+    MCLBM_FP32 = 1,
+    MCLBM_FP32_DEV = 2,
+    MCLBM_FP16_DEV = 3,
+    MCLBM_BF16_DEV = 4
+} mclbm_precision;
+
+/* Switches for mclbm_set_flag. */
+typedef enum {
+    /* 1: periodic in y.  0 (default): rows 0 and ny-1 must be solid walls. */
+    MCLBM_FLAG_PERIODIC_Y = 0,
+    /* 1 (default): the velocity in Eqs. 2 and 11 carries half the total
+     * force, u = (sum_sigma sum_i e_i f_i + F/2) / rho, which the
+     * (1 - 1/(2 tau_s)) prefactor of Eq. 1 needs for the momentum balance.
+     * 0: the literal barycentric velocity of Eq. 8. */
+    MCLBM_FLAG_VEL_SHIFT = 1,
+    /* k > 0: every k steps mclbm_step runs the divergence check (non-finite
+     * or negative density); a hit is reported by the next synchronising
+     * call as MCLBM_ERR_DIVERGED.  0 (default): off. */
+    MCLBM_FLAG_DIAG_EVERY = 2
+} mclbm_flag;
+
+typedef struct mclbm_lattice mclbm_lattice;
+
+/*
+ * Create a lattice of nx * ny nodes (nx >= 3, ny >= 3).
+ *   solid [ny][nx]  1 = solid node (phi = 1 of Eq. 16), 0 = fluid.
+ *   xi    [ny][nx]  wettability parameter of Eq. 17 (chi^1 = 1 + xi,
+ *                   chi^2 = 1 - xi), read at solid nodes only.  At most 254
+ *                   distinct values over the solid nodes.  May be NULL
+ *                   (xi = 0 everywhere, neutral wetting).
+ *   prec            storage precision.
+ *   cuda_stream     cudaStream_t to run on, or NULL for a stream the library
+ *                   creates and owns.
+ * Defaults: nu1 = nu2 = 1/6 (tau = 1), G_coh = G_ads = 3.5 (Sec. 2.1),
+ * no body force, periodic x (no pressure boundaries), walls in y, velocity
+ * shift on.  The populations start at zero: call mclbm_init_densities.
+ */
+int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi,
+                 mclbm_precision prec, void *cuda_stream, mclbm_lattice **out);
+
+/* Free the lattice and all its device memory.  NULL is accepted. */
+int mclbm_destroy(mclbm_lattice *lat);
+
+int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value);
+
+/* Kinematic viscosities of the components, Eq. 7 read as
+ * nu = c_s^2 (tau - 1/2); they set the system relaxation time of Eq. 6. */
+int mclbm_set_viscosity(mclbm_lattice *lat, double nu1, double nu2);
+
+/* Cohesion strength G_coh (Eq. 13) and adhesion strength G_ads (Eq. 15);
+ * the paper uses 3.5 for both (Sec. 2.2). */
+int mclbm_set_coupling(mclbm_lattice *lat, double g_coh, double g_ads);
+
+/* Body acceleration g: F^b,sigma = rho^sigma g (Eq. 12). */
+int mclbm_set_body_force(mclbm_lattice *lat, double gx, double gy);
+
+/* Set-3 pressure boundaries (Sec. 2.3): rho_in1 is the density of component
+ * 1 imposed at x = 0 (Eqs. 22-25), rho_out2 that of component 2 at
+ * x = nx-1 (Eqs. 18-21).  Either value < 0 switches the boundaries off and
+ * makes x periodic. */
+int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2);
+
+/* The same boundaries given as pressures: Eq. 14 is inverted for the
+ * majority density with the minority density held at 0.027 (the dissolved
+ * density at G = 3.5, Sec. 3.2).  A negative pressure switches them off. */
+int mclbm_set_pressure_bc_p(mclbm_lattice *lat, double p_in, double p_out);
+
+/* Change the stream subsequent work is enqueued on (NULL: the library's
+ * own stream). */
+int mclbm_set_stream(mclbm_lattice *lat, void *cuda_stream);
+
+/*
+ * Initialise at rest from component densities rho1, rho2 [ny][nx] (host or
+ * device, FP64): f_i = f_i^eq(rho^sigma, u = 0) of Eq. 2 on fluid nodes,
+ * zero on solid nodes; the step counter restarts at 0.  The values taken by
+ * component 1's f_3, f_6, f_7 on the outlet column are recorded as the
+ * values Eq. 26 keeps there.
+ */
+int mclbm_init_densities(mclbm_lattice *lat, const double *rho1, const double *rho2);
+
+/* Replace the post-collision populations by f [2][9][ny][nx] (FP64, host or
+ * device).  Values on solid nodes are ignored.  Like mclbm_init_densities,
+ * this records component 1's outlet f_3, f_6, f_7 for Eq. 26. */
+int mclbm_set_populations(mclbm_lattice *lat, const double *f);
+
+/* Copy the post-collision populations into f [2][9][ny][nx] (FP64, host or
+ * device); zero on solid nodes.  Synchronises the stream. */
+int mclbm_get_populations(mclbm_lattice *lat, double *f);
+
+/*
+ * Advance nsteps time steps of Eq. 1 with the fused kernel: pull streaming
+ * with half-way bounce-back, Set-3 boundaries, moments (Eqs. 3-5), virtual
+ * solid densities (Eqs. 16-17), forces (Eqs. 12-15 with the boundary-column
+ * mirror of Sec. 2.1), system relaxation time and velocity (Eqs. 6-9), and
+ * the forced BGK collision (Eqs. 1, 2, 11).  Asynchronous.
+ */
+int mclbm_step(mclbm_lattice *lat, int64_t nsteps);
+
+/* Wait for the lattice's stream; returns MCLBM_ERR_DIVERGED if the
+ * divergence check (MCLBM_FLAG_DIAG_EVERY) fired since the last call. */
+int mclbm_synchronize(mclbm_lattice *lat);
+
+/* Component density rho^sigma (Eq. 3) of the current state, comp = 1 or 2,
+ * into out [ny][nx] (FP64, host or device); zero on solid nodes. */
+int mclbm_read_density(mclbm_lattice *lat, int comp, double *out);
+
+/* Common velocity u = u^eq of the last collision (Eq. 9) into ux, uy
+ * [ny][nx] (FP64, host or device); zero on solid nodes. */
+int mclbm_read_velocity(mclbm_lattice *lat, double *ux, double *uy);
+
+/* Pressure of Eq. 14, P = (rho1 + rho2)/3 + (G_coh/3) rho1 rho2, into
+ * out [ny][nx] (FP64); zero on solid nodes. */
+int mclbm_read_pressure(mclbm_lattice *lat, double *out);
+
+/* Phase field (rho1 - rho2)/(rho1 + rho2) into out [ny][nx] (FP32); zero on
+ * solid nodes. */
+int mclbm_read_phase(mclbm_lattice *lat, float *out);
+
+/*
+ * All global diagnostics of the current state, reduced in FP64 (Sec. 4.2.1):
+ *   out[0], out[1]  mass of component 1 and 2 over the fluid nodes
+ *   out[2]          water saturation S_w by count: fluid nodes with
+ *                   rho2 > rho1 over all fluid nodes
+ *   out[3]          S_w by mass: sum rho2 / sum (rho1 + rho2)
+ *   out[4], out[5]  P_in, P_out: mean of Eq. 14 over the fluid nodes of
+ *                   column 0 (nx-1) more than 2 nodes in y from any solid
+ *                   node of that column (NaN if there is none)
+ *   out[6]          capillary pressure P_c = P_in - P_out
+ *   out[7]          number of fluid nodes
+ * out is host memory.  Synchronises the stream.
+ */
+int mclbm_diagnostics(mclbm_lattice *lat, double out[8]);
+
+/* Conveniences over mclbm_diagnostics. */
+int mclbm_saturation(mclbm_lattice *lat, double *sw_count, double *sw_mass);
+int mclbm_capillary_pressure(mclbm_lattice *lat, double *pc, double *p_in, double *p_out);
+int mclbm_mass(mclbm_lattice *lat, double out[2]);
+
+/* Lattice facts: out[0] nx, out[1] ny, out[2] row pitch in elements,
+ * out[3] precision, out[4] steps taken since initialisation, out[5] bytes
+ * of device memory held. */
+int mclbm_info(mclbm_lattice *lat, int64_t out[6]);
+
+/* Kernel launches enqueued by this library since it was loaded (all
+ * lattices); used to count the GPU work inside a timed region. */
+int64_t mclbm_launch_count(void);
+
+const char *mclbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCLBM_H */

@@ -1,0 +1,149 @@
+// Internal declarations of the CUDA library: D2Q9 constants, storage
+// precisions, the lattice object and the kernel launchers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "mclbm.h"
+
+namespace mclbm {
+
+// ---------------------------------------------------------------------------
+// D2Q9 lattice (Sec. 2.1).  Written as constexpr functions so that unrolled
+// loops fold them into immediates.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ex(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 5 + 2) % 4) + 5);
+}
+template <class R>
+__host__ __device__ constexpr R wgt(int i) {
+    return i == 0 ? R(4) / R(9) : (i <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
+
+// Geometry code of a node: 0 fluid, 1..254 solid with wettability-table
+// index, 255 outside the domain (beyond a non-periodic edge).
+constexpr uint8_t GEO_FLUID = 0;
+constexpr uint8_t GEO_OUTSIDE = 255;
+constexpr int MAX_XI_VALUES = 254;
+
+// ---------------------------------------------------------------------------
+// Storage precisions.  Populations are stored as S and computed in R; the
+// deviation variants store f_i - w_i (reference density 1).
+// ---------------------------------------------------------------------------
+template <class S, class R, bool DEV>
+struct Prec {
+    using store_t = S;
+    using real_t = R;
+    static constexpr bool dev = DEV;
+};
+using P64 = Prec<double, double, false>;
+using P32 = Prec<float, float, false>;
+using P32D = Prec<float, float, true>;
+using P16D = Prec<__half, float, true>;
+using PB16D = Prec<__nv_bfloat16, float, true>;
+
+__device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_real(float v) { return v; }
+__device__ __forceinline__ double to_real(double v) { return v; }
+template <class S> __device__ __forceinline__ S from_real(float v);
+template <> __device__ __forceinline__ float from_real<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_real<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <class S> __device__ __forceinline__ S from_real(double v) { return (S)v; }
+
+// ---------------------------------------------------------------------------
+// Physical and boundary parameters of a lattice, passed by value to kernels.
+// ---------------------------------------------------------------------------
+struct Params {
+    double nu1 = 1.0 / 6.0, nu2 = 1.0 / 6.0;
+    double g_coh = 3.5, g_ads = 3.5;
+    double gx = 0.0, gy = 0.0;
+    double rho_in1 = -1.0, rho_out2 = -1.0;
+    int open_x = 0;      // Set-3 boundaries on at x = 0 and x = nx-1
+    int periodic_y = 0;  // else rows 0 and ny-1 must be solid
+    int vel_shift = 1;   // u carries F/2
+};
+
+// Arguments of the fused step kernel and the field kernels.
+struct Geometry {
+    int nx, ny, pitch;         // pitch: row stride in elements
+    long long plane;           // pitch * ny: elements per direction plane
+    const uint8_t *geo;        // [ny][pitch] geometry code
+    const double *chi;         // [256][2] (1 + xi, 1 - xi) by code, in FP64
+};
+
+struct StepArgs {
+    Geometry g;
+    Params p;
+    const void *fin;           // [2][9][ny][pitch] post-collision, step t
+    void *fout;                // post-collision, step t+1
+    const void *d5;            // [3][ny] component-1 outlet f_{3,6,7} (real type)
+};
+
+// ---------------------------------------------------------------------------
+// The lattice object behind the opaque handle of the C ABI.
+// ---------------------------------------------------------------------------
+struct Lattice {
+    int nx = 0, ny = 0, pitch = 0;
+    mclbm_precision prec = MCLBM_FP32;
+    size_t store_bytes = 4;    // bytes per stored population
+    size_t real_bytes = 4;     // bytes of the math type
+    Params p;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    uint8_t *geo = nullptr;    // [ny][pitch]
+    double *chi = nullptr;     // [256][2]
+    void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
+    int cur = 0;               // index of the buffer holding the state
+    void *d5 = nullptr;        // [3][ny] real type
+    double *diag_partial = nullptr;   // scratch of the diagnostics reduction
+    int diag_blocks = 0;
+    double *diag_out = nullptr;       // [8] device
+    double *host_diag = nullptr;      // [8] pinned
+    unsigned long long *bad_flag = nullptr;  // device: divergence count
+    int64_t diag_every = 0;
+    int64_t steps = 0;
+    size_t device_bytes = 0;
+    bool boundary_rows_solid = false;
+    bool boundary_cols_fluid_ok = true;
+    bool initialised = false;
+};
+
+// status helpers (capi.cu)
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+void count_launch(int n = 1);
+
+// launchers (step.cu, fields.cu); return cudaError_t of the launch
+cudaError_t launch_step(Lattice &L, int tile_cfg);
+cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
+cudaError_t launch_set_populations(Lattice &L, const double *f);
+cudaError_t launch_get_populations(Lattice &L, double *f);
+cudaError_t launch_diagnostics(Lattice &L);
+cudaError_t launch_bad_check(Lattice &L);
+cudaError_t launch_density(Lattice &L, int comp, double *out);
+cudaError_t launch_pressure(Lattice &L, double *out);
+cudaError_t launch_phase(Lattice &L, float *out);
+cudaError_t launch_velocity(Lattice &L, double *ux, double *uy, void *scratch);
+size_t velocity_scratch_bytes(const Lattice &L);
+int diag_blocks_for(const Lattice &L);
+
+}  // namespace mclbm

@@ -1,0 +1,344 @@
+"""ctypes binding of the C ABI in ``include/mclbm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``_lib/libmclbm.so``.  Functions keep the C names; buffers may be
+numpy arrays (host) or torch tensors (host or CUDA), and must be contiguous
+with the dtype the C signature names.  There is no CPU fallback: if the
+library cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+MCLBM_OK = 0
+MCLBM_ERR_ARG = -1
+MCLBM_ERR_CUDA = -2
+MCLBM_ERR_DIVERGED = -3
+MCLBM_ERR_TIMEOUT = -4
+MCLBM_ERR_STATE = -5
+MCLBM_ERR_NOMEM = -6
+
+MCLBM_FP64, MCLBM_FP32, MCLBM_FP32_DEV, MCLBM_FP16_DEV, MCLBM_BF16_DEV = range(5)
+PRECISIONS = {"fp64": MCLBM_FP64, "fp32": MCLBM_FP32, "fp32dev": MCLBM_FP32_DEV,
+              "fp16dev": MCLBM_FP16_DEV, "bf16dev": MCLBM_BF16_DEV}
+STORE_BYTES = {MCLBM_FP64: 8, MCLBM_FP32: 4, MCLBM_FP32_DEV: 4, MCLBM_FP16_DEV: 2,
+               MCLBM_BF16_DEV: 2}
+
+MCLBM_FLAG_PERIODIC_Y = 0
+MCLBM_FLAG_VEL_SHIFT = 1
+MCLBM_FLAG_DIAG_EVERY = 2
+
+DIAG_FIELDS = ("mass1", "mass2", "sw_count", "sw_mass", "p_in", "p_out", "pc", "n_fluid")
+
+
+class MclbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mclbm error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_P = C.POINTER
+_vp = C.c_void_p
+_i64 = C.c_int64
+
+_SIGS = {
+    "mclbm_create": (C.c_int, [C.c_int, C.c_int, _vp, _vp, C.c_int, _vp, _P(_vp)]),
+    "mclbm_destroy": (C.c_int, [_vp]),
+    "mclbm_set_flag": (C.c_int, [_vp, C.c_int, _i64]),
+    "mclbm_set_viscosity": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_coupling": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_body_force": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_pressure_bc": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_pressure_bc_p": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_stream": (C.c_int, [_vp, _vp]),
+    "mclbm_init_densities": (C.c_int, [_vp, _vp, _vp]),
+    "mclbm_set_populations": (C.c_int, [_vp, _vp]),
+    "mclbm_get_populations": (C.c_int, [_vp, _vp]),
+    "mclbm_step": (C.c_int, [_vp, _i64]),
+    "mclbm_synchronize": (C.c_int, [_vp]),
+    "mclbm_read_density": (C.c_int, [_vp, C.c_int, _vp]),
+    "mclbm_read_velocity": (C.c_int, [_vp, _vp, _vp]),
+    "mclbm_read_pressure": (C.c_int, [_vp, _vp]),
+    "mclbm_read_phase": (C.c_int, [_vp, _vp]),
+    "mclbm_diagnostics": (C.c_int, [_vp, _vp]),
+    "mclbm_saturation": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double)]),
+    "mclbm_capillary_pressure": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
+    "mclbm_mass": (C.c_int, [_vp, _vp]),
+    "mclbm_info": (C.c_int, [_vp, _vp]),
+    "mclbm_launch_count": (_i64, []),
+    "mclbm_last_error": (C.c_char_p, []),
+}
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libmclbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    path = library_path()
+    if not path.exists():
+        raise RuntimeError(f"CUDA library {path} is missing; run the package build first")
+    lib = C.CDLL(str(path))
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> None:
+    if rc != MCLBM_OK:
+        msg = load().mclbm_last_error()
+        raise MclbmError(rc, msg.decode() if msg else "")
+
+
+def _addr(buf, dtype) -> int:
+    """Address of a contiguous numpy array or torch tensor of the given dtype."""
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.dtype(dtype):
+            raise TypeError(f"expected {np.dtype(dtype)}, got {buf.dtype}")
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data
+    # torch tensor
+    import torch
+    want = {np.float64: torch.float64, np.float32: torch.float32,
+            np.uint8: torch.uint8}[np.dtype(dtype).type]
+    if buf.dtype != want:
+        raise TypeError(f"expected {want}, got {buf.dtype}")
+    if not buf.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return buf.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# --- the C functions, same names -------------------------------------------------
+
+def mclbm_create(nx: int, ny: int, solid, xi=None, prec: int = MCLBM_FP32, stream=None):
+    lib = load()
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    if solid.shape != (ny, nx):
+        raise ValueError(f"solid must be [ny][nx] = [{ny}][{nx}]")
+    xi_arr = None if xi is None else np.ascontiguousarray(xi, dtype=np.float32)
+    if xi_arr is not None and xi_arr.shape != (ny, nx):
+        raise ValueError("xi must be [ny][nx]")
+    h = _vp()
+    _check(lib.mclbm_create(nx, ny, _addr(solid, np.uint8), _addr(xi_arr, np.float32),
+                            int(prec), _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def mclbm_destroy(h) -> None:
+    _check(load().mclbm_destroy(h))
+
+
+def mclbm_set_flag(h, flag: int, value: int) -> None:
+    _check(load().mclbm_set_flag(h, flag, int(value)))
+
+
+def mclbm_set_viscosity(h, nu1: float, nu2: float) -> None:
+    _check(load().mclbm_set_viscosity(h, nu1, nu2))
+
+
+def mclbm_set_coupling(h, g_coh: float, g_ads: float) -> None:
+    _check(load().mclbm_set_coupling(h, g_coh, g_ads))
+
+
+def mclbm_set_body_force(h, gx: float, gy: float) -> None:
+    _check(load().mclbm_set_body_force(h, gx, gy))
+
+
+def mclbm_set_pressure_bc(h, rho_in1: float, rho_out2: float) -> None:
+    _check(load().mclbm_set_pressure_bc(h, rho_in1, rho_out2))
+
+
+def mclbm_set_pressure_bc_p(h, p_in: float, p_out: float) -> None:
+    _check(load().mclbm_set_pressure_bc_p(h, p_in, p_out))
+
+
+def mclbm_set_stream(h, stream) -> None:
+    _check(load().mclbm_set_stream(h, _stream_handle(stream)))
+
+
+def mclbm_init_densities(h, rho1, rho2) -> None:
+    _check(load().mclbm_init_densities(h, _addr(rho1, np.float64), _addr(rho2, np.float64)))
+
+
+def mclbm_set_populations(h, f) -> None:
+    _check(load().mclbm_set_populations(h, _addr(f, np.float64)))
+
+
+def mclbm_get_populations(h, f) -> None:
+    _check(load().mclbm_get_populations(h, _addr(f, np.float64)))
+
+
+def mclbm_step(h, nsteps: int) -> None:
+    _check(load().mclbm_step(h, int(nsteps)))
+
+
+def mclbm_synchronize(h) -> None:
+    _check(load().mclbm_synchronize(h))
+
+
+def mclbm_read_density(h, comp: int, out) -> None:
+    _check(load().mclbm_read_density(h, comp, _addr(out, np.float64)))
+
+
+def mclbm_read_velocity(h, ux, uy) -> None:
+    _check(load().mclbm_read_velocity(h, _addr(ux, np.float64), _addr(uy, np.float64)))
+
+
+def mclbm_read_pressure(h, out) -> None:
+    _check(load().mclbm_read_pressure(h, _addr(out, np.float64)))
+
+
+def mclbm_read_phase(h, out) -> None:
+    _check(load().mclbm_read_phase(h, _addr(out, np.float32)))
+
+
+def mclbm_diagnostics(h) -> dict:
+    out = np.zeros(8)
+    _check(load().mclbm_diagnostics(h, out.ctypes.data))
+    return dict(zip(DIAG_FIELDS, out.tolist()))
+
+
+def mclbm_saturation(h) -> tuple[float, float]:
+    a, b = C.c_double(), C.c_double()
+    _check(load().mclbm_saturation(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def mclbm_capillary_pressure(h) -> tuple[float, float, float]:
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(load().mclbm_capillary_pressure(h, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def mclbm_mass(h) -> tuple[float, float]:
+    out = np.zeros(2)
+    _check(load().mclbm_mass(h, out.ctypes.data))
+    return float(out[0]), float(out[1])
+
+
+def mclbm_info(h) -> dict:
+    out = np.zeros(6, dtype=np.int64)
+    _check(load().mclbm_info(h, out.ctypes.data))
+    return dict(zip(("nx", "ny", "pitch", "precision", "steps", "device_bytes"), out.tolist()))
+
+
+def mclbm_launch_count() -> int:
+    return int(load().mclbm_launch_count())
+
+
+def mclbm_last_error() -> str:
+    msg = load().mclbm_last_error()
+    return msg.decode() if msg else ""
+
+
+# --- a small object wrapper ---------------------------------------------------------
+
+class Lattice:
+    """Owning handle of one lattice (context manager)."""
+
+    def __init__(self, solid, xi=None, *, prec: int | str = MCLBM_FP32, nu1: float = 1 / 6,
+                 nu2: float = 1 / 6, g_coh: float = 3.5, g_ads: float | None = None,
+                 rho_in1: float = -1.0, rho_out2: float = -1.0, periodic_y: bool = False,
+                 vel_shift: bool = True, gx: float = 0.0, gy: float = 0.0, stream=None):
+        self.h = None
+        if isinstance(prec, str):
+            prec = PRECISIONS[prec]
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        self.ny, self.nx = solid.shape
+        self.prec = prec
+        self.h = mclbm_create(self.nx, self.ny, solid, xi, prec, stream)
+        mclbm_set_viscosity(self.h, nu1, nu2)
+        mclbm_set_coupling(self.h, g_coh, g_coh if g_ads is None else g_ads)
+        mclbm_set_pressure_bc(self.h, rho_in1, rho_out2)
+        mclbm_set_flag(self.h, MCLBM_FLAG_PERIODIC_Y, int(periodic_y))
+        mclbm_set_flag(self.h, MCLBM_FLAG_VEL_SHIFT, int(vel_shift))
+        mclbm_set_body_force(self.h, gx, gy)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            mclbm_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, rho1, rho2) -> None:
+        r1 = rho1 if not isinstance(rho1, np.ndarray) else np.ascontiguousarray(rho1, np.float64)
+        r2 = rho2 if not isinstance(rho2, np.ndarray) else np.ascontiguousarray(rho2, np.float64)
+        mclbm_init_densities(self.h, r1, r2)
+
+    def step(self, n: int = 1) -> None:
+        mclbm_step(self.h, n)
+
+    def sync(self) -> None:
+        mclbm_synchronize(self.h)
+
+    def populations(self) -> np.ndarray:
+        f = np.zeros((2, 9, self.ny, self.nx))
+        mclbm_get_populations(self.h, f)
+        return f
+
+    def set_populations(self, f) -> None:
+        mclbm_set_populations(self.h, np.ascontiguousarray(f, dtype=np.float64))
+
+    def density(self) -> np.ndarray:
+        out = np.zeros((2, self.ny, self.nx))
+        mclbm_read_density(self.h, 1, out[0])
+        mclbm_read_density(self.h, 2, out[1])
+        return out
+
+    def velocity(self):
+        ux = np.zeros((self.ny, self.nx))
+        uy = np.zeros((self.ny, self.nx))
+        mclbm_read_velocity(self.h, ux, uy)
+        return ux, uy
+
+    def pressure(self) -> np.ndarray:
+        out = np.zeros((self.ny, self.nx))
+        mclbm_read_pressure(self.h, out)
+        return out
+
+    def phase(self) -> np.ndarray:
+        out = np.zeros((self.ny, self.nx), dtype=np.float32)
+        mclbm_read_phase(self.h, out)
+        return out
+
+    def diagnostics(self) -> dict:
+        return mclbm_diagnostics(self.h)
+
+    def set_pressure_bc(self, rho_in1: float, rho_out2: float) -> None:
+        mclbm_set_pressure_bc(self.h, rho_in1, rho_out2)
+
+    def info(self) -> dict:
+        return mclbm_info(self.h)

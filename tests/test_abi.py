@@ -1,0 +1,54 @@
+"""The C ABI library builds, loads without a GPU, exports every function the
+header declares, and rejects bad arguments before touching the device."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_2111_08666_gb300 import mclbm
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(mclbm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mclbm_create", "mclbm_step", "mclbm_read_density", "mclbm_read_velocity",
+                     "mclbm_saturation", "mclbm_capillary_pressure", "mclbm_mass",
+                     "mclbm_set_pressure_bc", "mclbm_set_viscosity", "mclbm_set_coupling",
+                     "mclbm_destroy", "mclbm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = mclbm.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    missing = [n for n in declared_functions() if not hasattr(mclbm, n)]
+    assert not missing, missing
+
+
+def test_argument_errors_without_a_device():
+    lib = mclbm.load()
+    h = C.c_void_p()
+    assert lib.mclbm_create(8, 8, None, None, 1, None, C.byref(h)) == mclbm.MCLBM_ERR_ARG
+    assert b"solid" in lib.mclbm_last_error()
+    assert lib.mclbm_create(2, 8, None, None, 1, None, C.byref(h)) == mclbm.MCLBM_ERR_ARG
+    assert lib.mclbm_create(8, 8, None, None, 1, None, None) == mclbm.MCLBM_ERR_ARG
+    assert lib.mclbm_step(None, 1) == mclbm.MCLBM_ERR_ARG
+    assert lib.mclbm_set_viscosity(None, 0.1, 0.1) == mclbm.MCLBM_ERR_ARG
+    assert lib.mclbm_destroy(None) == mclbm.MCLBM_OK
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_step(None, 1)
+    assert e.value.code == mclbm.MCLBM_ERR_ARG

@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: FP64 populations within 1e-10 of max|f| after 200+ steps; FP32
+densities within 1e-4 and saturation within 1e-3 (absolute).  Inputs are the
+seeded synthetic media of ``paper_2111_08666_gb300.media``; the oracle and
+the GPU start from the same arrays.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_08666_gb300 import media
+from paper_2111_08666_gb300 import mclbm
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+def nu_of_tau(t):
+    return (t - 0.5) / 3.0
+
+
+def pair(solid, xi, rho1, rho2, prec="fp64", **kw):
+    """The same case on the oracle and on the GPU."""
+    o = oracle.Oracle(solid, xi, **kw)
+    o.init(rho1, rho2)
+    g = mclbm.Lattice(solid, xi, prec=prec, **kw)
+    g.init(rho1, rho2)
+    return o, g
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def assert_fp64_parity(o, g, steps):
+    o.step(steps)
+    g.step(steps)
+    f = g.populations()
+    err = rel_err(f, o.f)
+    assert err < FP64_TOL, err
+    return f
+
+
+def test_init_and_roundtrip_exact():
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], nu1=c["nu1"], nu2=c["nu2"],
+                rho_in1=1.01, rho_out2=1.0)
+    f = g.populations()
+    assert np.array_equal(f, o.f)
+    rng = np.random.default_rng(0)
+    h = rng.random(f.shape) * (c["solid"] == 0)
+    g.set_populations(h)
+    assert np.array_equal(g.populations(), h)
+
+
+def test_fp64_disk_medium_drainage_200_steps():
+    """128x64 disk medium, radii U[4,8], porosity ~0.65, Set-3 boundaries
+    with rho_in = 1.01, rho_out = 1, neutral wetting, M = 1."""
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], nu1=c["nu1"], nu2=c["nu2"],
+                rho_in1=c["rho_in1"], rho_out2=c["rho_out2"])
+    assert_fp64_parity(o, g, 200)
+    assert_fp64_parity(o, g, 300)  # 500 in total
+
+
+def test_fp64_ragged_mixed_wettability_viscosity_ratio_25():
+    """Sizes off every tile multiple, several per-site xi values, M = 25."""
+    nx, ny = 45, 21
+    m = media.make_disk_medium(nx, ny, 7, radius="uniform", r_lo=2.0, r_hi=4.0,
+                               porosity=0.75, reservoir=5)
+    rng = np.random.default_rng(1)
+    xi = np.where(m.solid != 0, rng.choice([-0.55, -0.4, 0.0, 0.2, 0.5], size=m.solid.shape),
+                  0.0).astype(np.float32)
+    rho1, rho2 = media.drainage_densities(m.solid, oil_columns=4)
+    o, g = pair(m.solid, xi, rho1, rho2, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62),
+                rho_in1=1.02, rho_out2=1.0)
+    assert_fp64_parity(o, g, 300)
+
+
+def test_fp64_periodic_droplet_with_grain_and_body_force():
+    nx, ny = 40, 30
+    solid = np.zeros((ny, nx), np.uint8)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    solid[(xx - 28) ** 2 + (yy - 15) ** 2 <= 20] = 1
+    xi = media.uniform_xi(solid, 0.3)
+    rho1, rho2 = media.droplet_densities(nx, ny, 12, 14, 6, solid=solid)
+    o, g = pair(solid, xi, rho1, rho2, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
+                periodic_y=True, gx=2e-5, gy=-1e-5)
+    assert_fp64_parity(o, g, 250)
+
+
+def test_fp64_open_x_periodic_y():
+    nx, ny = 50, 24
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[8:14, 20:27] = 1
+    xi = media.uniform_xi(solid, -0.3)
+    rho1, rho2 = media.drainage_densities(solid)
+    o, g = pair(solid, xi, rho1, rho2, nu1=nu_of_tau(1.0), nu2=nu_of_tau(0.62),
+                rho_in1=1.015, rho_out2=1.0, periodic_y=True)
+    assert_fp64_parity(o, g, 200)
+
+
+def test_fp64_unshifted_velocity_reading():
+    nx, ny = 37, 19
+    m = media.make_disk_medium(nx, ny, 3, radius="uniform", r_lo=2.0, r_hi=3.0,
+                               porosity=0.8, reservoir=4)
+    rho1, rho2 = media.drainage_densities(m.solid, oil_columns=3)
+    o, g = pair(m.solid, media.uniform_xi(m.solid, -0.2), rho1, rho2, nu1=0.1, nu2=0.05,
+                rho_in1=1.01, rho_out2=1.0, vel_shift=False)
+    assert_fp64_parity(o, g, 200)
+
+
+def test_fp64_lattice_smaller_than_a_tile():
+    nx, ny = 7, 5
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[2, 3] = 1
+    rng = np.random.default_rng(5)
+    rho1 = (0.1 + rng.random((ny, nx))) * (solid == 0)
+    rho2 = (0.1 + rng.random((ny, nx))) * (solid == 0)
+    o, g = pair(solid, media.uniform_xi(solid, 0.1), rho1, rho2, nu1=0.12, nu2=0.2,
+                periodic_y=True)
+    assert_fp64_parity(o, g, 200)
+
+
+def test_readouts_and_diagnostics_match_oracle():
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], media.uniform_xi(c["solid"], -0.4), c["rho1"], c["rho2"],
+                nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+    o.step(150)
+    g.step(150)
+    assert rel_err(g.density(), o.density()) < FP64_TOL
+    ux, uy = g.velocity()
+    umax = max(np.abs(o.ux).max(), np.abs(o.uy).max())
+    assert np.max(np.abs(ux - o.ux)) < 1e-9 * umax
+    assert np.max(np.abs(uy - o.uy)) < 1e-9 * umax
+    assert rel_err(g.pressure(), o.pressure_field()) < FP64_TOL
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass1", "mass2", "sw_mass", "p_in", "p_out"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-12), k
+    assert dg["sw_count"] == do["sw_count"]
+    assert dg["n_fluid"] == do["n_fluid"]
+    assert dg["pc"] == pytest.approx(do["pc"], abs=1e-13)
+    rho = o.density()
+    phase = np.where(c["solid"] == 0, (rho[0] - rho[1]) / np.maximum(rho[0] + rho[1], 1e-300), 0)
+    assert np.max(np.abs(g.phase() - phase)) < 1e-6
+
+
+def test_fp32_matches_oracle_after_2000_steps():
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], prec="fp32", nu1=c["nu1"],
+                nu2=c["nu2"], rho_in1=c["rho_in1"], rho_out2=c["rho_out2"])
+    o.step(2000)
+    g.step(2000)
+    assert rel_err(g.density(), o.density()) < 1e-4
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert abs(dg["sw_count"] - do["sw_count"]) <= 1e-3
+    assert abs(dg["sw_mass"] - do["sw_mass"]) <= 1e-3
+
+
+def test_mass_conserved_on_gpu_closed_box():
+    nx, ny = 64, 40
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    solid[15:25, 40:50] = 1
+    rho1, rho2 = media.droplet_densities(nx, ny, 20, 20, 8, solid=solid)
+    g = mclbm.Lattice(solid, media.uniform_xi(solid, -0.4), prec="fp64",
+                      nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62))
+    g.init(rho1, rho2)
+    d0 = g.diagnostics()
+    g.step(3000)
+    d1 = g.diagnostics()
+    assert abs(d1["mass1"] / d0["mass1"] - 1) < 1e-12
+    assert abs(d1["mass2"] / d0["mass2"] - 1) < 1e-12
+
+
+def test_all_solid_lattice_has_no_fluid():
+    solid = np.ones((6, 9), np.uint8)
+    g = mclbm.Lattice(solid, prec="fp32")
+    g.init(np.zeros((6, 9)), np.zeros((6, 9)))
+    g.step(3)
+    d = g.diagnostics()
+    assert d["n_fluid"] == 0 and d["mass1"] == 0
+    assert np.isnan(d["sw_count"]) and np.isnan(d["p_in"])
+
+
+def test_errors_are_reported():
+    solid = np.zeros((8, 8), np.uint8)    # fluid on the edge rows, not periodic
+    g = mclbm.Lattice(solid, prec="fp32")
+    with pytest.raises(mclbm.MclbmError) as e:
+        g.step(1)                           # not initialised
+    assert e.value.code == mclbm.MCLBM_ERR_STATE
+    g.init(np.ones((8, 8)), np.ones((8, 8)))
+    with pytest.raises(mclbm.MclbmError) as e:
+        g.step(1)                           # rows 0 and ny-1 must be walls
+    assert e.value.code == mclbm.MCLBM_ERR_ARG
+    xi = np.arange(64, dtype=np.float32).reshape(8, 8) / 1000
+    many = np.ones((8, 8), np.uint8)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.Lattice(np.ones((20, 20), np.uint8), np.arange(400, dtype=np.float32).reshape(20, 20))
+    mclbm.Lattice(many, xi).close()     # 64 distinct values are fine
+
+
+def test_divergence_flag():
+    nx, ny = 16, 16
+    solid = np.zeros((ny, nx), np.uint8)
+    g = mclbm.Lattice(solid, prec="fp32", periodic_y=True, nu1=0.1, nu2=0.1)
+    rho = np.ones((ny, nx))
+    rho[5, 5] = -3.0                       # a negative density is caught
+    g.init(rho, np.ones((ny, nx)))
+    mclbm.mclbm_set_flag(g.h, mclbm.MCLBM_FLAG_DIAG_EVERY, 1)
+    g.step(1)
+    with pytest.raises(mclbm.MclbmError) as e:
+        g.sync()
+    assert e.value.code == mclbm.MCLBM_ERR_DIVERGED
+    g.sync()                               # the flag is cleared once reported
