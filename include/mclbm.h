@@ -46,9 +46,11 @@ extern "C" {
 #define MCLBM_ERR_STATE (-5)    /* call not valid in the lattice's state */
 #define MCLBM_ERR_NOMEM (-6)    /* device or host allocation failed */
 
-/* Storage precision of the populations.  FP64 and FP32 store f_i; the
- * deviation variants store f_i - w_i (reference density 1) in FP32, FP16 or
- * BF16 and compute in FP32.  Global reductions are FP64 in every variant. */
+/* Storage precision of the populations.  FP64 and FP32 store f_i.  The
+ * deviation variants store, per node and component, a reference density
+ * rho_hat (the node's density rounded to the storage type) and the
+ * deviations f_i - w_i rho_hat from that rest equilibrium, in FP32, FP16 or
+ * BF16, and compute in FP32.  Global reductions are FP64 in every variant. */
 typedef enum {
     MCLBM_FP64 = 0,
     MCLBM_FP32 = 1,
@@ -69,7 +71,12 @@ typedef enum {
     /* k > 0: every k steps mclbm_step runs the divergence check (non-finite
      * or negative density); a hit is reported by the next synchronising
      * call as MCLBM_ERR_DIVERGED.  0 (default): off. */
-    MCLBM_FLAG_DIAG_EVERY = 2
+    MCLBM_FLAG_DIAG_EVERY = 2,
+    /* Step kernel: 0 (default) the row-sweeping strip kernel, which stages
+     * rows in shared memory with bulk copies; 1 the 2-D tile kernel, which
+     * pulls straight from global memory; 2 the strip kernel.  Both compute
+     * the same update. */
+    MCLBM_FLAG_KERNEL = 3
 } mclbm_flag;
 
 typedef struct mclbm_lattice mclbm_lattice;
@@ -149,8 +156,10 @@ int mclbm_get_populations(mclbm_lattice *lat, double *f);
  */
 int mclbm_step(mclbm_lattice *lat, int64_t nsteps);
 
-/* Wait for the lattice's stream; returns MCLBM_ERR_DIVERGED if the
- * divergence check (MCLBM_FLAG_DIAG_EVERY) fired since the last call. */
+/* Wait for the lattice's stream; returns MCLBM_ERR_TIMEOUT if a bounded
+ * wait inside the step kernel ran out (the state is then not valid), or
+ * MCLBM_ERR_DIVERGED if the divergence check (MCLBM_FLAG_DIAG_EVERY) fired
+ * since the last call. */
 int mclbm_synchronize(mclbm_lattice *lat);
 
 /* Component density rho^sigma (Eq. 3) of the current state, comp = 1 or 2,

@@ -104,6 +104,7 @@ void release(Lattice *L) {
     cudaFree(L->diag_partial);
     cudaFree(L->diag_out);
     cudaFree(L->bad_flag);
+    cudaFree(L->err);
     if (L->host_diag) cudaFreeHost(L->host_diag);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     L->own_stream = false;
@@ -129,6 +130,16 @@ int run_diagnostics(Lattice &L, double out[8]) {
     e = cudaStreamSynchronize(L.stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     std::memcpy(out, L.host_diag, 8 * sizeof(double));
+    return MCLBM_OK;
+}
+
+// Rebuild the ghost columns if the x boundary mode changed since they were
+// last built.
+int refresh_ghosts(Lattice &L) {
+    if (L.geo_ghost_open == L.p.open_x) return MCLBM_OK;
+    cudaError_t e = launch_geo_ghosts(L);
+    if (e != cudaSuccess) return cuda_fail(e, "ghost columns");
+    L.geo_ghost_open = L.p.open_x;
     return MCLBM_OK;
 }
 
@@ -184,13 +195,27 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
     }
     L->nx = nx;
     L->ny = ny;
-    L->pitch = (nx + 31) / 32 * 32;
     L->prec = prec;
     L->store_bytes = store_bytes_of(prec);
     L->real_bytes = prec == MCLBM_FP64 ? 8 : 4;
+    L->planes = (prec == MCLBM_FP64 || prec == MCLBM_FP32) ? 18 : 20;
+    L->hx = L->store_bytes >= 4 ? 4 : 16 / (int)L->store_bytes;
+    {
+        // rows: every strip's staged copy in bounds, 128-byte aligned, an odd
+        // number of 128-byte lines; planes: an odd number of lines as well
+        const long long sb = (long long)L->store_bytes;
+        const long long cols = (long long)(nx + SWEEP_W - 1) / SWEEP_W * SWEEP_W + 2 * L->hx;
+        long long row_bytes = (cols * sb + 127) / 128 * 128;
+        if ((row_bytes / 128) % 2 == 0) row_bytes += 128;
+        L->pitch = (int)(row_bytes / sb);
+        long long plane_bytes = row_bytes * ny;
+        if ((plane_bytes / 128) % 2 == 0) plane_bytes += 128;
+        L->plane = plane_bytes / sb;
+        L->gpitch = (int)(((long long)(nx + SWEEP_W - 1) / SWEEP_W * SWEEP_W + 2 * GEO_HX + 15) / 16 * 16);
+    }
 
     // geometry codes and the wettability table (chi^1 = 1 + xi, chi^2 = 1 - xi)
-    std::vector<uint8_t> geo((size_t)L->pitch * ny, GEO_OUTSIDE);
+    std::vector<uint8_t> geo((size_t)L->gpitch * ny, GEO_OUTSIDE);
     std::vector<double> chi(512, 1.0);
     std::map<uint32_t, int> codes;
     bool rows_solid = true;
@@ -223,7 +248,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
             } else if (y == 0 || y == ny - 1) {
                 rows_solid = false;
             }
-            geo[(size_t)y * L->pitch + x] = c;
+            geo[(size_t)y * L->gpitch + GEO_HX + x] = c;
         }
     L->boundary_rows_solid = rows_solid;
 
@@ -237,13 +262,15 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         }
         L->own_stream = true;
     }
-    const size_t plane = (size_t)L->pitch * ny;
+    const size_t geo_bytes = (size_t)L->gpitch * ny;
+    const size_t pop_bytes = (size_t)L->planes * (size_t)L->plane * L->store_bytes;
     int rc = MCLBM_OK;
     L->diag_blocks = diag_blocks_for(*L);
-    if ((rc = dev_alloc(*L, (void **)&L->geo, plane)) ||
+    if ((rc = dev_alloc(*L, (void **)&L->geo, geo_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->chi, 512 * sizeof(double))) ||
-        (rc = dev_alloc(*L, &L->f[0], 18 * plane * L->store_bytes)) ||
-        (rc = dev_alloc(*L, &L->f[1], 18 * plane * L->store_bytes)) ||
+        (rc = dev_alloc(*L, &L->f[0], pop_bytes)) ||
+        (rc = dev_alloc(*L, &L->f[1], pop_bytes)) ||
+        (rc = dev_alloc(*L, (void **)&L->err, sizeof(int))) ||
         (rc = dev_alloc(*L, &L->d5, 3 * (size_t)ny * L->real_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->diag_partial, (size_t)L->diag_blocks * 9 * sizeof(double))) ||
         (rc = dev_alloc(*L, (void **)&L->diag_out, 8 * sizeof(double))) ||
@@ -258,11 +285,12 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         delete L;
         return cuda_fail(e, "cudaMallocHost");
     }
-    if ((e = cudaMemcpyAsync(L->geo, geo.data(), plane, cudaMemcpyHostToDevice, L->stream)) ||
+    if ((e = cudaMemcpyAsync(L->geo, geo.data(), geo_bytes, cudaMemcpyHostToDevice, L->stream)) ||
         (e = cudaMemcpyAsync(L->chi, chi.data(), 512 * sizeof(double), cudaMemcpyHostToDevice,
                              L->stream)) ||
-        (e = cudaMemsetAsync(L->f[0], 0, 18 * plane * L->store_bytes, L->stream)) ||
-        (e = cudaMemsetAsync(L->f[1], 0, 18 * plane * L->store_bytes, L->stream)) ||
+        (e = cudaMemsetAsync(L->f[0], 0, pop_bytes, L->stream)) ||
+        (e = cudaMemsetAsync(L->f[1], 0, pop_bytes, L->stream)) ||
+        (e = cudaMemsetAsync(L->err, 0, sizeof(int), L->stream)) ||
         (e = cudaMemsetAsync(L->d5, 0, 3 * (size_t)ny * L->real_bytes, L->stream)) ||
         (e = cudaMemsetAsync(L->bad_flag, 0, sizeof(unsigned long long), L->stream)) ||
         (e = cudaStreamSynchronize(L->stream))) {
@@ -288,6 +316,10 @@ int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
     switch (flag) {
         case MCLBM_FLAG_PERIODIC_Y: lat->p.periodic_y = value ? 1 : 0; return MCLBM_OK;
         case MCLBM_FLAG_VEL_SHIFT: lat->p.vel_shift = value ? 1 : 0; return MCLBM_OK;
+        case MCLBM_FLAG_KERNEL:
+            if (value < 0 || value > 2) return fail(MCLBM_ERR_ARG, "kernel must be 0, 1 or 2");
+            lat->kernel = value;
+            return MCLBM_OK;
         case MCLBM_FLAG_DIAG_EVERY:
             if (value < 0) return fail(MCLBM_ERR_ARG, "diag_every must be >= 0");
             lat->diag_every = value;
@@ -377,6 +409,8 @@ int mclbm_init_densities(mclbm_lattice *lat, const double *rho1, const double *r
     DeviceView v1, v2;
     if (int rc = view_in(*lat, rho1, bytes, v1)) return rc;
     if (int rc = view_in(*lat, rho2, bytes, v2)) return rc;
+    lat->geo_ghost_open = -1;
+    if (int rc = refresh_ghosts(*lat)) return rc;
     cudaError_t e = launch_init_equilibrium(*lat, static_cast<const double *>(v1.ptr),
                                             static_cast<const double *>(v2.ptr));
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
@@ -393,6 +427,8 @@ int mclbm_set_populations(mclbm_lattice *lat, const double *f) {
     if (int rc = make_current(*lat)) return rc;
     DeviceView v;
     if (int rc = view_in(*lat, f, (size_t)18 * lat->nx * lat->ny * sizeof(double), v)) return rc;
+    lat->geo_ghost_open = -1;
+    if (int rc = refresh_ghosts(*lat)) return rc;
     cudaError_t e = launch_set_populations(*lat, static_cast<const double *>(v.ptr));
     if (e != cudaSuccess) return cuda_fail(e, "import kernel");
     e = cudaStreamSynchronize(lat->stream);
@@ -418,12 +454,14 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
     if (nsteps < 0) return fail(MCLBM_ERR_ARG, "nsteps < 0");
     if (int rc = check_ready(*lat)) return rc;
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = refresh_ghosts(*lat)) return rc;
+    const bool sweep = lat->kernel == 2 || (lat->kernel == 0 && sweep_supported(*lat));
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = launch_step(*lat, 0);
+        cudaError_t e = sweep ? launch_step_sweep(*lat) : launch_step_tile(*lat, 0);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         ++lat->steps;
         if (lat->diag_every > 0 && lat->steps % lat->diag_every == 0) {
-            e = launch_bad_check(*lat);
+            e = launch_diagnostics(*lat);
             if (e != cudaSuccess) return cuda_fail(e, "divergence check");
         }
     }
@@ -435,6 +473,13 @@ int mclbm_synchronize(mclbm_lattice *lat) {
     if (int rc = make_current(*lat)) return rc;
     cudaError_t e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int err = 0;
+    e = cudaMemcpy(&err, lat->err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error word)");
+    if (err) {
+        cudaMemset(lat->err, 0, sizeof(err));
+        return fail(err, "a bounded wait in the step kernel ran out; the state is not valid");
+    }
     unsigned long long bad = 0;
     e = cudaMemcpy(&bad, lat->bad_flag, sizeof(bad), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(flag)");

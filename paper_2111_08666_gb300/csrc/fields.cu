@@ -13,55 +13,52 @@ inline int blocks_for(long long n, int per = BLK) { return (int)((n + per - 1) /
 // f_i = f_i^eq(rho^sigma, u = 0) = w_i rho^sigma (Eq. 2 at rest); records
 // component 1's outlet f_{3,6,7} for Eq. 26.
 template <class P>
-__global__ void init_equilibrium_kernel(Geometry g, const double *rho1, const double *rho2,
-                                        typename P::store_t *f, typename P::real_t *d5) {
+__global__ void init_equilibrium_kernel(Geometry g, Params p, const double *rho1,
+                                        const double *rho2, typename P::store_t *f,
+                                        typename P::real_t *d5) {
     using R = typename P::real_t;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
-    const bool fluid = g.geo[site] == GEO_FLUID;
-    const R r[2] = {fluid ? R(rho1[k]) : R(0), fluid ? R(rho2[k]) : R(0)};
+    const bool fluid = g.geo[(long long)y * g.gpitch + GEO_HX + x] == GEO_FLUID;
+    const R r1 = fluid ? R(rho1[k]) : R(0), r2 = fluid ? R(rho2[k]) : R(0);
+    R fs[2][9];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            if (fluid)
-                store_f<P>(f, g.plane, c, i, site, wgt<R>(i) * r[c]);
-            else
-                f[(long long)(c * 9 + i) * g.plane + site] = from_real<typename P::store_t>(R(0));
-        }
+    for (int i = 0; i < 9; ++i) {
+        fs[0][i] = wgt<R>(i) * r1;
+        fs[1][i] = wgt<R>(i) * r2;
+    }
+    pop_store_node<P>(g, p, f, x, y, fs, r1, r2);
     if (x == g.nx - 1) {
-        d5[y] = wgt<R>(3) * r[0];
-        d5[g.ny + y] = wgt<R>(6) * r[0];
-        d5[2 * g.ny + y] = wgt<R>(7) * r[0];
+        d5[y] = fs[0][3];
+        d5[g.ny + y] = fs[0][6];
+        d5[2 * g.ny + y] = fs[0][7];
     }
 }
 
 template <class P>
-__global__ void import_kernel(Geometry g, const double *src, typename P::store_t *f,
+__global__ void import_kernel(Geometry g, Params p, const double *src, typename P::store_t *f,
                               typename P::real_t *d5) {
     using R = typename P::real_t;
     const long long n = (long long)g.nx * g.ny;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
-    const bool fluid = g.geo[site] == GEO_FLUID;
+    const bool fluid = g.geo[(long long)y * g.gpitch + GEO_HX + x] == GEO_FLUID;
+    R fs[2][9];
+    R r[2] = {R(0), R(0)};
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double v = fluid ? src[(c * 9 + i) * n + k] : 0.0;
-            if (fluid)
-                store_f<P>(f, g.plane, c, i, site, R(v));
-            else
-                f[(long long)(c * 9 + i) * g.plane + site] = from_real<typename P::store_t>(R(0));
+            fs[c][i] = fluid ? R(src[(c * 9 + i) * n + k]) : R(0);
+            r[c] += fs[c][i];
         }
+    pop_store_node<P>(g, p, f, x, y, fs, r[0], r[1]);
     if (x == g.nx - 1) {
-        d5[y] = fluid ? R(src[3 * n + k]) : R(0);
-        d5[g.ny + y] = fluid ? R(src[6 * n + k]) : R(0);
-        d5[2 * g.ny + y] = fluid ? R(src[7 * n + k]) : R(0);
+        d5[y] = fs[0][3];
+        d5[g.ny + y] = fs[0][6];
+        d5[2 * g.ny + y] = fs[0][7];
     }
 }
 
@@ -71,13 +68,42 @@ __global__ void export_kernel(Geometry g, const typename P::store_t *f, double *
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
-    const bool fluid = g.geo[site] == GEO_FLUID;
+    const long long site = site_of(g, x, y);
+    const bool fluid = g.geo[(long long)y * g.gpitch + GEO_HX + x] == GEO_FLUID;
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            dst[(c * 9 + i) * n + k] = fluid ? (double)load_f<P>(f, g.plane, c, i, site) : 0.0;
+            dst[(c * 9 + i) * n + k] = fluid ? (double)pop_load<P>(f, g.plane, c, i, site) : 0.0;
+}
+
+// Geometry ghost columns for the current x boundary mode: with periodic x
+// the hx columns on each side repeat the opposite edge (matching the
+// population ghosts); everything else outside 0..nx-1 is outside.
+__global__ void geo_ghost_kernel(Geometry g, int open_x) {
+    const int y = blockIdx.x;
+    uint8_t *row = const_cast<uint8_t *>(g.geo) + (long long)y * g.gpitch;
+    for (int c = threadIdx.x; c < g.gpitch; c += blockDim.x) {
+        const int x = c - GEO_HX;
+        if (x >= 0 && x < g.nx) continue;
+        uint8_t code = GEO_OUTSIDE;
+        if (!open_x && x >= -g.hx && x < g.nx + g.hx) code = row[GEO_HX + pmod(x, g.nx)];
+        row[c] = code;
+    }
+}
+
+// Population ghost columns for periodic x: copy the hx edge columns of
+// every plane of the current state to the opposite side.
+template <class P>
+__global__ void pop_ghost_kernel(Geometry g, typename P::store_t *f) {
+    const int y = blockIdx.x;
+    const int ng = 2 * g.hx;
+    for (int k = threadIdx.x; k < P::planes * ng; k += blockDim.x) {
+        const int pl = k / ng, j = k % ng;
+        const int gx = j < g.hx ? j - g.hx : g.nx + (j - g.hx);
+        const long long base = (long long)pl * g.plane;
+        f[base + site_of(g, gx, y)] = f[base + site_of(g, pmod(gx, g.nx), y)];
+    }
 }
 
 template <class P>
@@ -88,9 +114,13 @@ __device__ __forceinline__ void node_rho(const Geometry &g, const typename P::st
     r2 = 0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        r1 += load_f<P>(f, g.plane, 0, i, site);
-        r2 += load_f<P>(f, g.plane, 1, i, site);
+        r1 += pop_load<P>(f, g.plane, 0, i, site);
+        r2 += pop_load<P>(f, g.plane, 1, i, site);
     }
+}
+
+__device__ __forceinline__ bool is_fluid(const Geometry &g, int x, int y) {
+    return g.geo[(long long)y * g.gpitch + GEO_HX + x] == GEO_FLUID;
 }
 
 // ---------------------------------------------------------------------------
@@ -118,7 +148,7 @@ __device__ __forceinline__ bool pressure_site(const Geometry &g, const Params &p
             if (!p.periodic_y) return false;
             yy = (yy + g.ny) % g.ny;
         }
-        if (g.geo[(long long)yy * g.pitch + x] != GEO_FLUID) return false;
+        if (!is_fluid(g, x, yy)) return false;
     }
     return true;
 }
@@ -135,8 +165,8 @@ __global__ void __launch_bounds__(BLK) diag_partial_kernel(Geometry g, Params p,
     for (long long k = (long long)blockIdx.x * BLK + threadIdx.x; k < n;
          k += (long long)gridDim.x * BLK) {
         const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-        const long long site = (long long)y * g.pitch + x;
-        if (g.geo[site] != GEO_FLUID) continue;
+        const long long site = site_of(g, x, y);
+        if (!is_fluid(g, x, y)) continue;
         R r1, r2;
         node_rho<P>(g, f, site, r1, r2);
         const double d1 = (double)r1, d2 = (double)r2;
@@ -199,11 +229,11 @@ __global__ void density_kernel(Geometry g, const typename P::store_t *f, int com
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
+    const long long site = site_of(g, x, y);
     R r = 0;
-    if (g.geo[site] == GEO_FLUID)
+    if (is_fluid(g, x, y))
 #pragma unroll
-        for (int i = 0; i < 9; ++i) r += load_f<P>(f, g.plane, comp, i, site);
+        for (int i = 0; i < 9; ++i) r += pop_load<P>(f, g.plane, comp, i, site);
     out[k] = (double)r;
 }
 
@@ -213,9 +243,9 @@ __global__ void pressure_kernel(Geometry g, Params p, const typename P::store_t 
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
+    const long long site = site_of(g, x, y);
     double v = 0.0;
-    if (g.geo[site] == GEO_FLUID) {
+    if (is_fluid(g, x, y)) {
         R r1, r2;
         node_rho<P>(g, f, site, r1, r2);
         v = ((double)r1 + (double)r2) / 3.0 + p.g_coh / 3.0 * (double)r1 * (double)r2;
@@ -229,9 +259,9 @@ __global__ void phase_kernel(Geometry g, const typename P::store_t *f, float *ou
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
+    const long long site = site_of(g, x, y);
     float v = 0.0f;
-    if (g.geo[site] == GEO_FLUID) {
+    if (is_fluid(g, x, y)) {
         R r1, r2;
         node_rho<P>(g, f, site, r1, r2);
         v = (float)((r1 - r2) / (r1 + r2));
@@ -253,11 +283,11 @@ __global__ void vel_rho_kernel(Geometry g, const typename P::store_t *f,
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
     R r1 = 0, r2 = 0;
-    if (g.geo[site] == GEO_FLUID) node_rho<P>(g, f, site, r1, r2);
-    rho[site] = r1;
-    rho[g.plane + site] = r2;
+    if (is_fluid(g, x, y)) node_rho<P>(g, f, site_of(g, x, y), r1, r2);
+    const long long n = (long long)g.nx * g.ny;
+    rho[k] = r1;
+    rho[n + k] = r2;
 }
 
 template <class R>
@@ -265,11 +295,11 @@ __global__ void vel_psi_kernel(Geometry g, Params p, const R *rho, R *psi) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
-    const uint8_t code = g.geo[site];
+    const long long n = (long long)g.nx * g.ny;
+    const uint8_t code = g.geo[(long long)y * g.gpitch + GEO_HX + x];
     if (code == GEO_FLUID) {
-        psi[site] = rho[site];
-        psi[g.plane + site] = rho[g.plane + site];
+        psi[k] = rho[k];
+        psi[n + k] = rho[n + k];
         return;
     }
     R n1 = 0, n2 = 0, den = 0;
@@ -279,10 +309,10 @@ __global__ void vel_psi_kernel(Geometry g, Params p, const R *rho, R *psi) {
         if (geo_at(g, p, nx_, ny_) != GEO_FLUID) continue;
         nx_ = pmod(nx_, g.nx);
         ny_ = pmod(ny_, g.ny);
-        const long long ns = (long long)ny_ * g.pitch + nx_;
+        const long long ns = (long long)ny_ * g.nx + nx_;
         const R w = wgt<R>(i);
         n1 += w * rho[ns];
-        n2 += w * rho[g.plane + ns];
+        n2 += w * rho[n + ns];
         den += w;
     }
     R s1 = 0, s2 = 0;
@@ -290,8 +320,8 @@ __global__ void vel_psi_kernel(Geometry g, Params p, const R *rho, R *psi) {
         s1 = R(g.chi[2 * code]) * n1 / den;
         s2 = R(g.chi[2 * code + 1]) * n2 / den;
     }
-    psi[site] = s1;
-    psi[g.plane + site] = s2;
+    psi[k] = s1;
+    psi[n + k] = s2;
 }
 
 template <class P>
@@ -302,13 +332,14 @@ __global__ void vel_final_kernel(Geometry g, Params p, const typename P::store_t
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long long)g.nx * g.ny) return;
     const int x = (int)(k % g.nx), y = (int)(k / g.nx);
-    const long long site = (long long)y * g.pitch + x;
-    if (g.geo[site] != GEO_FLUID) {
+    const long long site = site_of(g, x, y);
+    const long long n = (long long)g.nx * g.ny;
+    if (!is_fluid(g, x, y)) {
         ux_out[k] = 0.0;
         uy_out[k] = 0.0;
         return;
     }
-    const R r1 = rho[site], r2 = rho[g.plane + site];
+    const R r1 = rho[k], r2 = rho[n + k];
     const bool mirror_in = p.open_x && x == 0;
     const bool mirror_out = p.open_x && x == g.nx - 1;
     R fx1, fy1, fx2, fy2;
@@ -323,16 +354,16 @@ __global__ void vel_final_kernel(Geometry g, Params p, const typename P::store_t
                       s1 = s2 = R(0);
                       if (code != GEO_OUTSIDE) {
                           const long long ns =
-                              (long long)pmod(y + dy, g.ny) * g.pitch + pmod(x + dx, g.nx);
+                              (long long)pmod(y + dy, g.ny) * g.nx + pmod(x + dx, g.nx);
                           s1 = psi[ns];
-                          s2 = psi[g.plane + ns];
+                          s2 = psi[n + ns];
                       }
                   },
                   fx1, fy1, fx2, fy2);
     R jx = 0, jy = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const R fi = load_f<P>(f, g.plane, 0, i, site) + load_f<P>(f, g.plane, 1, i, site);
+        const R fi = pop_load<P>(f, g.plane, 0, i, site) + pop_load<P>(f, g.plane, 1, i, site);
         jx += R(ex(i)) * fi;
         jy += R(ey(i)) * fi;
     }
@@ -347,9 +378,7 @@ __global__ void vel_final_kernel(Geometry g, Params p, const typename P::store_t
     uy_out[k] = (double)((jy - c * Fy) / rho_t);
 }
 
-Geometry geometry_of(const Lattice &L) {
-    return Geometry{L.nx, L.ny, L.pitch, (long long)L.pitch * L.ny, L.geo, L.chi};
-}
+Geometry geometry_of(const Lattice &L) { return L.geometry(); }
 
 template <class F>
 cudaError_t dispatch(const Lattice &L, F &&fn) {
@@ -375,7 +404,7 @@ cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double
     return dispatch(L, [&](auto tag) {
         using P = decltype(tag);
         init_equilibrium_kernel<P><<<blocks_for((long long)L.nx * L.ny), BLK, 0, L.stream>>>(
-            g, rho1, rho2, static_cast<typename P::store_t *>(L.f[L.cur]),
+            g, L.p, rho1, rho2, static_cast<typename P::store_t *>(L.f[L.cur]),
             static_cast<typename P::real_t *>(L.d5));
         count_launch();
         return cudaGetLastError();
@@ -387,7 +416,7 @@ cudaError_t launch_set_populations(Lattice &L, const double *src) {
     return dispatch(L, [&](auto tag) {
         using P = decltype(tag);
         import_kernel<P><<<blocks_for((long long)L.nx * L.ny), BLK, 0, L.stream>>>(
-            g, src, static_cast<typename P::store_t *>(L.f[L.cur]),
+            g, L.p, src, static_cast<typename P::store_t *>(L.f[L.cur]),
             static_cast<typename P::real_t *>(L.d5));
         count_launch();
         return cudaGetLastError();
@@ -418,7 +447,20 @@ cudaError_t launch_diagnostics(Lattice &L) {
     });
 }
 
-cudaError_t launch_bad_check(Lattice &L) { return launch_diagnostics(L); }
+cudaError_t launch_geo_ghosts(Lattice &L) {
+    geo_ghost_kernel<<<L.ny, 128, 0, L.stream>>>(geometry_of(L), L.p.open_x);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.p.open_x) return e;
+    const Geometry g = geometry_of(L);
+    return dispatch(L, [&](auto tag) {
+        using P = decltype(tag);
+        pop_ghost_kernel<P><<<L.ny, 128, 0, L.stream>>>(
+            g, static_cast<typename P::store_t *>(L.f[L.cur]));
+        count_launch();
+        return cudaGetLastError();
+    });
+}
 
 cudaError_t launch_density(Lattice &L, int comp, double *out) {
     const Geometry g = geometry_of(L);
@@ -454,7 +496,7 @@ cudaError_t launch_phase(Lattice &L, float *out) {
 }
 
 size_t velocity_scratch_bytes(const Lattice &L) {
-    return 4 * (size_t)L.pitch * L.ny * L.real_bytes;
+    return 4 * (size_t)L.nx * L.ny * L.real_bytes;
 }
 
 cudaError_t launch_velocity(Lattice &L, double *ux, double *uy, void *scratch) {
@@ -463,7 +505,7 @@ cudaError_t launch_velocity(Lattice &L, double *ux, double *uy, void *scratch) {
         using P = decltype(tag);
         using R = typename P::real_t;
         R *rho = static_cast<R *>(scratch);
-        R *psi = rho + 2 * g.plane;
+        R *psi = rho + 2 * (long long)g.nx * g.ny;
         const int nb = blocks_for((long long)L.nx * L.ny);
         const auto *f = static_cast<const typename P::store_t *>(L.f[L.cur]);
         vel_rho_kernel<P><<<nb, BLK, 0, L.stream>>>(g, f, rho);

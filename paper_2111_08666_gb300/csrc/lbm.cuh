@@ -1,5 +1,5 @@
 // Internal declarations of the CUDA library: D2Q9 constants, storage
-// precisions, the lattice object and the kernel launchers.
+// precisions, memory layout, the lattice object and the kernel launchers.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -39,16 +39,25 @@ static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
 constexpr uint8_t GEO_FLUID = 0;
 constexpr uint8_t GEO_OUTSIDE = 255;
 constexpr int MAX_XI_VALUES = 254;
+// Geometry rows carry 16 ghost columns on each side; column x sits at byte
+// GEO_HX + x of its row.
+constexpr int GEO_HX = 16;
 
 // ---------------------------------------------------------------------------
-// Storage precisions.  Populations are stored as S and computed in R; the
-// deviation variants store f_i - w_i (reference density 1).
+// Storage precisions.  Populations are stored as S and computed in R.  With
+// REF the store holds, per node and component, a reference density rho_hat
+// (the node's own density rounded to S) and the deviations
+// d_i = f_i - w_i rho_hat from that rest equilibrium; f_i = w_i rho_hat + d_i.
 // ---------------------------------------------------------------------------
-template <class S, class R, bool DEV>
+template <class S, class R, bool REF>
 struct Prec {
     using store_t = S;
     using real_t = R;
-    static constexpr bool dev = DEV;
+    static constexpr bool ref = REF;
+    static constexpr int planes = REF ? 20 : 18;
+    // ghost columns per side of a population row: at least 3 (the deepest
+    // stencil reach) and a whole 16-byte chunk
+    static constexpr int hx = sizeof(S) >= 4 ? 4 : 16 / (int)sizeof(S);
 };
 using P64 = Prec<double, double, false>;
 using P32 = Prec<float, float, false>;
@@ -81,27 +90,43 @@ struct Params {
     int vel_shift = 1;   // u carries F/2
 };
 
-// Arguments of the fused step kernel and the field kernels.
+// Memory layout shared by every kernel.  Population (c, i, y, x) lives at
+// f[(c*9 + i) * plane + y * pitch + hx + x]; columns -hx..-1 and nx..nx+hx-1
+// are ghost copies of the opposite edge when x is periodic.  Reference
+// densities (REF precisions) are planes 18 and 19.  pitch and plane are odd
+// multiples of 128 bytes so that the direction planes and rows do not alias
+// in the caches.
 struct Geometry {
-    int nx, ny, pitch;         // pitch: row stride in elements
-    long long plane;           // pitch * ny: elements per direction plane
-    const uint8_t *geo;        // [ny][pitch] geometry code
+    int nx, ny;
+    int pitch;                 // population row stride, elements
+    int hx;                    // column of x = 0 within a population row
+    long long plane;           // population plane stride, elements
+    int gpitch;                // geometry row stride, bytes
+    const uint8_t *geo;        // [ny][gpitch], column x at GEO_HX + x
     const double *chi;         // [256][2] (1 + xi, 1 - xi) by code, in FP64
 };
 
 struct StepArgs {
     Geometry g;
     Params p;
-    const void *fin;           // [2][9][ny][pitch] post-collision, step t
-    void *fout;                // post-collision, step t+1
+    const void *fin;           // post-collision state of step t
+    void *fout;                // post-collision state of step t+1
     const void *d5;            // [3][ny] component-1 outlet f_{3,6,7} (real type)
+    int *err;                  // device error word (bounded waits)
+    int rows_per_cta;          // strip kernel: rows of one CTA
 };
+
+// strip width (columns per CTA) of the row-sweeping kernel
+constexpr int SWEEP_W = 128;
 
 // ---------------------------------------------------------------------------
 // The lattice object behind the opaque handle of the C ABI.
 // ---------------------------------------------------------------------------
 struct Lattice {
-    int nx = 0, ny = 0, pitch = 0;
+    int nx = 0, ny = 0;
+    int pitch = 0, hx = 0, gpitch = 0;
+    long long plane = 0;
+    int planes = 18;
     mclbm_precision prec = MCLBM_FP32;
     size_t store_bytes = 4;    // bytes per stored population
     size_t real_bytes = 4;     // bytes of the math type
@@ -109,22 +134,27 @@ struct Lattice {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    uint8_t *geo = nullptr;    // [ny][pitch]
+    uint8_t *geo = nullptr;    // [ny][gpitch]
+    int geo_ghost_open = -1;   // x mode the geometry ghosts were built for
     double *chi = nullptr;     // [256][2]
     void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
     int cur = 0;               // index of the buffer holding the state
     void *d5 = nullptr;        // [3][ny] real type
+    int *err = nullptr;        // device error word
     double *diag_partial = nullptr;   // scratch of the diagnostics reduction
     int diag_blocks = 0;
     double *diag_out = nullptr;       // [8] device
     double *host_diag = nullptr;      // [8] pinned
     unsigned long long *bad_flag = nullptr;  // device: divergence count
     int64_t diag_every = 0;
+    int64_t kernel = 0;        // 0 auto, 1 tile kernel, 2 strip kernel
     int64_t steps = 0;
     size_t device_bytes = 0;
     bool boundary_rows_solid = false;
-    bool boundary_cols_fluid_ok = true;
     bool initialised = false;
+    Geometry geometry() const {
+        return Geometry{nx, ny, pitch, hx, plane, gpitch, geo, chi};
+    }
 };
 
 // status helpers (capi.cu)
@@ -132,13 +162,15 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n = 1);
 
-// launchers (step.cu, fields.cu); return cudaError_t of the launch
-cudaError_t launch_step(Lattice &L, int tile_cfg);
+// launchers (step.cu, sweep.cu, fields.cu); return cudaError_t of the launch
+cudaError_t launch_step_tile(Lattice &L, int tile_cfg);
+cudaError_t launch_step_sweep(Lattice &L);
+bool sweep_supported(const Lattice &L);
+cudaError_t launch_geo_ghosts(Lattice &L);
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
 cudaError_t launch_set_populations(Lattice &L, const double *f);
 cudaError_t launch_get_populations(Lattice &L, double *f);
 cudaError_t launch_diagnostics(Lattice &L);
-cudaError_t launch_bad_check(Lattice &L);
 cudaError_t launch_density(Lattice &L, int comp, double *out);
 cudaError_t launch_pressure(Lattice &L, double *out);
 cudaError_t launch_phase(Lattice &L, float *out);

@@ -1,4 +1,7 @@
-// Fused stream-collide-force kernel: one launch per time step.
+// Fused stream-collide-force kernel, 2-D tile variant: one launch per time
+// step.  The row-sweeping strip kernel (sweep.cu) is the default; this one
+// pulls straight from global memory and serves as the second, independent
+// formulation that the strip kernel is checked against.
 //
 // One CTA owns a TX x TY tile.  The force at a node needs the pseudopotential
 // of its 8 neighbours (Eq. 13), and a solid neighbour's virtual density
@@ -147,13 +150,7 @@ __global__ void __launch_bounds__(TX *TY) fused_step_kernel(const StepArgs a) {
     node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
     collide_component<R>(f[0], rho1, ux, uy, fx1, fy1, omega);
     collide_component<R>(f[1], rho2, ux, uy, fx2, fy2, omega);
-    S *fout = static_cast<S *>(a.fout);
-    const long long site = (long long)y * a.g.pitch + x;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        store_f<P>(fout, a.g.plane, 0, i, site, f[0][i]);
-        store_f<P>(fout, a.g.plane, 1, i, site, f[1][i]);
-    }
+    pop_store_node<P>(a.g, a.p, static_cast<S *>(a.fout), x, y, f, rho1, rho2);
 }
 
 template <class P, int TX, int TY>
@@ -174,13 +171,15 @@ static cudaError_t launch_prec(Lattice &L, const StepArgs &a, int tile_cfg) {
     }
 }
 
-cudaError_t launch_step(Lattice &L, int tile_cfg) {
+cudaError_t launch_step_tile(Lattice &L, int tile_cfg) {
     StepArgs a;
-    a.g = Geometry{L.nx, L.ny, L.pitch, (long long)L.pitch * L.ny, L.geo, L.chi};
+    a.g = L.geometry();
     a.p = L.p;
     a.fin = L.f[L.cur];
     a.fout = L.f[1 - L.cur];
     a.d5 = L.d5;
+    a.err = L.err;
+    a.rows_per_cta = 0;
     cudaError_t e;
     switch (L.prec) {
         case MCLBM_FP64: e = launch_prec<P64>(L, a, tile_cfg); break;

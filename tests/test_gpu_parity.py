@@ -21,11 +21,19 @@ def nu_of_tau(t):
     return (t - 0.5) / 3.0
 
 
-def pair(solid, xi, rho1, rho2, prec="fp64", **kw):
+KERNELS = {"tile": 1, "strip": 2}
+
+
+@pytest.fixture(params=list(KERNELS))
+def kernel(request):
+    return KERNELS[request.param]
+
+
+def pair(solid, xi, rho1, rho2, prec="fp64", kernel=0, **kw):
     """The same case on the oracle and on the GPU."""
     o = oracle.Oracle(solid, xi, **kw)
     o.init(rho1, rho2)
-    g = mclbm.Lattice(solid, xi, prec=prec, **kw)
+    g = mclbm.Lattice(solid, xi, prec=prec, kernel=kernel, **kw)
     g.init(rho1, rho2)
     return o, g
 
@@ -55,17 +63,17 @@ def test_init_and_roundtrip_exact():
     assert np.array_equal(g.populations(), h)
 
 
-def test_fp64_disk_medium_drainage_200_steps():
+def test_fp64_disk_medium_drainage_200_steps(kernel):
     """128x64 disk medium, radii U[4,8], porosity ~0.65, Set-3 boundaries
     with rho_in = 1.01, rho_out = 1, neutral wetting, M = 1."""
     c = media.config_small_fp64()
-    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], nu1=c["nu1"], nu2=c["nu2"],
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], kernel=kernel, nu1=c["nu1"], nu2=c["nu2"],
                 rho_in1=c["rho_in1"], rho_out2=c["rho_out2"])
     assert_fp64_parity(o, g, 200)
     assert_fp64_parity(o, g, 300)  # 500 in total
 
 
-def test_fp64_ragged_mixed_wettability_viscosity_ratio_25():
+def test_fp64_ragged_mixed_wettability_viscosity_ratio_25(kernel):
     """Sizes off every tile multiple, several per-site xi values, M = 25."""
     nx, ny = 45, 21
     m = media.make_disk_medium(nx, ny, 7, radius="uniform", r_lo=2.0, r_hi=4.0,
@@ -74,60 +82,62 @@ def test_fp64_ragged_mixed_wettability_viscosity_ratio_25():
     xi = np.where(m.solid != 0, rng.choice([-0.55, -0.4, 0.0, 0.2, 0.5], size=m.solid.shape),
                   0.0).astype(np.float32)
     rho1, rho2 = media.drainage_densities(m.solid, oil_columns=4)
-    o, g = pair(m.solid, xi, rho1, rho2, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62),
+    o, g = pair(m.solid, xi, rho1, rho2, kernel=kernel, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62),
                 rho_in1=1.02, rho_out2=1.0)
     assert_fp64_parity(o, g, 300)
 
 
-def test_fp64_periodic_droplet_with_grain_and_body_force():
+def test_fp64_periodic_droplet_with_grain_and_body_force(kernel):
     nx, ny = 40, 30
     solid = np.zeros((ny, nx), np.uint8)
     yy, xx = np.mgrid[0:ny, 0:nx]
     solid[(xx - 28) ** 2 + (yy - 15) ** 2 <= 20] = 1
     xi = media.uniform_xi(solid, 0.3)
     rho1, rho2 = media.droplet_densities(nx, ny, 12, 14, 6, solid=solid)
-    o, g = pair(solid, xi, rho1, rho2, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
+    o, g = pair(solid, xi, rho1, rho2, kernel=kernel, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
                 periodic_y=True, gx=2e-5, gy=-1e-5)
     assert_fp64_parity(o, g, 250)
 
 
-def test_fp64_open_x_periodic_y():
+def test_fp64_open_x_periodic_y(kernel):
     nx, ny = 50, 24
     solid = np.zeros((ny, nx), np.uint8)
     solid[8:14, 20:27] = 1
     xi = media.uniform_xi(solid, -0.3)
     rho1, rho2 = media.drainage_densities(solid)
-    o, g = pair(solid, xi, rho1, rho2, nu1=nu_of_tau(1.0), nu2=nu_of_tau(0.62),
+    o, g = pair(solid, xi, rho1, rho2, kernel=kernel, nu1=nu_of_tau(1.0), nu2=nu_of_tau(0.62),
                 rho_in1=1.015, rho_out2=1.0, periodic_y=True)
     assert_fp64_parity(o, g, 200)
 
 
-def test_fp64_unshifted_velocity_reading():
+def test_fp64_unshifted_velocity_reading(kernel):
     nx, ny = 37, 19
     m = media.make_disk_medium(nx, ny, 3, radius="uniform", r_lo=2.0, r_hi=3.0,
                                porosity=0.8, reservoir=4)
     rho1, rho2 = media.drainage_densities(m.solid, oil_columns=3)
-    o, g = pair(m.solid, media.uniform_xi(m.solid, -0.2), rho1, rho2, nu1=0.1, nu2=0.05,
+    o, g = pair(m.solid, media.uniform_xi(m.solid, -0.2), rho1, rho2, kernel=kernel, nu1=0.1,
+                nu2=0.05,
                 rho_in1=1.01, rho_out2=1.0, vel_shift=False)
     assert_fp64_parity(o, g, 200)
 
 
-def test_fp64_lattice_smaller_than_a_tile():
+def test_fp64_lattice_smaller_than_a_tile(kernel):
     nx, ny = 7, 5
     solid = np.zeros((ny, nx), np.uint8)
     solid[2, 3] = 1
     rng = np.random.default_rng(5)
     rho1 = (0.1 + rng.random((ny, nx))) * (solid == 0)
     rho2 = (0.1 + rng.random((ny, nx))) * (solid == 0)
-    o, g = pair(solid, media.uniform_xi(solid, 0.1), rho1, rho2, nu1=0.12, nu2=0.2,
+    o, g = pair(solid, media.uniform_xi(solid, 0.1), rho1, rho2, kernel=kernel, nu1=0.12,
+                nu2=0.2,
                 periodic_y=True)
     assert_fp64_parity(o, g, 200)
 
 
-def test_readouts_and_diagnostics_match_oracle():
+def test_readouts_and_diagnostics_match_oracle(kernel):
     c = media.config_small_fp64()
     o, g = pair(c["solid"], media.uniform_xi(c["solid"], -0.4), c["rho1"], c["rho2"],
-                nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+                kernel=kernel, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
     o.step(150)
     g.step(150)
     assert rel_err(g.density(), o.density()) < FP64_TOL
@@ -239,3 +249,37 @@ def test_divergence_flag():
         g.sync()
     assert e.value.code == mclbm.MCLBM_ERR_DIVERGED
     g.sync()                               # the flag is cleared once reported
+
+
+def test_boundary_mode_switch_keeps_parity(kernel):
+    """Switching between periodic x and the Set-3 boundaries mid-run (the
+    ghost columns of the strip kernel are rebuilt) matches the oracle."""
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], kernel=kernel, nu1=c["nu1"],
+                nu2=c["nu2"])
+    assert_fp64_parity(o, g, 60)
+    o.set_pressure_bc(1.01, 1.0)
+    g.set_pressure_bc(1.01, 1.0)
+    assert_fp64_parity(o, g, 60)
+    o.set_pressure_bc(-1, -1)
+    g.set_pressure_bc(-1, -1)
+    assert_fp64_parity(o, g, 60)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32dev", "fp16dev", "bf16dev"])
+def test_strip_and_tile_kernels_agree(prec):
+    """The two formulations of the step compute the same update in every
+    storage precision (same arithmetic, different data movement)."""
+    m = media.make_disk_medium(200, 70, 11, radius="uniform", r_lo=3.0, r_hi=6.0,
+                               porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.4)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    kw = dict(prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+    a = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
+    b = mclbm.Lattice(m.solid, xi, kernel=2, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(300)
+    b.step(300)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= 1e-6 * np.max(np.abs(fa))
