@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
                 f[1][i] = dec(ss, 1, i, lx - ex(i) + HX);
             }
         }
-        apply_set3<R>(a, x, q, [&](int c, int i) { return dec(s0, c, i, lx + HX); }, f);
+        // halo rows of a periodic-y lattice lie outside 0..ny-1: the outlet
+        // values of Eq. 26 are indexed by the wrapped row
+        apply_set3<R>(a, x, pmod(q, g.ny), [&](int c, int i) { return dec(s0, c, i, lx + HX); }, f);
     };
 
     bool bad = false;    // this thread saw a wait run out
