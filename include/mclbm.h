@@ -203,6 +203,32 @@ int mclbm_mass(mclbm_lattice *lat, double out[2]);
  * of device memory held. */
 int mclbm_info(mclbm_lattice *lat, int64_t out[6]);
 
+/*
+ * mclbm_diagnostics without any allocation.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc, or let a library call it
+ * for them (a process whose device memory all comes from its own pool
+ * allocator, a loop that must not allocate once running).
+ *   f      [2][9][ny][nx] FP64 populations in device memory (the layout of
+ *          mclbm_get_populations), owned by the caller
+ *   solid  [ny][nx] uint8 in device memory, 1 = solid, owned by the caller
+ *   g_coh  cohesion strength used in the boundary pressures (Eq. 14)
+ *   periodic_y  1 if rows wrap (affects which boundary nodes count as near
+ *          a wall for P_in/P_out)
+ *   out    [8] results as in mclbm_diagnostics, device or host memory
+ *   cuda_stream  stream to run on (NULL: the legacy default stream)
+ * The per-block partial sums live in a fixed array in the library's device
+ * globals (74 KB per device, held until the process exits), which bounds the
+ * lattice to at most 4194304 nodes; larger lattices are rejected with
+ * MCLBM_ERR_ARG.  Allocates nothing.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so it should come
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  With a device
+ * output the call is asynchronous; with a host output it synchronises the
+ * stream.
+ */
+int mclbm_diagnostics_noalloc(const double *f, const uint8_t *solid, int nx, int ny,
+                              double g_coh, int periodic_y, double *out, void *cuda_stream);
+
 /* Kernel launches enqueued by this library since it was loaded (all
  * lattices); used to count the GPU work inside a timed region. */
 int64_t mclbm_launch_count(void);

@@ -72,6 +72,8 @@ _SIGS = {
     "mclbm_capillary_pressure": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
     "mclbm_mass": (C.c_int, [_vp, _vp]),
     "mclbm_info": (C.c_int, [_vp, _vp]),
+    "mclbm_diagnostics_noalloc": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_int,
+                                            _vp, _vp]),
     "mclbm_launch_count": (_i64, []),
     "mclbm_last_error": (C.c_char_p, []),
 }
@@ -247,6 +249,16 @@ def mclbm_info(h) -> dict:
     out = np.zeros(6, dtype=np.int64)
     _check(load().mclbm_info(h, out.ctypes.data))
     return dict(zip(("nx", "ny", "pitch", "precision", "steps", "device_bytes"), out.tolist()))
+
+
+def mclbm_diagnostics_noalloc(f, solid, nx: int, ny: int, g_coh: float, periodic_y: bool,
+                              out, stream=None) -> None:
+    """Diagnostics of caller-owned device populations [2][9][ny][nx] and
+    solid mask [ny][nx], without any allocation (see include/mclbm.h); out
+    is a [8] float64 buffer on the device or the host."""
+    _check(load().mclbm_diagnostics_noalloc(_addr(f, np.float64), _addr(solid, np.uint8),
+                                            int(nx), int(ny), float(g_coh), int(periodic_y),
+                                            _addr(out, np.float64), _stream_handle(stream)))
 
 
 def mclbm_launch_count() -> int:
