@@ -146,8 +146,10 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.Stream()
     prec = mclbm.PRECISIONS[args.prec]
     c = workload()
+    kernel = {"auto": 0, "tile": 1, "strip": 2}[args.kernel]
     lat = mclbm.Lattice(c["solid"], c["xi"], prec=prec, nu1=c["nu1"], nu2=c["nu2"],
-                        rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream)
+                        rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream,
+                        kernel=kernel)
     lat.init(c["rho1"], c["rho2"])
     n_all = c["nx"] * c["ny"]
     for _ in range(max(args.warmup, 3)):
@@ -207,7 +209,8 @@ def run_gpu(args, rank, world):
     # the 1024x512 lattice of the same recipe: L2-resident, context only
     c2 = workload(1024, 512, 1)
     lat2 = mclbm.Lattice(c2["solid"], c2["xi"], prec=prec, nu1=c2["nu1"], nu2=c2["nu2"],
-                         rho_in1=c2["rho_in1"], rho_out2=c2["rho_out2"], stream=stream)
+                         rho_in1=c2["rho_in1"], rho_out2=c2["rho_out2"], stream=stream,
+                         kernel=kernel)
     lat2.init(c2["rho1"], c2["rho2"])
     lat2.step(20)
     lat2.sync()
@@ -234,7 +237,8 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{c['name']} seed 99 (drainage, M=10, theta=50 deg, "
                                f"rho_in=1.005, rho_out=1)",
                    "nx": c["nx"], "ny": c["ny"], "porosity": round(c["porosity"], 4),
-                   "storage": args.prec, "parallelism": f"replicas x{world}",
+                   "storage": args.prec, "step_kernel": args.kernel,
+                   "parallelism": f"replicas x{world}",
                    "l2": "working set 302 MB > 129 MB L2, no flush needed",
                    "mflups": round(value * (c["solid"] == 0).mean(), 1),
                    "l2_resident_1024x512_mlups": round(l2_mlups, 1)},
@@ -324,6 +328,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["fp64", "fp32", "fp32dev", "fp16dev", "bf16dev"],
                     default="fp32")
+    ap.add_argument("--kernel", choices=["auto", "tile", "strip"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

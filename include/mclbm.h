@@ -72,10 +72,11 @@ typedef enum {
      * or negative density); a hit is reported by the next synchronising
      * call as MCLBM_ERR_DIVERGED.  0 (default): off. */
     MCLBM_FLAG_DIAG_EVERY = 2,
-    /* Step kernel: 0 (default) the row-sweeping strip kernel, which stages
-     * rows in shared memory with bulk copies; 1 the 2-D tile kernel, which
-     * pulls straight from global memory; 2 the strip kernel.  Both compute
-     * the same update. */
+    /* Step kernel, all computing the same update: 0 (default) chooses 3
+     * for the FP32 and deviation storages and 1 for FP64; 1 the 2-D tile
+     * kernel pulling straight from global memory; 2 the row-sweeping strip
+     * kernel staging rows with bulk copies; 3 the 2-D tile kernel staging
+     * the tile and its ring with one tensor copy (not for FP64). */
     MCLBM_FLAG_KERNEL = 3
 } mclbm_flag;
 

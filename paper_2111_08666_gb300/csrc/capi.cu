@@ -105,6 +105,7 @@ void release(Lattice *L) {
     cudaFree(L->diag_out);
     cudaFree(L->bad_flag);
     cudaFree(L->err);
+    tma_release(*L);
     if (L->host_diag) cudaFreeHost(L->host_diag);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     L->own_stream = false;
@@ -136,10 +137,10 @@ int run_diagnostics(Lattice &L, double out[8]) {
 // Rebuild the ghost columns if the x boundary mode changed since they were
 // last built.
 int refresh_ghosts(Lattice &L) {
-    if (L.geo_ghost_open == L.p.open_x) return MCLBM_OK;
+    if (L.ghost_mode == L.ghost_key()) return MCLBM_OK;
     cudaError_t e = launch_geo_ghosts(L);
     if (e != cudaSuccess) return cuda_fail(e, "ghost columns");
-    L.geo_ghost_open = L.p.open_x;
+    L.ghost_mode = L.ghost_key();
     return MCLBM_OK;
 }
 
@@ -208,7 +209,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         long long row_bytes = (cols * sb + 127) / 128 * 128;
         if ((row_bytes / 128) % 2 == 0) row_bytes += 128;
         L->pitch = (int)(row_bytes / sb);
-        long long plane_bytes = row_bytes * ny;
+        long long plane_bytes = row_bytes * (ny + 2 * HY);
         if ((plane_bytes / 128) % 2 == 0) plane_bytes += 128;
         L->plane = plane_bytes / sb;
         L->gpitch = (int)(((long long)(nx + SWEEP_W - 1) / SWEEP_W * SWEEP_W + 2 * GEO_HX + 15) / 16 * 16);
@@ -279,6 +280,11 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         delete L;
         return rc;
     }
+    if ((rc = tma_prepare(*L))) {
+        release(L);
+        delete L;
+        return rc;
+    }
     e = cudaMallocHost((void **)&L->host_diag, 8 * sizeof(double));
     if (e != cudaSuccess) {
         release(L);
@@ -317,7 +323,7 @@ int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
         case MCLBM_FLAG_PERIODIC_Y: lat->p.periodic_y = value ? 1 : 0; return MCLBM_OK;
         case MCLBM_FLAG_VEL_SHIFT: lat->p.vel_shift = value ? 1 : 0; return MCLBM_OK;
         case MCLBM_FLAG_KERNEL:
-            if (value < 0 || value > 2) return fail(MCLBM_ERR_ARG, "kernel must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(MCLBM_ERR_ARG, "kernel must be 0..3");
             lat->kernel = value;
             return MCLBM_OK;
         case MCLBM_FLAG_DIAG_EVERY:
@@ -409,7 +415,7 @@ int mclbm_init_densities(mclbm_lattice *lat, const double *rho1, const double *r
     DeviceView v1, v2;
     if (int rc = view_in(*lat, rho1, bytes, v1)) return rc;
     if (int rc = view_in(*lat, rho2, bytes, v2)) return rc;
-    lat->geo_ghost_open = -1;
+    lat->ghost_mode = -1;
     if (int rc = refresh_ghosts(*lat)) return rc;
     cudaError_t e = launch_init_equilibrium(*lat, static_cast<const double *>(v1.ptr),
                                             static_cast<const double *>(v2.ptr));
@@ -427,7 +433,7 @@ int mclbm_set_populations(mclbm_lattice *lat, const double *f) {
     if (int rc = make_current(*lat)) return rc;
     DeviceView v;
     if (int rc = view_in(*lat, f, (size_t)18 * lat->nx * lat->ny * sizeof(double), v)) return rc;
-    lat->geo_ghost_open = -1;
+    lat->ghost_mode = -1;
     if (int rc = refresh_ghosts(*lat)) return rc;
     cudaError_t e = launch_set_populations(*lat, static_cast<const double *>(v.ptr));
     if (e != cudaSuccess) return cuda_fail(e, "import kernel");
@@ -455,9 +461,16 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
     if (int rc = check_ready(*lat)) return rc;
     if (int rc = make_current(*lat)) return rc;
     if (int rc = refresh_ghosts(*lat)) return rc;
-    const bool sweep = lat->kernel == 2 || (lat->kernel == 0 && sweep_supported(*lat));
+    int which = (int)lat->kernel;
+    if (which == 0) which = tma_supported(*lat) ? 3 : 1;
+    if (which == 3 && !tma_supported(*lat))
+        return fail(MCLBM_ERR_ARG, "the TMA tile kernel is not available for this precision");
+    if (which == 2 && !sweep_supported(*lat))
+        return fail(MCLBM_ERR_ARG, "the strip kernel is not available for this lattice");
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = sweep ? launch_step_sweep(*lat) : launch_step_tile(*lat, 0);
+        cudaError_t e = which == 3   ? launch_step_tma(*lat)
+                        : which == 2 ? launch_step_sweep(*lat)
+                                     : launch_step_tile(*lat, 0);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
         ++lat->steps;
         if (lat->diag_every > 0 && lat->steps % lat->diag_every == 0) {

@@ -93,9 +93,9 @@ __global__ void geo_ghost_kernel(Geometry g, int open_x) {
 }
 
 // Population ghost columns for periodic x: copy the hx edge columns of
-// every plane of the current state to the opposite side.
+// every plane of the current state to the opposite side (rows 0..ny-1).
 template <class P>
-__global__ void pop_ghost_kernel(Geometry g, typename P::store_t *f) {
+__global__ void pop_ghost_cols_kernel(Geometry g, typename P::store_t *f) {
     const int y = blockIdx.x;
     const int ng = 2 * g.hx;
     for (int k = threadIdx.x; k < P::planes * ng; k += blockDim.x) {
@@ -103,6 +103,20 @@ __global__ void pop_ghost_kernel(Geometry g, typename P::store_t *f) {
         const int gx = j < g.hx ? j - g.hx : g.nx + (j - g.hx);
         const long long base = (long long)pl * g.plane;
         f[base + site_of(g, gx, y)] = f[base + site_of(g, pmod(gx, g.nx), y)];
+    }
+}
+
+// Population ghost rows for periodic y: copy whole rows (ghost columns
+// included) of every plane to the rows beyond the opposite edge.
+template <class P>
+__global__ void pop_ghost_rows_kernel(Geometry g, typename P::store_t *f) {
+    const int j = blockIdx.x;  // 0..2 HY - 1
+    const int gy = j < HY ? j - HY : g.ny + (j - HY);
+    const int sy = pmod(gy, g.ny);
+    for (long long k = threadIdx.x; k < (long long)P::planes * g.pitch; k += blockDim.x) {
+        const long long base = (k / g.pitch) * g.plane;
+        const int col = (int)(k % g.pitch);
+        f[base + (long long)(gy + HY) * g.pitch + col] = f[base + (long long)(sy + HY) * g.pitch + col];
     }
 }
 
@@ -451,13 +465,19 @@ cudaError_t launch_geo_ghosts(Lattice &L) {
     geo_ghost_kernel<<<L.ny, 128, 0, L.stream>>>(geometry_of(L), L.p.open_x);
     count_launch();
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || L.p.open_x) return e;
+    if (e != cudaSuccess) return e;
     const Geometry g = geometry_of(L);
     return dispatch(L, [&](auto tag) {
         using P = decltype(tag);
-        pop_ghost_kernel<P><<<L.ny, 128, 0, L.stream>>>(
-            g, static_cast<typename P::store_t *>(L.f[L.cur]));
-        count_launch();
+        auto *f = static_cast<typename P::store_t *>(L.f[L.cur]);
+        if (!L.p.open_x) {
+            pop_ghost_cols_kernel<P><<<L.ny, 128, 0, L.stream>>>(g, f);
+            count_launch();
+        }
+        if (L.p.periodic_y) {
+            pop_ghost_rows_kernel<P><<<2 * HY, 256, 0, L.stream>>>(g, f);
+            count_launch();
+        }
         return cudaGetLastError();
     });
 }

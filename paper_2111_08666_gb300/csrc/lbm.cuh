@@ -91,16 +91,20 @@ struct Params {
 };
 
 // Memory layout shared by every kernel.  Population (c, i, y, x) lives at
-// f[(c*9 + i) * plane + y * pitch + hx + x]; columns -hx..-1 and nx..nx+hx-1
-// are ghost copies of the opposite edge when x is periodic.  Reference
-// densities (REF precisions) are planes 18 and 19.  pitch and plane are odd
-// multiples of 128 bytes so that the direction planes and rows do not alias
-// in the caches.
+// f[(c*9 + i) * plane + (y + HY) * pitch + hx + x]; columns -hx..-1 and
+// nx..nx+hx-1 are ghost copies of the opposite edge when x is periodic, and
+// rows -HY..-1 and ny..ny+HY-1 likewise when y is periodic, so that a tile
+// and its 3-node ring are always one rectangular box.  Reference densities
+// (REF precisions) are planes 18 and 19.  pitch and plane are odd multiples
+// of 128 bytes so that the direction planes and rows do not alias in the
+// caches.
+constexpr int HY = 3;
+
 struct Geometry {
     int nx, ny;
     int pitch;                 // population row stride, elements
     int hx;                    // column of x = 0 within a population row
-    long long plane;           // population plane stride, elements
+    long long plane;           // population plane stride, elements (ny + 2 HY rows)
     int gpitch;                // geometry row stride, bytes
     const uint8_t *geo;        // [ny][gpitch], column x at GEO_HX + x
     const double *chi;         // [256][2] (1 + xi, 1 - xi) by code, in FP64
@@ -135,7 +139,7 @@ struct Lattice {
     bool own_stream = false;
     int device = 0;
     uint8_t *geo = nullptr;    // [ny][gpitch]
-    int geo_ghost_open = -1;   // x mode the geometry ghosts were built for
+    int ghost_mode = -1;       // boundary mode the ghosts were built for
     double *chi = nullptr;     // [256][2]
     void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
     int cur = 0;               // index of the buffer holding the state
@@ -152,6 +156,8 @@ struct Lattice {
     size_t device_bytes = 0;
     bool boundary_rows_solid = false;
     bool initialised = false;
+    void *tmaps = nullptr;     // host copies of the TMA descriptors (tile kernel)
+    int ghost_key() const { return p.open_x * 2 + p.periodic_y; }
     Geometry geometry() const {
         return Geometry{nx, ny, pitch, hx, plane, gpitch, geo, chi};
     }
@@ -166,6 +172,10 @@ void count_launch(int n = 1);
 cudaError_t launch_step_tile(Lattice &L, int tile_cfg);
 cudaError_t launch_step_sweep(Lattice &L);
 bool sweep_supported(const Lattice &L);
+cudaError_t launch_step_tma(Lattice &L);
+bool tma_supported(const Lattice &L);
+int tma_prepare(Lattice &L);      // builds the TMA descriptors; MCLBM_OK or error
+void tma_release(Lattice &L);
 cudaError_t launch_geo_ghosts(Lattice &L);
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
 cudaError_t launch_set_populations(Lattice &L, const double *f);

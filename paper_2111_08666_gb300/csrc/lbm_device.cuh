@@ -15,7 +15,7 @@ __device__ __forceinline__ int pmod(int v, int n) { return ((v % n) + n) % n; }
 
 // element offset of node (x, y) in a population plane
 __device__ __forceinline__ long long site_of(const Geometry &g, int x, int y) {
-    return (long long)y * g.pitch + g.hx + x;
+    return (long long)(y + HY) * g.pitch + g.hx + x;
 }
 
 // ---------------------------------------------------------------------------
@@ -59,19 +59,36 @@ __device__ __forceinline__ void pop_store_site(typename P::store_t *f, long long
     }
 }
 
+// Store the ghost images of node (x, y) (periodic x and/or y); the node's
+// own site is not written.
+template <class P>
+__device__ __forceinline__ void pop_store_ghosts(const Geometry &g, const Params &p,
+                                                 typename P::store_t *f, int x, int y,
+                                                 const typename P::real_t fs[2][9],
+                                                 typename P::real_t rho1,
+                                                 typename P::real_t rho2) {
+    const bool px = !p.open_x, py = p.periodic_y != 0;
+    if (!px && !py) return;
+    const bool near_x = px && (x < g.hx || x >= g.nx - g.hx);
+    const bool near_y = py && (y < HY || y >= g.ny - HY);
+    if (!near_x && !near_y) return;
+    // every image (x + a nx, y + b ny) inside the ghost frame, except a = b = 0
+    const int ax0 = px ? -((x + g.hx) / g.nx) : 0, ax1 = px ? (g.nx + g.hx - 1 - x) / g.nx : 0;
+    const int by0 = py ? -((y + HY) / g.ny) : 0, by1 = py ? (g.ny + HY - 1 - y) / g.ny : 0;
+    for (int a = ax0; a <= ax1; ++a)
+        for (int b = by0; b <= by1; ++b) {
+            if (a == 0 && b == 0) continue;
+            pop_store_site<P>(f, g.plane, site_of(g, x + a * g.nx, y + b * g.ny), fs, rho1, rho2);
+        }
+}
+
 template <class P>
 __device__ __forceinline__ void pop_store_node(const Geometry &g, const Params &p,
                                                typename P::store_t *f, int x, int y,
                                                const typename P::real_t fs[2][9],
                                                typename P::real_t rho1, typename P::real_t rho2) {
     pop_store_site<P>(f, g.plane, site_of(g, x, y), fs, rho1, rho2);
-    if (!p.open_x) {
-        // ghost images of this column for periodic x
-        for (int gx = x - g.nx; gx >= -g.hx; gx -= g.nx)
-            pop_store_site<P>(f, g.plane, site_of(g, gx, y), fs, rho1, rho2);
-        for (int gx = x + g.nx; gx < g.nx + g.hx; gx += g.nx)
-            pop_store_site<P>(f, g.plane, site_of(g, gx, y), fs, rho1, rho2);
-    }
+    pop_store_ghosts<P>(g, p, f, x, y, fs, rho1, rho2);
 }
 
 // Geometry code of (x, y) with periodic wrap where the lattice is periodic,

@@ -20,78 +20,12 @@
 // Every wait on an mbarrier is bounded (about one second of %globaltimer);
 // on expiry the CTA records MCLBM_ERR_TIMEOUT in the error word, waits a
 // bounded time for the copies it issued, and returns.
+#include "async_copy.cuh"
 #include "lbm_device.cuh"
 
 namespace mclbm {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Wait for the phase of the given parity; false if it did not complete
-// within limit_ns.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_test(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_test(bar, parity)) {
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;  // 1 s
-constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;  // 0.1 s
 
 template <class P, int W, int NR>
 struct SweepLayout {
@@ -152,7 +86,7 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
             fence_proxy_async();
             mbar_expect_tx(&bar[slot], L::row_tx);
             // element x0 - HX of the row is column x0 + hx - HX = x0 in memory
-            const S *src = fin + (long long)qq * g.pitch + x0;
+            const S *src = fin + (long long)(qq + HY) * g.pitch + x0;
             for (int p = 0; p < NPL; ++p)
                 bulk_g2s(raw + (slot * NPL + p) * RW, src + (long long)p * g.plane,
                          RW * sizeof(S), &bar[slot]);

@@ -266,20 +266,44 @@ def test_boundary_mode_switch_keeps_parity(kernel):
     assert_fp64_parity(o, g, 60)
 
 
+@pytest.mark.parametrize("other", [2, 3])
 @pytest.mark.parametrize("prec", ["fp32", "fp32dev", "fp16dev", "bf16dev"])
-def test_strip_and_tile_kernels_agree(prec):
-    """The two formulations of the step compute the same update in every
-    storage precision (same arithmetic, different data movement)."""
+def test_step_kernels_agree(prec, other):
+    """The formulations of the step (global-pull tile, strip, TMA tile)
+    compute the same update in every storage precision (same arithmetic,
+    different data movement)."""
     m = media.make_disk_medium(200, 70, 11, radius="uniform", r_lo=3.0, r_hi=6.0,
                                porosity=0.7)
     xi = media.uniform_xi(m.solid, -0.4)
     rho1, rho2 = media.drainage_densities(m.solid)
     kw = dict(prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
     a = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
-    b = mclbm.Lattice(m.solid, xi, kernel=2, **kw)
+    b = mclbm.Lattice(m.solid, xi, kernel=other, **kw)
     a.init(rho1, rho2)
     b.init(rho1, rho2)
     a.step(300)
     b.step(300)
     fa, fb = a.populations(), b.populations()
     assert np.max(np.abs(fa - fb)) <= 1e-6 * np.max(np.abs(fa))
+
+
+@pytest.mark.parametrize("periodic_y,open_x", [(True, False), (True, True), (False, False)])
+def test_tma_kernel_ghost_frames_fp32(periodic_y, open_x):
+    """The TMA tile kernel reads its ring from the ghost columns and rows at
+    periodic edges; a lattice off every tile multiple, against the oracle."""
+    nx, ny = 75, 41
+    solid = np.zeros((ny, nx), np.uint8)
+    if not periodic_y:
+        solid[0] = solid[-1] = 1
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    solid[(xx - 50) ** 2 + (yy - 20) ** 2 <= 30] = 1
+    xi = media.uniform_xi(solid, -0.3)
+    rho1, rho2 = media.droplet_densities(nx, ny, 20, 20, 9, solid=solid)
+    kw = dict(nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), periodic_y=periodic_y)
+    if open_x:
+        rho1, rho2 = media.drainage_densities(solid)
+        kw.update(rho_in1=1.01, rho_out2=1.0)
+    o, g = pair(solid, xi, rho1, rho2, prec="fp32", kernel=3, **kw)
+    o.step(300)
+    g.step(300)
+    assert rel_err(g.populations(), o.f) < 2e-5
