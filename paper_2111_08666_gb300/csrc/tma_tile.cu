@@ -130,16 +130,20 @@ __global__ void __launch_bounds__(TX *TY, 2)
     auto geo_s = [&](int r, int c) -> uint8_t { return geo[r * GXW + c]; };
 
     // ---- work lists ---------------------------------------------------------
+    // L1: fluid positions of the 2-ring around the tile (the tile's own
+    // nodes are pulled by the threads that collide them, L3)
     for (int base = warp * 32; base < L::N1; base += NT) {
         const int k = base + lane;
         bool f = false;
         if (k < L::N1) {
             const int dr = k / DXW, dc = k % DXW;
-            f = geo_s(dr + 1, dc + 2) == GEO_FLUID;
-            if (!f) {
+            const bool inner = dr >= 2 && dr < TY + 2 && dc >= 2 && dc < TX + 2;
+            const bool fl = geo_s(dr + 1, dc + 2) == GEO_FLUID;
+            if (!fl || inner) {
                 rho[k] = R(0);
                 rho[L::N1 + k] = R(0);
             }
+            f = fl && !inner;
         }
         list_append(f, (uint16_t)k, l1, &cnt[0]);
     }
@@ -201,12 +205,14 @@ __global__ void __launch_bounds__(TX *TY, 2)
     };
 
     // ---- A: densities on the density frame -----------------------------------
+    // ring positions (the frame reaches at most 2 rows past an edge, and
+    // ny >= 3, so one period of wrap suffices)
     const int n1 = cnt[0];
     for (int k = tid; k < n1; k += NT) {
         const int pos = l1[k];
         const int dr = pos / DXW, dc = pos % DXW;
         R f[2][9];
-        pull(dr + 1, dc - 2 + HX, x0 - 2 + dc, pmod(y0 - 2 + dr, g.ny), f);
+        pull(dr + 1, dc - 2 + HX, x0 - 2 + dc, wrap(y0 - 2 + dr, g.ny), f);
         R r1 = 0, r2 = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -215,6 +221,26 @@ __global__ void __launch_bounds__(TX *TY, 2)
         }
         rho[pos] = r1;
         rho[L::N1 + pos] = r2;
+    }
+    // the tile's own fluid nodes: each thread pulls at most one and keeps its
+    // populations in registers for the collision
+    const int n3 = cnt[2];
+    const bool have = tid < n3;
+    int ty = 0, tx = 0;
+    R f[2][9];
+    R rho1 = 0, rho2 = 0;
+    if (have) {
+        const int idx = l3[tid];
+        ty = idx / TX;
+        tx = idx % TX;
+        pull(ty + 3, tx + HX, x0 + tx, y0 + ty, f);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            rho1 += f[0][i];
+            rho2 += f[1][i];
+        }
+        rho[(ty + 2) * DXW + tx + 2] = rho1;
+        rho[L::N1 + (ty + 2) * DXW + tx + 2] = rho2;
     }
     __syncthreads();
 
@@ -247,20 +273,9 @@ __global__ void __launch_bounds__(TX *TY, 2)
     __syncthreads();
 
     // ---- C: collision of the tile's fluid nodes ---------------------------------
-    const int n3 = cnt[2];
     S *fout = static_cast<S *>(a.fout);
-    for (int k = tid; k < n3; k += NT) {
-        const int idx = l3[k];
-        const int ty = idx / TX, tx = idx % TX;
+    if (have) {
         const int x = x0 + tx, y = y0 + ty;
-        R f[2][9];
-        pull(ty + 3, tx + HX, x, y, f);
-        R rho1 = 0, rho2 = 0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            rho1 += f[0][i];
-            rho2 += f[1][i];
-        }
         const bool mirror_in = a.p.open_x && x == 0;
         const bool mirror_out = a.p.open_x && x == g.nx - 1;
         const int dpos = (ty + 2) * DXW + tx + 2;
@@ -376,8 +391,10 @@ cudaError_t launch_tma_cfg(Lattice &L, const StepArgs &a) {
     }
     const CUtensorMap *maps = static_cast<const CUtensorMap *>(L.tmaps);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY);
-    tma_tile_kernel<P, TX, TY><<<grid, TX * TY, Lay::total, L.stream>>>(maps[2 * L.cur],
-                                                                        maps[2 * L.cur + 1], a);
+    // read through the input map of the current buffer, store through the
+    // output map of the other one
+    tma_tile_kernel<P, TX, TY><<<grid, TX * TY, Lay::total, L.stream>>>(
+        maps[2 * L.cur], maps[2 * (1 - L.cur) + 1], a);
     count_launch();
     return cudaGetLastError();
 }
