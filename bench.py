@@ -222,6 +222,10 @@ def run_gpu(args, rank, world):
     l2_mlups = 1024 * 512 * k2 / (start.elapsed_time(end) / 1e3) / 1e6
     lat2.close()
 
+    batched = None
+    if args.batch_steps > 0:
+        batched = batched_section(args, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -252,12 +256,64 @@ def run_gpu(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "batched": batched,
         "diag": {k: (None if isinstance(v, float) and math.isnan(v) else v)
                  for k, v in diag.items()},
     }
     lat.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def batched_section(args, stream) -> dict:
+    """24 uneven cases (256x256 .. 1024x512, seeds 10..33, theta 30..150 deg,
+    M = 1, 10, 50), FP32: one persistent launch per step under a CUDA graph
+    with the autotuned tile, against the same cases stepped one at a time."""
+    import torch
+    from paper_2111_08666_gb300 import mclbm
+    cases = [media.config_batch(k) for k in range(24)]
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    k_steps = args.batch_steps
+    b = mclbm.mclbm_batch_create(cases, mclbm.MCLBM_FP32, stream)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        mclbm.mclbm_batch_step(b, 48)          # tuning + graph capture + warm-up
+        torch.cuda.synchronize()
+        l0 = mclbm.mclbm_launch_count()
+        start.record(stream)
+        mclbm.mclbm_batch_step(b, k_steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        launches = mclbm.mclbm_launch_count() - l0
+        t_batch = start.elapsed_time(end) / 1e3
+        info = mclbm.mclbm_batch_info(b)
+        tuning = mclbm.mclbm_batch_tuning(b)
+    finally:
+        mclbm.mclbm_batch_destroy(b)
+    lats = []
+    for c in cases:
+        lat = mclbm.Lattice(c["solid"], c["xi"], prec="fp32", nu1=c["nu1"], nu2=c["nu2"],
+                            rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream)
+        lat.init(c["rho1"], c["rho2"])
+        lat.step(3)
+        lats.append(lat)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for lat in lats:
+        lat.step(k_steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    t_seq = start.elapsed_time(end) / 1e3
+    for lat in lats:
+        lat.close()
+    return {"workload": "24 disk media 256x256..1024x512, seeds 10-33, theta 30-150 deg, "
+                        "M=1/10/50, FP32, drainage rho_in=1.005",
+            "nodes": nodes, "steps": k_steps,
+            "mlups_batched": round(nodes * k_steps / t_batch / 1e6, 1),
+            "mlups_one_at_a_time": round(nodes * k_steps / t_seq / 1e6, 1),
+            "launches": int(launches), "tile_shape": info["shape"],
+            "grid": "persistent" if info["grid"] == 0 else "one CTA per tile",
+            "tuner_ms_per_step": [round(x, 4) for x in tuning]}
 
 
 def cpu_baseline(seconds: float) -> dict:
@@ -330,6 +386,8 @@ def main():
                     default="fp32")
     ap.add_argument("--kernel", choices=["auto", "tile", "strip"], default="auto")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-steps", type=int, default=400,
+                    help="steps of the 24-case batched section (0: skip it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, world, _ = replicas.rank_info()

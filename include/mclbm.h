@@ -230,6 +230,60 @@ int mclbm_info(mclbm_lattice *lat, int64_t out[6]);
 int mclbm_diagnostics_noalloc(const double *f, const uint8_t *solid, int nx, int ny,
                               double g_coh, int periodic_y, double *out, void *cuda_stream);
 
+/*
+ * Batches: many independent lattices (porous-medium realisations or
+ * wettability states of uneven sizes) advanced together, one persistent
+ * launch per step over a work list of (lattice, tile) items, replayed from a
+ * captured CUDA graph.  The paper runs one lattice at a time; batching is a
+ * throughput feature of this library.  Every case computes exactly what
+ * mclbm_step computes for it alone.
+ */
+typedef struct {
+    int nx, ny;                 /* lattice size (as mclbm_create) */
+    const uint8_t *solid;       /* [ny][nx] host, 1 = solid */
+    const float *xi;            /* [ny][nx] host wettability, or NULL */
+    double nu1, nu2;            /* viscosities (mclbm_set_viscosity) */
+    double g_coh, g_ads;        /* coupling strengths (mclbm_set_coupling) */
+    double gx, gy;              /* body acceleration */
+    double rho_in1, rho_out2;   /* Set-3 densities; < 0: periodic x */
+    int periodic_y;             /* 1: periodic y */
+    const double *rho1, *rho2;  /* initial densities [ny][nx], or NULL */
+} mclbm_case_desc;
+
+typedef struct mclbm_batch mclbm_batch;
+
+/* Create a batch of 1..32 cases in one storage precision (not FP64); the
+ * library copies the host arrays.  cuda_stream as for mclbm_create. */
+int mclbm_batch_create(int ncases, const mclbm_case_desc *cases, mclbm_precision prec,
+                       void *cuda_stream, mclbm_batch **out);
+
+/* Free the batch and all its lattices.  NULL is accepted. */
+int mclbm_batch_destroy(mclbm_batch *b);
+
+/* Borrow case k as a lattice handle for parameters and read-outs (valid
+ * until the batch is destroyed; do not destroy it, and do not step it with
+ * mclbm_step).  A parameter change makes the next batch step re-capture
+ * its graph. */
+int mclbm_batch_lattice(mclbm_batch *b, int k, mclbm_lattice **view);
+
+/* Advance every case nsteps steps.  The first call times the candidate tile
+ * shapes and grid sizes on its first steps (ordinary steps: all candidates
+ * compute identical results) and keeps the fastest; steps then run in
+ * graph replays of 16 launches.  Asynchronous. */
+int mclbm_batch_step(mclbm_batch *b, int64_t nsteps);
+
+/* out[0] cases, out[1] total nodes, out[2] chosen tile shape (0: 32 x 16
+ * or 32 x 12, 1: 32 x 8; -1 not yet chosen), out[3] grid (0: one CTA per
+ * resident slot, persistent; -1: one CTA per tile), out[4] steps per graph
+ * replay, out[5] steps taken, out[6] resident CTA slots, out[7] 1 if a graph
+ * is captured. */
+int mclbm_batch_info(mclbm_batch *b, int64_t out[8]);
+
+/* Milliseconds per step the tuner measured for its 4 candidates (shape 0
+ * persistent, shape 0 one CTA per tile, shape 1 persistent, shape 1 one CTA
+ * per tile). */
+int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[4]);
+
 /* Kernel launches enqueued by this library since it was loaded (all
  * lattices); used to count the GPU work inside a timed region. */
 int64_t mclbm_launch_count(void);

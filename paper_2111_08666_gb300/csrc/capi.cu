@@ -167,11 +167,15 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int lattice_prepare_step(Lattice &L) {
+    if (int rc = check_ready(L)) return rc;
+    return refresh_ghosts(L);
+}
+
 }  // namespace mclbm
 
 using namespace mclbm;
 
-struct mclbm_lattice : public Lattice {};
 
 extern "C" {
 
@@ -320,8 +324,14 @@ int mclbm_destroy(mclbm_lattice *lat) {
 int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
     if (int rc = check_lat(lat)) return rc;
     switch (flag) {
-        case MCLBM_FLAG_PERIODIC_Y: lat->p.periodic_y = value ? 1 : 0; return MCLBM_OK;
-        case MCLBM_FLAG_VEL_SHIFT: lat->p.vel_shift = value ? 1 : 0; return MCLBM_OK;
+        case MCLBM_FLAG_PERIODIC_Y:
+            lat->p.periodic_y = value ? 1 : 0;
+            ++lat->version;
+            return MCLBM_OK;
+        case MCLBM_FLAG_VEL_SHIFT:
+            lat->p.vel_shift = value ? 1 : 0;
+            ++lat->version;
+            return MCLBM_OK;
         case MCLBM_FLAG_KERNEL:
             if (value < 0 || value > 3) return fail(MCLBM_ERR_ARG, "kernel must be 0..3");
             lat->kernel = value;
@@ -340,6 +350,7 @@ int mclbm_set_viscosity(mclbm_lattice *lat, double nu1, double nu2) {
         return fail(MCLBM_ERR_ARG, "viscosities must be positive and finite");
     lat->p.nu1 = nu1;
     lat->p.nu2 = nu2;
+    ++lat->version;
     return MCLBM_OK;
 }
 
@@ -349,6 +360,7 @@ int mclbm_set_coupling(mclbm_lattice *lat, double g_coh, double g_ads) {
         return fail(MCLBM_ERR_ARG, "coupling strengths must be finite");
     lat->p.g_coh = g_coh;
     lat->p.g_ads = g_ads;
+    ++lat->version;
     return MCLBM_OK;
 }
 
@@ -357,6 +369,7 @@ int mclbm_set_body_force(mclbm_lattice *lat, double gx, double gy) {
     if (!std::isfinite(gx) || !std::isfinite(gy)) return fail(MCLBM_ERR_ARG, "g must be finite");
     lat->p.gx = gx;
     lat->p.gy = gy;
+    ++lat->version;
     return MCLBM_OK;
 }
 
@@ -364,6 +377,7 @@ int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2) {
     if (int rc = check_lat(lat)) return rc;
     if (!std::isfinite(rho_in1) || !std::isfinite(rho_out2))
         return fail(MCLBM_ERR_ARG, "boundary densities must be finite");
+    ++lat->version;
     if (rho_in1 < 0 || rho_out2 < 0) {
         lat->p.open_x = 0;
         lat->p.rho_in1 = lat->p.rho_out2 = -1.0;

@@ -157,6 +157,7 @@ struct Lattice {
     bool boundary_rows_solid = false;
     bool initialised = false;
     void *tmaps = nullptr;     // host copies of the TMA descriptors (tile kernel)
+    uint64_t version = 0;      // bumped whenever a parameter changes
     int ghost_key() const { return p.open_x * 2 + p.periodic_y; }
     Geometry geometry() const {
         return Geometry{nx, ny, pitch, hx, plane, gpitch, geo, chi};
@@ -167,6 +168,7 @@ struct Lattice {
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n = 1);
+int lattice_prepare_step(Lattice &L);  // checks and ghost refresh before stepping (capi.cu)
 
 // launchers (step.cu, sweep.cu, fields.cu); return cudaError_t of the launch
 cudaError_t launch_step_tile(Lattice &L, int tile_cfg);
@@ -176,6 +178,13 @@ cudaError_t launch_step_tma(Lattice &L);
 bool tma_supported(const Lattice &L);
 int tma_prepare(Lattice &L);      // builds the TMA descriptors; MCLBM_OK or error
 void tma_release(Lattice &L);
+// batched persistent launch over several lattices (tma_tile.cu)
+constexpr int MAX_BATCH = 32;
+size_t tile_maps_bytes();         // bytes of the 4 descriptors of one lattice
+int tile_maps_for(const Lattice &L, int shape, void *out);
+cudaError_t launch_step_batch(Lattice *const *cases, int n, const void *maps, int shape, int grid,
+                              cudaStream_t stream);
+int batch_slots(mclbm_precision p, int shape);
 cudaError_t launch_geo_ghosts(Lattice &L);
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
 cudaError_t launch_set_populations(Lattice &L, const double *f);
@@ -189,3 +198,6 @@ size_t velocity_scratch_bytes(const Lattice &L);
 int diag_blocks_for(const Lattice &L);
 
 }  // namespace mclbm
+
+// the opaque handle type of the C ABI is the lattice object itself
+struct mclbm_lattice : public mclbm::Lattice {};

@@ -78,17 +78,19 @@ __device__ __forceinline__ void list_append(bool flag, uint16_t val, uint16_t *l
     if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
+// One tile (bx, by) of one lattice.  The caller has initialised the
+// mbarrier at bar_off; parity is the phase this tile's input copy completes.
+// Returns false (uniformly over the CTA) if the wait for the copy ran out.
 template <class P, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 2)
-    tma_tile_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-                    const StepArgs a) {
+__device__ __forceinline__ bool tma_tile_body(const CUtensorMap *tin, const CUtensorMap *tout,
+                                              const StepArgs &a, int bx, int by, uint32_t parity,
+                                              unsigned char *smem) {
     using L = TileLayout<P, TX, TY>;
     using S = typename P::store_t;
     using R = typename P::real_t;
     constexpr int NT = L::NT, HX = L::HX, RXW = L::RXW, PSTR = L::PSTR, DXW = L::DXW,
                   GXW = L::GXW;
 
-    extern __shared__ __align__(128) unsigned char smem[];
     const S *in = reinterpret_cast<const S *>(smem);
     S *out = reinterpret_cast<S *>(smem + L::out_off);
     R *rho = reinterpret_cast<R *>(smem + L::rho_off);
@@ -101,18 +103,15 @@ __global__ void __launch_bounds__(TX *TY, 2)
 
     const Geometry &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
 
+    __syncthreads();  // a previous tile of this CTA is done with shared memory
     if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
         cnt[0] = cnt[1] = cnt[2] = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
+        fence_proxy_async();
         mbar_expect_tx(bar, (uint32_t)L::in_bytes);
         // element (x0 - HX, y0 - 3) is column x0, row y0 + HY - 3 in memory
-        tma_load_3d(smem, &tin, x0, y0 + HY - 3, 0, bar);
+        tma_load_3d(smem, tin, x0, y0 + HY - 3, 0, bar);
     }
     // geometry frame; rows beyond a wall edge are outside
     for (int k = tid; k < L::GYH * (GXW / 4); k += NT) {
@@ -130,20 +129,23 @@ __global__ void __launch_bounds__(TX *TY, 2)
     auto geo_s = [&](int r, int c) -> uint8_t { return geo[r * GXW + c]; };
 
     // ---- work lists ---------------------------------------------------------
-    // L1: fluid positions of the 2-ring around the tile (the tile's own
-    // nodes are pulled by the threads that collide them, L3)
+    // L1: fluid positions of the density frame that no collision thread
+    // pulls: the 2-ring, and in a ragged edge tile the positions past the
+    // lattice edge (periodic images whose densities the edge nodes need).
+    // The tile's own nodes are pulled by the threads that collide them (L3).
     for (int base = warp * 32; base < L::N1; base += NT) {
         const int k = base + lane;
         bool f = false;
         if (k < L::N1) {
             const int dr = k / DXW, dc = k % DXW;
-            const bool inner = dr >= 2 && dr < TY + 2 && dc >= 2 && dc < TX + 2;
+            const bool own = dr >= 2 && dr < TY + 2 && dc >= 2 && dc < TX + 2 &&
+                             x0 - 2 + dc < g.nx && y0 - 2 + dr < g.ny;
             const bool fl = geo_s(dr + 1, dc + 2) == GEO_FLUID;
-            if (!fl || inner) {
+            if (!fl || own) {
                 rho[k] = R(0);
                 rho[L::N1 + k] = R(0);
             }
-            f = fl && !inner;
+            f = fl && !own;
         }
         list_append(f, (uint16_t)k, l1, &cnt[0]);
     }
@@ -169,10 +171,10 @@ __global__ void __launch_bounds__(TX *TY, 2)
         list_append(f, (uint16_t)k, l3, &cnt[2]);
     }
 
-    const bool bad = !mbar_wait(bar, 0, WAIT_LIMIT_NS);
+    const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
     if (__syncthreads_or(bad)) {
         if (tid == 0) atomicExch(a.err, MCLBM_ERR_TIMEOUT);
-        return;
+        return false;
     }
 
     // populations of the node at staged row r, column c (geometry row r,
@@ -326,15 +328,63 @@ __global__ void __launch_bounds__(TX *TY, 2)
     if (tid == 0) {
         // element (x0, y0) is column hx + x0, row HY + y0; the store map's
         // extent ends at the lattice edge, so ghost columns and rows are kept
-        tma_store_3d(&tout, g.hx + x0, HY + y0, 0, out);
+        tma_store_3d(tout, g.hx + x0, HY + y0, 0, out);
         bulk_commit();
         bulk_wait_read();
+    }
+    return true;
+}
+
+template <class P, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 2)
+    tma_tile_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                    const StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TileLayout<P, TX, TY>::bar_off);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    tma_tile_body<P, TX, TY>(&tin, &tout, a, blockIdx.x, blockIdx.y, 0, smem);
+}
+
+// Many lattices in one persistent launch: CTAs walk a work list of
+// (lattice, tile) items; every lattice's arguments and tensor descriptors
+// travel in the kernel parameters.
+struct BatchArgs {
+    int ncases, total;
+    int tiles_x[MAX_BATCH];
+    int first[MAX_BATCH + 1];  // first work item of each lattice
+    StepArgs a[MAX_BATCH];
+    CUtensorMap tin[MAX_BATCH];
+    CUtensorMap tout[MAX_BATCH];
+};
+
+template <class P, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 2) tma_batch_kernel(const __grid_constant__ BatchArgs b) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + TileLayout<P, TX, TY>::bar_off);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t parity = 0;
+    for (int w = blockIdx.x; w < b.total; w += gridDim.x) {
+        int c = 0;
+        while (c + 1 < b.ncases && w >= b.first[c + 1]) ++c;
+        const int t = w - b.first[c];
+        if (!tma_tile_body<P, TX, TY>(&b.tin[c], &b.tout[c], b.a[c], t % b.tiles_x[c],
+                                      t / b.tiles_x[c], parity, smem))
+            return;
+        parity ^= 1u;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Host side: tensor descriptors and launch.
 // ---------------------------------------------------------------------------
+static_assert(sizeof(BatchArgs) < 32000, "batch arguments must fit the kernel parameter space");
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -360,14 +410,12 @@ struct TileShape {
     int tx, ty, hx;
 };
 
-TileShape shape_of(mclbm_precision p) {
-    switch (p) {
-        case MCLBM_FP32: return {32, 16, 4};
-        case MCLBM_FP32_DEV: return {32, 12, 4};
-        case MCLBM_FP16_DEV:
-        case MCLBM_BF16_DEV: return {32, 16, 8};
-        default: return {0, 0, 0};
-    }
+// shape 0: the default tile of each precision; shape 1: 32 x 8
+TileShape shape_of(mclbm_precision p, int shape = 0) {
+    const int hx = (p == MCLBM_FP16_DEV || p == MCLBM_BF16_DEV) ? 8 : 4;
+    if (p == MCLBM_FP64) return {0, 0, 0};
+    if (shape == 1) return {32, 8, hx};
+    return {32, p == MCLBM_FP32_DEV ? 12 : 16, hx};
 }
 
 CUtensorMapDataType dtype_of(mclbm_precision p) {
@@ -403,13 +451,12 @@ cudaError_t launch_tma_cfg(Lattice &L, const StepArgs &a) {
 
 bool tma_supported(const Lattice &L) { return L.tmaps != nullptr; }
 
-int tma_prepare(Lattice &L) {
-    const TileShape sh = shape_of(L.prec);
-    if (sh.tx == 0) return MCLBM_OK;  // not offered for this precision
+// Input and output descriptors of both population buffers for a tile shape:
+// maps[2 b] input of buffer b, maps[2 b + 1] output into buffer b.
+int encode_tile_maps(const Lattice &L, int shape, CUtensorMap *maps) {
+    const TileShape sh = shape_of(L.prec, shape);
     EncodeTiledFn enc = encode_fn();
-    if (!enc) return MCLBM_OK;        // no driver entry point: other kernels serve
-    CUtensorMap *maps = new (std::nothrow) CUtensorMap[4];
-    if (!maps) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
+    if (sh.tx == 0 || !enc) return fail(MCLBM_ERR_STATE, "TMA descriptors not available");
     const cuuint64_t sb = L.store_bytes;
     for (int b = 0; b < 2; ++b) {
         // input: the whole padded array, box = tile + 3-node ring, all planes
@@ -430,15 +477,77 @@ int tma_prepare(Lattice &L) {
         CUresult r2 = enc(&maps[2 * b + 1], dtype_of(L.prec), 3, L.f[b], dim_out, stride, box_out,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
-            delete[] maps;
+        if (r != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
             return fail(MCLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed (" +
                                             std::to_string((int)r) + ", " +
                                             std::to_string((int)r2) + ")");
-        }
+    }
+    return MCLBM_OK;
+}
+
+int tma_prepare(Lattice &L) {
+    if (shape_of(L.prec).tx == 0 || !encode_fn()) return MCLBM_OK;  // other kernels serve
+    CUtensorMap *maps = new (std::nothrow) CUtensorMap[4];
+    if (!maps) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
+    if (int rc = encode_tile_maps(L, 0, maps)) {
+        delete[] maps;
+        return rc;
     }
     L.tmaps = maps;
     return MCLBM_OK;
+}
+
+size_t tile_maps_bytes() { return 4 * sizeof(CUtensorMap); }
+
+int tile_maps_for(const Lattice &L, int shape, void *out) {
+    return encode_tile_maps(L, shape, static_cast<CUtensorMap *>(out));
+}
+
+template <class P, int TX, int TY>
+cudaError_t launch_batch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, int grid,
+                             cudaStream_t stream, int *slots_out) {
+    using Lay = TileLayout<P, TX, TY>;
+    static int slots = 0;
+    if (slots == 0) {
+        cudaError_t e = cudaFuncSetAttribute(tma_batch_kernel<P, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Lay::total);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_batch_kernel<P, TX, TY>, TX * TY,
+                                                      Lay::total);
+        slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
+    }
+    if (slots_out) *slots_out = slots;
+    if (!cases) return cudaSuccess;  // query only
+    static BatchArgs b;  // host staging of the parameter block
+    std::memset(&b, 0, sizeof(b));
+    b.ncases = n;
+    int total = 0;
+    for (int c = 0; c < n; ++c) {
+        const Lattice &L = *cases[c];
+        b.tiles_x[c] = (L.nx + TX - 1) / TX;
+        b.first[c] = total;
+        total += b.tiles_x[c] * ((L.ny + TY - 1) / TY);
+        StepArgs &a = b.a[c];
+        a.g = L.geometry();
+        a.p = L.p;
+        a.fin = L.f[L.cur];
+        a.fout = L.f[1 - L.cur];
+        a.d5 = L.d5;
+        a.err = L.err;
+        a.rows_per_cta = 0;
+        b.tin[c] = maps[4 * c + 2 * L.cur];
+        b.tout[c] = maps[4 * c + 2 * (1 - L.cur) + 1];
+    }
+    b.first[n] = total;
+    b.total = total;
+    const int g = grid > 0 ? (grid < total ? grid : total) : (slots < total ? slots : total);
+    tma_batch_kernel<P, TX, TY><<<g, TX * TY, Lay::total, stream>>>(b);
+    count_launch();
+    return cudaGetLastError();
 }
 
 void tma_release(Lattice &L) {
@@ -464,6 +573,67 @@ cudaError_t launch_step_tma(Lattice &L) {
         default: return cudaErrorInvalidValue;
     }
     if (e == cudaSuccess) L.cur = 1 - L.cur;
+    return e;
+}
+
+}  // namespace mclbm
+
+namespace mclbm {
+
+int batch_slots(mclbm_precision p, int shape) {
+    int slots = 0;
+    switch (p) {
+        case MCLBM_FP32:
+            shape ? launch_batch_cfg<P32, 32, 8>(nullptr, 0, nullptr, 0, 0, &slots)
+                  : launch_batch_cfg<P32, 32, 16>(nullptr, 0, nullptr, 0, 0, &slots);
+            break;
+        case MCLBM_FP32_DEV:
+            shape ? launch_batch_cfg<P32D, 32, 8>(nullptr, 0, nullptr, 0, 0, &slots)
+                  : launch_batch_cfg<P32D, 32, 12>(nullptr, 0, nullptr, 0, 0, &slots);
+            break;
+        case MCLBM_FP16_DEV:
+            shape ? launch_batch_cfg<P16D, 32, 8>(nullptr, 0, nullptr, 0, 0, &slots)
+                  : launch_batch_cfg<P16D, 32, 16>(nullptr, 0, nullptr, 0, 0, &slots);
+            break;
+        case MCLBM_BF16_DEV:
+            shape ? launch_batch_cfg<PB16D, 32, 8>(nullptr, 0, nullptr, 0, 0, &slots)
+                  : launch_batch_cfg<PB16D, 32, 16>(nullptr, 0, nullptr, 0, 0, &slots);
+            break;
+        default: break;
+    }
+    return slots;
+}
+
+// One persistent launch advancing every lattice of a batch by one step
+// (all share the precision and are at the same buffer parity).  grid <= 0
+// means one CTA per resident slot.
+cudaError_t launch_step_batch(Lattice *const *cases, int n, const void *maps, int shape, int grid,
+                              cudaStream_t stream) {
+    if (n < 1 || n > MAX_BATCH) return cudaErrorInvalidValue;
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(maps);
+    cudaError_t e;
+    const mclbm_precision p = cases[0]->prec;
+    switch (p) {
+        case MCLBM_FP32:
+            e = shape ? launch_batch_cfg<P32, 32, 8>(cases, n, m, grid, stream, nullptr)
+                      : launch_batch_cfg<P32, 32, 16>(cases, n, m, grid, stream, nullptr);
+            break;
+        case MCLBM_FP32_DEV:
+            e = shape ? launch_batch_cfg<P32D, 32, 8>(cases, n, m, grid, stream, nullptr)
+                      : launch_batch_cfg<P32D, 32, 12>(cases, n, m, grid, stream, nullptr);
+            break;
+        case MCLBM_FP16_DEV:
+            e = shape ? launch_batch_cfg<P16D, 32, 8>(cases, n, m, grid, stream, nullptr)
+                      : launch_batch_cfg<P16D, 32, 16>(cases, n, m, grid, stream, nullptr);
+            break;
+        case MCLBM_BF16_DEV:
+            e = shape ? launch_batch_cfg<PB16D, 32, 8>(cases, n, m, grid, stream, nullptr)
+                      : launch_batch_cfg<PB16D, 32, 16>(cases, n, m, grid, stream, nullptr);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess)
+        for (int c = 0; c < n; ++c) cases[c]->cur = 1 - cases[c]->cur;
     return e;
 }
 

@@ -37,6 +37,14 @@ MCLBM_FLAG_KERNEL = 3
 DIAG_FIELDS = ("mass1", "mass2", "sw_count", "sw_mass", "p_in", "p_out", "pc", "n_fluid")
 
 
+class CaseDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("solid", C.c_void_p), ("xi", C.c_void_p),
+                ("nu1", C.c_double), ("nu2", C.c_double), ("g_coh", C.c_double),
+                ("g_ads", C.c_double), ("gx", C.c_double), ("gy", C.c_double),
+                ("rho_in1", C.c_double), ("rho_out2", C.c_double), ("periodic_y", C.c_int),
+                ("rho1", C.c_void_p), ("rho2", C.c_void_p)]
+
+
 class MclbmError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"mclbm error {code}: {msg}")
@@ -72,6 +80,12 @@ _SIGS = {
     "mclbm_capillary_pressure": (C.c_int, [_vp, _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
     "mclbm_mass": (C.c_int, [_vp, _vp]),
     "mclbm_info": (C.c_int, [_vp, _vp]),
+    "mclbm_batch_create": (C.c_int, [C.c_int, _vp, C.c_int, _vp, _P(_vp)]),
+    "mclbm_batch_destroy": (C.c_int, [_vp]),
+    "mclbm_batch_lattice": (C.c_int, [_vp, C.c_int, _P(_vp)]),
+    "mclbm_batch_step": (C.c_int, [_vp, _i64]),
+    "mclbm_batch_info": (C.c_int, [_vp, _vp]),
+    "mclbm_batch_tuning": (C.c_int, [_vp, _vp]),
     "mclbm_diagnostics_noalloc": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_int,
                                             _vp, _vp]),
     "mclbm_launch_count": (_i64, []),
@@ -261,6 +275,61 @@ def mclbm_diagnostics_noalloc(f, solid, nx: int, ny: int, g_coh: float, periodic
                                             _addr(out, np.float64), _stream_handle(stream)))
 
 
+def mclbm_batch_create(cases: list[dict], prec: int = MCLBM_FP32, stream=None):
+    """cases: dicts with solid, xi, nu1, nu2, g_coh, g_ads, gx, gy, rho_in1,
+    rho_out2, periodic_y, rho1, rho2 (numpy host arrays)."""
+    lib = load()
+    keep = []
+    arr = (CaseDesc * len(cases))()
+    for d, c in zip(arr, cases):
+        solid = np.ascontiguousarray(c["solid"], dtype=np.uint8)
+        ny, nx = solid.shape
+        xi = np.ascontiguousarray(c.get("xi", np.zeros((ny, nx))), dtype=np.float32)
+        r1 = np.ascontiguousarray(c["rho1"], dtype=np.float64)
+        r2 = np.ascontiguousarray(c["rho2"], dtype=np.float64)
+        keep += [solid, xi, r1, r2]
+        d.nx, d.ny = nx, ny
+        d.solid, d.xi = solid.ctypes.data, xi.ctypes.data
+        d.nu1, d.nu2 = c.get("nu1", 1 / 6), c.get("nu2", 1 / 6)
+        d.g_coh = c.get("g_coh", 3.5)
+        d.g_ads = c.get("g_ads", d.g_coh)
+        d.gx, d.gy = c.get("gx", 0.0), c.get("gy", 0.0)
+        d.rho_in1, d.rho_out2 = c.get("rho_in1", -1.0), c.get("rho_out2", -1.0)
+        d.periodic_y = int(c.get("periodic_y", False))
+        d.rho1, d.rho2 = r1.ctypes.data, r2.ctypes.data
+    h = _vp()
+    _check(lib.mclbm_batch_create(len(cases), C.cast(arr, _vp), int(prec),
+                                  _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def mclbm_batch_destroy(b) -> None:
+    _check(load().mclbm_batch_destroy(b))
+
+
+def mclbm_batch_lattice(b, k: int):
+    h = _vp()
+    _check(load().mclbm_batch_lattice(b, int(k), C.byref(h)))
+    return h
+
+
+def mclbm_batch_step(b, nsteps: int) -> None:
+    _check(load().mclbm_batch_step(b, int(nsteps)))
+
+
+def mclbm_batch_info(b) -> dict:
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().mclbm_batch_info(b, out.ctypes.data))
+    return dict(zip(("cases", "nodes", "shape", "grid", "graph_steps", "steps", "slots",
+                     "graph"), out.tolist()))
+
+
+def mclbm_batch_tuning(b) -> list[float]:
+    out = np.zeros(4)
+    _check(load().mclbm_batch_tuning(b, out.ctypes.data))
+    return out.tolist()
+
+
 def mclbm_launch_count() -> int:
     return int(load().mclbm_launch_count())
 
@@ -357,3 +426,17 @@ class Lattice:
 
     def info(self) -> dict:
         return mclbm_info(self.h)
+
+
+class LatticeView(Lattice):
+    """A borrowed case of a batch: parameters and read-outs, not stepping."""
+
+    def __init__(self, batch, k: int, ny: int, nx: int, prec: int):
+        self.h = mclbm_batch_lattice(batch, k)
+        self.ny, self.nx, self.prec = ny, nx, prec
+
+    def close(self) -> None:  # owned by the batch
+        self.h = None
+
+    def step(self, n: int = 1) -> None:
+        raise RuntimeError("a batch case is stepped with mclbm_batch_step")

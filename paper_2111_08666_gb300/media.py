@@ -230,3 +230,21 @@ def config_paper_scale(nx: int = 1024, ny: int = 512, seed: int = 1):
                 xi=uniform_xi(m.solid, xi), rho1=rho1, rho2=rho2,
                 nu1=(1.7 - 0.5) / 3.0, nu2=(0.62 - 0.5) / 3.0, g=3.5,
                 rho_in1=1.0, rho_out2=1.0, porosity=m.porosity)
+
+
+def config_batch(k: int):
+    """Case k (0..23) of the batched workload: disk medium of seed 10 + k,
+    size drawn from {256x256, 512x256, 512x512, 1024x256, 1024x512},
+    contact angle 30 + 120 k / 23 deg, viscosity ratio cycling 1, 10, 50
+    (tau2 = 0.62, or 0.56 at M = 50), primary drainage set-up."""
+    sizes = [(256, 256), (512, 256), (512, 512), (1024, 256), (1024, 512)]
+    nx, ny = sizes[int(np.random.default_rng(k).integers(len(sizes)))]
+    m = make_disk_medium(nx, ny, 10 + k, radius="lognormal", r_mean=10.0, sigma_log=0.4,
+                         porosity=0.6)
+    theta = 30.0 + 120.0 * k / 23.0
+    taus = [(1.0, 1.0), (1.7, 0.62), (3.5, 0.56)][k % 3]
+    rho1, rho2 = drainage_densities(m.solid)
+    return dict(name=f"batch{k}_{nx}x{ny}", nx=nx, ny=ny, solid=m.solid,
+                xi=uniform_xi(m.solid, theta_to_xi(theta)), rho1=rho1, rho2=rho2,
+                nu1=(taus[0] - 0.5) / 3.0, nu2=(taus[1] - 0.5) / 3.0, g_coh=3.5,
+                rho_in1=1.005, rho_out2=1.0, porosity=m.porosity, theta=theta)
