@@ -42,8 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per fused-step launch from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the workload below, and the hash of the kernel
 # sources they were taken with; reported only while the sources match.
-NCU_TRAFFIC = {"bytes_per_launch": None, "source_sha": None}
-KERNEL_SOURCES = ["paper_2111_08666_gb300/csrc/sweep.cu",
+NCU_TRAFFIC = {"bytes_per_launch": 260456448, "source_sha": "8949372ced97eb2b"}
+KERNEL_SOURCES = ["paper_2111_08666_gb300/csrc/tma_tile.cu",
+                  "paper_2111_08666_gb300/csrc/async_copy.cuh",
                   "paper_2111_08666_gb300/csrc/lbm_device.cuh",
                   "paper_2111_08666_gb300/csrc/lbm.cuh"]
 
@@ -249,7 +250,7 @@ def run_gpu(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": abytes,
-                     "kernel": "sweep_step_kernel", "launch_us": round(per_launch * 1e6, 3)},
+                     "kernel": "tma_tile_kernel", "launch_us": round(per_launch * 1e6, 3)},
         "e2e": {"value": round(e2e_units / e2e_job / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": round(h2d / e2e_steps, 1),
                 "d2h_bytes_per_step": round(d2h / e2e_steps, 1)},

@@ -369,7 +369,8 @@ class Lattice:
             mclbm_destroy(self.h)
             self.h = None
 
-    __del__ = close
+    def __del__(self):
+        self.close()
 
     def __enter__(self):
         return self
