@@ -73,6 +73,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int c0,
         : "memory");
 }
 
+// 2-D tiled tensor copy global -> shared (coordinates innermost first)
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 3-D tiled tensor copy shared -> global (clipped at the tensor bounds)
 __device__ __forceinline__ void tma_store_3d(const void *tmap, int c0, int c1, int c2,
                                              const void *src) {

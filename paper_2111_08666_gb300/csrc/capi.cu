@@ -105,6 +105,7 @@ void release(Lattice *L) {
     cudaFree(L->diag_out);
     cudaFree(L->bad_flag);
     cudaFree(L->err);
+    cudaFree(L->geo_pad);
     tma_release(*L);
     if (L->host_diag) cudaFreeHost(L->host_diag);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
@@ -268,6 +269,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         L->own_stream = true;
     }
     const size_t geo_bytes = (size_t)L->gpitch * ny;
+    L->geo_pad_rows = ny + 2 * HY + 16;  // room for the deepest tile frame past the edge
     const size_t pop_bytes = (size_t)L->planes * (size_t)L->plane * L->store_bytes;
     int rc = MCLBM_OK;
     L->diag_blocks = diag_blocks_for(*L);
@@ -276,6 +278,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         (rc = dev_alloc(*L, &L->f[0], pop_bytes)) ||
         (rc = dev_alloc(*L, &L->f[1], pop_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->err, sizeof(int))) ||
+        (rc = dev_alloc(*L, (void **)&L->geo_pad, (size_t)L->geo_pad_rows * L->gpitch)) ||
         (rc = dev_alloc(*L, &L->d5, 3 * (size_t)ny * L->real_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->diag_partial, (size_t)L->diag_blocks * 9 * sizeof(double))) ||
         (rc = dev_alloc(*L, (void **)&L->diag_out, 8 * sizeof(double))) ||

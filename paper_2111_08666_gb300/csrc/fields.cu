@@ -120,6 +120,20 @@ __global__ void pop_ghost_rows_kernel(Geometry g, typename P::store_t *f) {
     }
 }
 
+// Padded copy of the geometry for the tensor copies of the tile kernel:
+// row r holds lattice row r - HY (ghost columns included); rows beyond the
+// lattice repeat the opposite edge when y is periodic and are outside
+// otherwise, as are the spare rows at the end.
+__global__ void geo_pad_kernel(Geometry g, uint8_t *pad, int rows, int periodic_y) {
+    const int r = blockIdx.x;
+    const int y = r - HY;
+    int src = -1;
+    if (y >= 0 && y < g.ny) src = y;
+    else if (periodic_y && y >= -HY && y < g.ny + HY) src = pmod(y, g.ny);
+    for (int c = threadIdx.x; c < g.gpitch; c += blockDim.x)
+        pad[(long long)r * g.gpitch + c] = src >= 0 ? g.geo[(long long)src * g.gpitch + c] : GEO_OUTSIDE;
+}
+
 template <class P>
 __device__ __forceinline__ void node_rho(const Geometry &g, const typename P::store_t *f,
                                          long long site, typename P::real_t &r1,
@@ -466,6 +480,12 @@ cudaError_t launch_geo_ghosts(Lattice &L) {
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (L.geo_pad) {
+        geo_pad_kernel<<<L.geo_pad_rows, 128, 0, L.stream>>>(geometry_of(L), L.geo_pad,
+                                                             L.geo_pad_rows, L.p.periodic_y);
+        count_launch();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const Geometry g = geometry_of(L);
     return dispatch(L, [&](auto tag) {
         using P = decltype(tag);

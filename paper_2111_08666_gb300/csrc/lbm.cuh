@@ -139,6 +139,8 @@ struct Lattice {
     bool own_stream = false;
     int device = 0;
     uint8_t *geo = nullptr;    // [ny][gpitch]
+    uint8_t *geo_pad = nullptr;  // [geo_pad_rows][gpitch]: rows -HY.. of the geometry,
+    int geo_pad_rows = 0;        // ghost rows per the y mode, outside beyond
     int ghost_mode = -1;       // boundary mode the ghosts were built for
     double *chi = nullptr;     // [256][2]
     void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
