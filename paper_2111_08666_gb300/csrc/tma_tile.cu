@@ -21,7 +21,10 @@
 //           the forced collision (Eqs. 1, 2, 11) into an output tile
 // and one tensor copy stores the output tile (whole 32-byte sectors, so no
 // partially written sector is fetched first).  Ghost images of edge nodes
-// are stored directly.
+// are stored directly.  The store's extent ends at the last whole 16-byte
+// chunk of a lattice row: a tensor store clipped inside a chunk was seen to
+// write the rest of that chunk, which at a periodic edge is a ghost column
+// another CTA fills, so the few columns past that chunk go by plain stores.
 #include <cuda.h>
 
 #include <cstring>
@@ -74,6 +77,12 @@ struct TileLayout {
     static_assert(GXW % 16 == 0 && geo_bytes % 16 == 0, "geometry box rows must be 16-byte chunks");
     static_assert(HX >= 3, "halo must cover the stencil reach");
 };
+
+// Columns [0, store_cols) of a population row go by the tensor store: the
+// row up to the last whole 16-byte chunk that ends inside the lattice.
+__host__ __device__ constexpr int store_cols(int hx, int nx, int elem_bytes) {
+    return (hx + nx) / (16 / elem_bytes) * (16 / elem_bytes);
+}
 
 // Append val to a shared list when flag is set; all 32 lanes of the warp
 // must call it together.
@@ -357,14 +366,16 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
                     out[(9 + i) * OSTR + o] = from_real<S>(f[1][i]);
                 }
             }
+            if (g.hx + x >= store_cols(g.hx, g.nx, sizeof(S)))
+                pop_store_site<P>(static_cast<S *>(a.fout), g.plane, site_of(g, x, y), f, rho1, rho2);
             pop_store_ghosts<P>(g, a.p, static_cast<S *>(a.fout), x, y, f, rho1, rho2);
         }
         // make the generic-proxy writes of the output tile visible to the copy engine
         fence_proxy_async();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && g.hx + x0 < store_cols(g.hx, g.nx, sizeof(S))) {
             // element (x0, y0) is column hx + x0, row HY + y0; the store map's
-            // extent ends at the lattice edge, so ghost columns and rows are kept
+            // extent ends inside the lattice, so ghost columns and rows are kept
             tma_store_3d(&b.tout[c], g.hx + x0, HY + y0, 0, out);
             bulk_commit();
         }
@@ -514,10 +525,10 @@ int encode_tile_maps(const Lattice &L, int shape, void *out) {
         CUresult r = enc(&maps[2 * b], dtype_of(L.prec), 3, L.f[b], dim_in, stride, box_in, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        // output: extent ends at the lattice edge so the store never writes
-        // ghost columns or rows; box = the tile, all planes
-        const cuuint64_t dim_out[3] = {(cuuint64_t)(L.hx + L.nx), (cuuint64_t)(HY + L.ny),
-                                       (cuuint64_t)L.planes};
+        // output: extent ends inside the lattice (at a 16-byte chunk) so the
+        // store never writes ghost columns or rows; box = the tile, all planes
+        const cuuint64_t dim_out[3] = {(cuuint64_t)store_cols(L.hx, L.nx, (int)sb),
+                                       (cuuint64_t)(HY + L.ny), (cuuint64_t)L.planes};
         const cuuint32_t box_out[3] = {(cuuint32_t)sh.tx, (cuuint32_t)sh.ty, (cuuint32_t)L.planes};
         CUresult r2 = enc(&maps[2 * b + 1], dtype_of(L.prec), 3, L.f[b], dim_out, stride, box_out,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
