@@ -98,6 +98,7 @@ void release(Lattice *L) {
     cudaSetDevice(L->device);
     cudaFree(L->geo);
     cudaFree(L->chi);
+    cudaFree(L->chi_f);
     cudaFree(L->f[0]);
     cudaFree(L->f[1]);
     cudaFree(L->d5);
@@ -141,6 +142,7 @@ int refresh_ghosts(Lattice &L) {
     if (L.ghost_mode == L.ghost_key()) return MCLBM_OK;
     cudaError_t e = launch_geo_ghosts(L);
     if (e != cudaSuccess) return cuda_fail(e, "ghost columns");
+    if (int rc = tma_build_tables(L)) return rc;
     L.ghost_mode = L.ghost_key();
     return MCLBM_OK;
 }
@@ -257,6 +259,8 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
             geo[(size_t)y * L->gpitch + GEO_HX + x] = c;
         }
     L->boundary_rows_solid = rows_solid;
+    std::vector<float> chi_f(chi.begin(), chi.end());  // round to nearest, as on the device
+    L->p.round_fp32();
 
     if (cuda_stream) {
         L->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -275,6 +279,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
     L->diag_blocks = diag_blocks_for(*L);
     if ((rc = dev_alloc(*L, (void **)&L->geo, geo_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->chi, 512 * sizeof(double))) ||
+        (rc = dev_alloc(*L, (void **)&L->chi_f, 512 * sizeof(float))) ||
         (rc = dev_alloc(*L, &L->f[0], pop_bytes)) ||
         (rc = dev_alloc(*L, &L->f[1], pop_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->err, sizeof(int))) ||
@@ -300,6 +305,8 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
     }
     if ((e = cudaMemcpyAsync(L->geo, geo.data(), geo_bytes, cudaMemcpyHostToDevice, L->stream)) ||
         (e = cudaMemcpyAsync(L->chi, chi.data(), 512 * sizeof(double), cudaMemcpyHostToDevice,
+                             L->stream)) ||
+        (e = cudaMemcpyAsync(L->chi_f, chi_f.data(), 512 * sizeof(float), cudaMemcpyHostToDevice,
                              L->stream)) ||
         (e = cudaMemsetAsync(L->f[0], 0, pop_bytes, L->stream)) ||
         (e = cudaMemsetAsync(L->f[1], 0, pop_bytes, L->stream)) ||
@@ -353,6 +360,7 @@ int mclbm_set_viscosity(mclbm_lattice *lat, double nu1, double nu2) {
         return fail(MCLBM_ERR_ARG, "viscosities must be positive and finite");
     lat->p.nu1 = nu1;
     lat->p.nu2 = nu2;
+    lat->p.round_fp32();
     ++lat->version;
     return MCLBM_OK;
 }
@@ -363,6 +371,7 @@ int mclbm_set_coupling(mclbm_lattice *lat, double g_coh, double g_ads) {
         return fail(MCLBM_ERR_ARG, "coupling strengths must be finite");
     lat->p.g_coh = g_coh;
     lat->p.g_ads = g_ads;
+    lat->p.round_fp32();
     ++lat->version;
     return MCLBM_OK;
 }
@@ -372,6 +381,7 @@ int mclbm_set_body_force(mclbm_lattice *lat, double gx, double gy) {
     if (!std::isfinite(gx) || !std::isfinite(gy)) return fail(MCLBM_ERR_ARG, "g must be finite");
     lat->p.gx = gx;
     lat->p.gy = gy;
+    lat->p.round_fp32();
     ++lat->version;
     return MCLBM_OK;
 }
@@ -384,6 +394,7 @@ int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2) {
     if (rho_in1 < 0 || rho_out2 < 0) {
         lat->p.open_x = 0;
         lat->p.rho_in1 = lat->p.rho_out2 = -1.0;
+        lat->p.round_fp32();
         return MCLBM_OK;
     }
     if (rho_in1 == 0 || rho_out2 == 0)
@@ -391,6 +402,7 @@ int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2) {
     lat->p.open_x = 1;
     lat->p.rho_in1 = rho_in1;
     lat->p.rho_out2 = rho_out2;
+    lat->p.round_fp32();
     return MCLBM_OK;
 }
 

@@ -345,8 +345,8 @@ __global__ void vel_psi_kernel(Geometry g, Params p, const R *rho, R *psi) {
     }
     R s1 = 0, s2 = 0;
     if (den > R(0)) {
-        s1 = R(g.chi[2 * code]) * n1 / den;
-        s2 = R(g.chi[2 * code + 1]) * n2 / den;
+        s1 = chi_at<R>(g, 2 * code) * n1 / den;
+        s2 = chi_at<R>(g, 2 * code + 1) * n2 / den;
     }
     psi[k] = s1;
     psi[n + k] = s2;
@@ -399,7 +399,7 @@ __global__ void vel_final_kernel(Geometry g, Params p, const typename P::store_t
     const R Fx = fx1 + fx2, Fy = fy1 + fy2;
     R c = R(0.5);
     if (!p.vel_shift) {
-        const R tau = (r1 * R(p.nu1) + r2 * R(p.nu2)) * R(3) / rho_t + R(0.5);
+        const R tau = (r1 * par<R>(p.nu1, p.nu1_f) + r2 * par<R>(p.nu2, p.nu2_f)) * R(3) / rho_t + R(0.5);
         c = R(1) - R(0.5) / tau;
     }
     ux_out[k] = (double)((jx - c * Fx) / rho_t);

@@ -88,7 +88,27 @@ struct Params {
     int open_x = 0;      // Set-3 boundaries on at x = 0 and x = nx-1
     int periodic_y = 0;  // else rows 0 and ny-1 must be solid
     int vel_shift = 1;   // u carries F/2
+    // the same values rounded to FP32 once on the host: the FP32 kernels
+    // read these rather than converting from FP64 at every node (such a
+    // conversion occupies the narrow FP64 pipe)
+    float nu1_f = 0, nu2_f = 0, g_coh_f = 0, g_ads_f = 0, gx_f = 0, gy_f = 0;
+    float rho_in1_f = 0, rho_out2_f = 0;
+    void round_fp32() {
+        nu1_f = (float)nu1;
+        nu2_f = (float)nu2;
+        g_coh_f = (float)g_coh;
+        g_ads_f = (float)g_ads;
+        gx_f = (float)gx;
+        gy_f = (float)gy;
+        rho_in1_f = (float)rho_in1;
+        rho_out2_f = (float)rho_out2;
+    }
 };
+
+// A parameter in the arithmetic type R: the FP64 value, or its FP32 copy.
+template <class R> __device__ __forceinline__ R par(double d, float f);
+template <> __device__ __forceinline__ double par<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float par<float>(double, float f) { return f; }
 
 // Memory layout shared by every kernel.  Population (c, i, y, x) lives at
 // f[(c*9 + i) * plane + (y + HY) * pitch + hx + x]; columns -hx..-1 and
@@ -108,7 +128,17 @@ struct Geometry {
     int gpitch;                // geometry row stride, bytes
     const uint8_t *geo;        // [ny][gpitch], column x at GEO_HX + x
     const double *chi;         // [256][2] (1 + xi, 1 - xi) by code, in FP64
+    const float *chi_f;        // the same table rounded to FP32
 };
+
+// wetting factor k of the chi table in the arithmetic type R
+template <class R> __device__ __forceinline__ R chi_at(const Geometry &g, int k);
+template <> __device__ __forceinline__ double chi_at<double>(const Geometry &g, int k) {
+    return g.chi[k];
+}
+template <> __device__ __forceinline__ float chi_at<float>(const Geometry &g, int k) {
+    return g.chi_f[k];
+}
 
 struct StepArgs {
     Geometry g;
@@ -143,6 +173,7 @@ struct Lattice {
     int geo_pad_rows = 0;        // ghost rows per the y mode, outside beyond
     int ghost_mode = -1;       // boundary mode the ghosts were built for
     double *chi = nullptr;     // [256][2]
+    float *chi_f = nullptr;    // [256][2], rounded to FP32
     void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
     int cur = 0;               // index of the buffer holding the state
     void *d5 = nullptr;        // [3][ny] real type
@@ -159,10 +190,16 @@ struct Lattice {
     bool boundary_rows_solid = false;
     bool initialised = false;
     void *tmaps = nullptr;     // host copies of the TMA descriptors (tile kernel)
+    // work tables of the tile kernel, per tile shape: for every tile a
+    // header and the packed entries of its fluid nodes, ring pulls and ring
+    // solids; rebuilt with the ghosts whenever the boundary mode changes
+    uint32_t *tab[2] = {nullptr, nullptr};
+    int tab_words[2] = {0, 0};  // words copied per tile (largest table, 16-byte multiple)
+    int *tab_max = nullptr;     // device scratch of the table build
     uint64_t version = 0;      // bumped whenever a parameter changes
     int ghost_key() const { return p.open_x * 2 + p.periodic_y; }
     Geometry geometry() const {
-        return Geometry{nx, ny, pitch, hx, plane, gpitch, geo, chi};
+        return Geometry{nx, ny, pitch, hx, plane, gpitch, geo, chi, chi_f};
     }
 };
 
@@ -179,6 +216,7 @@ bool sweep_supported(const Lattice &L);
 cudaError_t launch_step_tma(Lattice &L);
 bool tma_supported(const Lattice &L);
 int tma_prepare(Lattice &L);      // builds the TMA descriptors; MCLBM_OK or error
+int tma_build_tables(Lattice &L); // work tables for the current boundary mode (synchronises)
 void tma_release(Lattice &L);
 // batched persistent launch over several lattices (tma_tile.cu)
 constexpr int MAX_BATCH = 32;

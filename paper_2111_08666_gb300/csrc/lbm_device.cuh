@@ -117,7 +117,7 @@ template <class R, class Own>
 __device__ __forceinline__ void apply_set3(const StepArgs &a, int x, int y, Own own, R f[2][9]) {
     if (!a.p.open_x) return;
     if (x == 0) {
-        const R rin = R(a.p.rho_in1);
+        const R rin = par<R>(a.p.rho_in1, a.p.rho_in1_f);
         const R ux = R(1) - (f[0][0] + f[0][2] + f[0][4] + R(2) * (f[0][3] + f[0][6] + f[0][7])) / rin;
         const R d24 = R(0.5) * (f[0][2] - f[0][4]);
         const R ru6 = rin * ux * (R(1) / R(6));
@@ -129,7 +129,7 @@ __device__ __forceinline__ void apply_set3(const StepArgs &a, int x, int y, Own 
         f[1][8] = own(1, 8);
     }
     if (x == a.g.nx - 1) {
-        const R rout = R(a.p.rho_out2);
+        const R rout = par<R>(a.p.rho_out2, a.p.rho_out2_f);
         const R ux = R(-1) + (f[1][0] + f[1][2] + f[1][4] + R(2) * (f[1][1] + f[1][5] + f[1][8])) / rout;
         const R d24 = R(0.5) * (f[1][2] - f[1][4]);
         const R ru6 = rout * ux * (R(1) / R(6));
@@ -182,35 +182,54 @@ __device__ __forceinline__ void pull_node(const StepArgs &a, int x, int y, SrcGe
     apply_set3<R>(a, x, y, [&](int c, int i) { return pop_load<P>(fin, plane, c, i, site); }, f);
 }
 
+// e_i . (vx, vy) without multiplications by 0 or 1 (i is a constant in the
+// unrolled loops, so this folds to at most one add)
+template <class R>
+__device__ __forceinline__ R edot(int i, R vx, R vy) {
+    R v = R(0);
+    if (ex(i) > 0) v = vx;
+    if (ex(i) < 0) v = -vx;
+    if (ey(i) > 0) v = ex(i) ? v + vy : vy;
+    if (ey(i) < 0) v = ex(i) ? v - vy : -vy;
+    return v;
+}
+
 // Interaction force on both components at a fluid node (Eqs. 12, 13, 15):
 // F^s = -rho^s [G_coh sum_fluid w_i psi^sb(x+e_i) e_i
 //              + G_ads sum_solid w_i s^sb(x+e_i) e_i] + rho^s g.
-// nb(i, &code, &psi1, &psi2) returns the neighbour used for direction i
-// (already mirrored at an open end).
-template <class R, class Nb>
+// Both sums are taken as one, each neighbour weighted by G_coh w_i or
+// G_ads w_i.  nb(i, &code, &psi1, &psi2) returns the neighbour used for
+// direction i (already mirrored at an open end); with OUTSIDE = false the
+// caller guarantees that no neighbour is outside the lattice.
+template <class R, bool OUTSIDE = true, class Nb>
 __device__ __forceinline__ void node_force(const Params &p, R rho1, R rho2, Nb nb,
                                            R &fx1, R &fy1, R &fx2, R &fy2) {
-    R cx1 = 0, cy1 = 0, cx2 = 0, cy2 = 0;  // cohesion sums over psi of the other component
-    R ax1 = 0, ay1 = 0, ax2 = 0, ay2 = 0;  // adhesion sums
+    const R gc = par<R>(p.g_coh, p.g_coh_f), ga = par<R>(p.g_ads, p.g_ads_f);
+    const R gc_a = gc * wgt<R>(1), gc_d = gc * wgt<R>(5);  // axis and diagonal weights
+    const R ga_a = ga * wgt<R>(1), ga_d = ga * wgt<R>(5);
+    R sx1 = 0, sy1 = 0, sx2 = 0, sy2 = 0;  // sums over psi (or s) of the other component
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         uint8_t code;
         R s1, s2;
         nb(i, code, s1, s2);
-        const R w = wgt<R>(i);
-        if (code == GEO_FLUID) {
-            if (ex(i)) { cx1 += R(ex(i)) * w * s2; cx2 += R(ex(i)) * w * s1; }
-            if (ey(i)) { cy1 += R(ey(i)) * w * s2; cy2 += R(ey(i)) * w * s1; }
-        } else if (code != GEO_OUTSIDE) {
-            if (ex(i)) { ax1 += R(ex(i)) * w * s2; ax2 += R(ex(i)) * w * s1; }
-            if (ey(i)) { ay1 += R(ey(i)) * w * s2; ay2 += R(ey(i)) * w * s1; }
+        const bool diag = i >= 5;
+        const R k = code == GEO_FLUID ? (diag ? gc_d : gc_a) : (diag ? ga_d : ga_a);
+        R a1 = k * s2, a2 = k * s1;
+        if (OUTSIDE && code == GEO_OUTSIDE) a1 = a2 = R(0);
+        if (ex(i)) {
+            sx1 = ex(i) > 0 ? sx1 + a1 : sx1 - a1;
+            sx2 = ex(i) > 0 ? sx2 + a2 : sx2 - a2;
+        }
+        if (ey(i)) {
+            sy1 = ey(i) > 0 ? sy1 + a1 : sy1 - a1;
+            sy2 = ey(i) > 0 ? sy2 + a2 : sy2 - a2;
         }
     }
-    const R gc = R(p.g_coh), ga = R(p.g_ads);
-    fx1 = -rho1 * (gc * cx1 + ga * ax1) + rho1 * R(p.gx);
-    fy1 = -rho1 * (gc * cy1 + ga * ay1) + rho1 * R(p.gy);
-    fx2 = -rho2 * (gc * cx2 + ga * ax2) + rho2 * R(p.gx);
-    fy2 = -rho2 * (gc * cy2 + ga * ay2) + rho2 * R(p.gy);
+    fx1 = rho1 * (par<R>(p.gx, p.gx_f) - sx1);
+    fy1 = rho1 * (par<R>(p.gy, p.gy_f) - sy1);
+    fx2 = rho2 * (par<R>(p.gx, p.gx_f) - sx2);
+    fy2 = rho2 * (par<R>(p.gy, p.gy_f) - sy2);
 }
 
 // System relaxation time (Eq. 6) and common velocity (Eqs. 8-9) of a node.
@@ -219,7 +238,7 @@ __device__ __forceinline__ void node_velocity(const Params &p, const R f[2][9], 
                                               R fx, R fy, R &omega, R &ux, R &uy) {
     const R rho = rho1 + rho2;
     const R inv_rho = R(1) / rho;
-    const R tau = (rho1 * R(p.nu1) + rho2 * R(p.nu2)) * R(3) * inv_rho + R(0.5);
+    const R tau = (rho1 * par<R>(p.nu1, p.nu1_f) + rho2 * par<R>(p.nu2, p.nu2_f)) * R(3) * inv_rho + R(0.5);
     omega = R(1) / tau;
     R jx = 0, jy = 0;
 #pragma unroll
@@ -236,30 +255,40 @@ __device__ __forceinline__ void node_velocity(const Params &p, const R f[2][9], 
     uy = jy * inv_rho;
 }
 
-// Forced BGK collision of one component (Eqs. 1, 2, 11), in place on f.
-// rho = sum_i f_i.  Since sum_i f^eq_i = rho and sum_i S_i = 0, the
-// post-collision populations also sum to rho; f*_0 is taken from that
-// identity so that rounding of the weights cannot bias the mass.
+// Forced BGK collision of both components (Eqs. 1, 2, 11), in place on f:
+//   f*_i = (1 - omega) f_i + omega rho^s E_i + (1 - omega/2) S^s_i
+// with f^eq_i = rho^s E_i, E_i = w_i [1 - 1.5 u.u + e_i.u (3 + 4.5 e_i.u)]
+// shared by the components, and the source of Eq. 11 written as
+//   S^s_i = w_i (3 + 9 e_i.u) e_i.F^s - 3 w_i u.F^s.
+// Since sum_i f^eq_i = rho^s and sum_i S^s_i = 0, the post-collision
+// populations sum to rho^s = sum_i f_i; f*_0 is taken from that identity so
+// that rounding of the weights cannot bias the mass.
 template <class R>
-__device__ __forceinline__ void collide_component(R f[9], R rho, R ux, R uy, R fx, R fy,
-                                                  R omega) {
-    const R uu = R(1.5) * (ux * ux + uy * uy);
-    const R uf = ux * fx + uy * fy;
+__device__ __forceinline__ void collide_pair(R f[2][9], R rho1, R rho2, R ux, R uy, R fx1, R fy1,
+                                             R fx2, R fy2, R omega) {
+    const R keep = R(1) - omega;
     const R pref = R(1) - R(0.5) * omega;
-    const R base = rho * (R(1) - uu);
-    R rest = R(0);
+    const R q1 = omega * rho1, q2 = omega * rho2;
+    const R gx1 = pref * fx1, gy1 = pref * fy1, gx2 = pref * fx2, gy2 = pref * fy2;
+    const R ub = R(1) - R(1.5) * (ux * ux + uy * uy);
+    const R v1 = R(3) * (ux * gx1 + uy * gy1), v2 = R(3) * (ux * gx2 + uy * gy2);
+    const R v1a = wgt<R>(1) * v1, v1d = wgt<R>(5) * v1, v2a = wgt<R>(1) * v2, v2d = wgt<R>(5) * v2;
+    R r1 = 0, r2 = 0;
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-        const R eu = R(ex(i)) * ux + R(ey(i)) * uy;
-        const R ef = R(ex(i)) * fx + R(ey(i)) * fy;
         const R w = wgt<R>(i);
-        const R feq = w * (base + rho * eu * (R(3) + R(4.5) * eu));
-        // S_i = w_i [ 3 (e_i - u) . F + 9 (e_i . u)(e_i . F) ]
-        const R src = w * (R(3) * (ef - uf) + R(9) * eu * ef);
-        f[i] = f[i] - omega * (f[i] - feq) + pref * src;
-        rest += f[i];
+        const R eu = edot<R>(i, ux, uy);
+        const R e = w * (ub + eu * (R(3) + R(4.5) * eu));
+        const R a = w * (R(3) + R(9) * eu);
+        const R s1 = a * edot<R>(i, gx1, gy1) - (i >= 5 ? v1d : v1a);
+        const R s2 = a * edot<R>(i, gx2, gy2) - (i >= 5 ? v2d : v2a);
+        f[0][i] = keep * f[0][i] + (q1 * e + s1);
+        f[1][i] = keep * f[1][i] + (q2 * e + s2);
+        r1 += f[0][i];
+        r2 += f[1][i];
     }
-    f[0] = rho - rest;
+    f[0][0] = rho1 - r1;
+    f[1][0] = rho2 - r2;
 }
 
 }  // namespace mclbm

@@ -198,8 +198,8 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
                 R s1 = 0, s2 = 0;
                 if (den > R(0)) {
                     const R inv = R(1) / den;
-                    s1 = R(g.chi[2 * code]) * n1 * inv;
-                    s2 = R(g.chi[2 * code + 1]) * n2 * inv;
+                    s1 = chi_at<R>(g, 2 * code) * n1 * inv;
+                    s2 = chi_at<R>(g, 2 * code + 1) * n2 * inv;
                 }
                 rho_ring(qB, 0, lx) = s1;
                 rho_ring(qB, 1, lx) = s2;
@@ -240,8 +240,7 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
                               fx1, fy1, fx2, fy2);
                 R omega, ux, uy;
                 node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
-                collide_component<R>(f[0], rho1, ux, uy, fx1, fy1, omega);
-                collide_component<R>(f[1], rho2, ux, uy, fx2, fy2, omega);
+                collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
                 pop_store_node<P>(g, a.p, static_cast<S *>(a.fout), x, qC, f, rho1, rho2);
             }
         }
@@ -294,6 +293,7 @@ cudaError_t launch_step_sweep(Lattice &L) {
     StepArgs a;
     a.g = L.geometry();
     a.p = L.p;
+    a.p.round_fp32();
     a.fin = L.f[L.cur];
     a.fout = L.f[1 - L.cur];
     a.d5 = L.d5;

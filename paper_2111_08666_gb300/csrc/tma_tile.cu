@@ -4,15 +4,18 @@
 //
 // A CTA walks a work list of (lattice, TX x TY tile) items.  For each tile,
 // one elected thread copies the tile and its 3-node ring, all direction
-// planes at once, into shared memory with a 3-D tensor copy, and the
-// geometry codes of the same frame with a 2-D tensor copy; both complete on
-// one mbarrier (waits bounded).  The ghost columns and rows of the layouts
-// make the ring one rectangular box even at periodic edges.  Then, from
-// shared memory:
-//   lists   fluid positions of the density frame that need a pull of their
-//           own (the 2-ring, periodic images in ragged edge tiles), solid
-//           positions of the 1-ring, and the tile's fluid nodes, compacted
-//           with warp ballots so that lanes are not spent on solid nodes
+// planes at once, into shared memory with a 3-D tensor copy, and the tile's
+// work table with a bulk copy; both complete on one mbarrier (waits
+// bounded).  The ghost columns and rows of the layouts make the ring one
+// rectangular box even at periodic edges.
+//
+// The work table of a tile is built once per geometry and boundary mode
+// (build_tables_kernel) and lists, as packed 32-bit entries: the tile's
+// fluid nodes, the other fluid nodes of the density frame (tile + 2-node
+// ring: the 2-ring, and periodic images in ragged edge tiles), and the
+// non-fluid nodes of the 1-ring, each with the fluid/solid pattern of its 8
+// neighbours.  So the step needs no geometry of its own and no branches on
+// it.  From shared memory:
 //   A       pull + bounce-back + Set-3 and component densities (Eq. 3); each
 //           thread keeps the pulled populations of its own tile node
 //   (the staged input is no longer read: the next tile's copies are issued)
@@ -36,10 +39,104 @@
 
 namespace mclbm {
 
+// Columns [0, store_cols) of a population row go by the tensor store: the
+// row up to the last whole 16-byte chunk that ends inside the lattice.
+__host__ __device__ constexpr int store_cols(int hx, int nx, int elem_bytes) {
+    return (hx + nx) / (16 / elem_bytes) * (16 / elem_bytes);
+}
+
 namespace {
 
-// geometry frame: columns x0-16 .. x0+TX+15 (a 16-byte aligned box)
-constexpr int GO = 16;
+// ---------------------------------------------------------------------------
+// Work tables.  Per tile: a 4-word header (n_own, n_ring, n_solid, 0), then
+// n_own + n_ring + n_solid entries:
+//   fluid node of the tile   tx | ty << 6 | nonfluid << 12 | set3 << 20
+//   ring pull                pos | nonfluid << 12 | set3 << 20
+//   ring non-fluid node      pos | code << 12 | fluid << 20
+// pos = row * (TX + 4) + column in the density frame, whose origin is the
+// node (x0 - 2, y0 - 2).  Bit i-1 of nonfluid (fluid) is set when the
+// neighbour x + e_i is not fluid (is fluid).  set3 bit 0: x = 0 of a lattice
+// with open ends, bit 1: x = nx - 1 of one.  Every frame position holds at
+// most one entry, so a table never exceeds 4 + frame words.
+// ---------------------------------------------------------------------------
+constexpr uint32_t SET3_BITS = 3u << 20;
+constexpr uint32_t AT_IN = 1u << 20, AT_OUT = 2u << 20;
+
+template <int TX, int TY>
+struct TableShape {
+    static constexpr int DXW = TX + 4, DYH = TY + 4, N1 = DXW * DYH;
+    static constexpr int words = (4 + N1 + 3) / 4 * 4;  // stride of one tile's table
+    static_assert(N1 <= 4096 && TX <= 64 && TY <= 64, "entry fields too narrow");
+};
+
+int table_words(int tx, int ty) { return (4 + (tx + 4) * (ty + 4) + 3) / 4 * 4; }
+
+// One warp per tile; entries appended in frame order (deterministic).
+template <int TX, int TY>
+__global__ void build_tables_kernel(Geometry g, const uint8_t *pad, int pad_rows, int open_x,
+                                    int tiles_x, int ntiles, uint32_t *tab, int *max_words) {
+    using TS = TableShape<TX, TY>;
+    constexpr int DXW = TS::DXW, N1 = TS::N1;
+    const int tile = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (tile >= ntiles) return;  // whole warps leave together
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    // geometry code of lattice position (x, y) as the step sees it: pad row
+    // y + HY, column GEO_HX + x (ghosts per the boundary mode); outside beyond
+    auto code_at = [&](int x, int y) -> int {
+        const int r = y + HY, col = GEO_HX + x;
+        if (r < 0 || r >= pad_rows || col < 0 || col >= g.gpitch) return GEO_OUTSIDE;
+        return pad[(long long)r * g.gpitch + col];
+    };
+    auto fluid_mask = [&](int x, int y) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            if (code_at(x + ex(i), y + ey(i)) == GEO_FLUID) m |= 1u << (i - 1);
+        return m;
+    };
+    auto set3 = [&](int x) -> uint32_t {
+        return (open_x && x == 0 ? AT_IN : 0u) | (open_x && x == g.nx - 1 ? AT_OUT : 0u);
+    };
+    uint32_t *T = tab + (size_t)tile * TS::words;
+    int n = 0;
+    auto append = [&](bool flag, uint32_t e) {
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (flag) T[4 + n + __popc(m & ((1u << lane) - 1u))] = e;
+        n += __popc(m);
+    };
+    for (int base = 0; base < TX * TY; base += 32) {
+        const int k = base + lane;
+        const int tx = k % TX, ty = k / TX, x = x0 + tx, y = y0 + ty;
+        const bool f = k < TX * TY && x < g.nx && y < g.ny && code_at(x, y) == GEO_FLUID;
+        append(f, f ? (uint32_t)tx | (uint32_t)ty << 6 | (~fluid_mask(x, y) & 0xffu) << 12 | set3(x)
+                    : 0u);
+    }
+    const int n_own = n;
+    for (int base = 0; base < N1; base += 32) {
+        const int k = base + lane;
+        const int dr = k / DXW, dc = k % DXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
+        const bool own = dr >= 2 && dr < TY + 2 && dc >= 2 && dc < TX + 2 && x < g.nx && y < g.ny;
+        const bool f = k < N1 && !own && code_at(x, y) == GEO_FLUID;
+        append(f, f ? (uint32_t)k | (~fluid_mask(x, y) & 0xffu) << 12 | set3(x) : 0u);
+    }
+    const int n_ring = n - n_own;
+    for (int base = 0; base < N1; base += 32) {
+        const int k = base + lane;
+        const int dr = k / DXW, dc = k % DXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
+        const bool ring1 = dr >= 1 && dr <= TY + 2 && dc >= 1 && dc <= TX + 2;
+        const int c = k < N1 && ring1 ? code_at(x, y) : GEO_FLUID;
+        const bool f = c != GEO_FLUID;
+        append(f, f ? (uint32_t)k | (uint32_t)c << 12 | fluid_mask(x, y) << 20 : 0u);
+    }
+    if (lane == 0) {
+        T[0] = (uint32_t)n_own;
+        T[1] = (uint32_t)n_ring;
+        T[2] = (uint32_t)(n - n_own - n_ring);
+        T[3] = 0;
+        atomicMax(max_words, 4 + n);
+    }
+}
 
 template <class P, int TX, int TY>
 struct TileLayout {
@@ -51,100 +148,75 @@ struct TileLayout {
     static constexpr int RXW = TX + 2 * HX;  // staged input: columns x0-HX .. x0+TX+HX-1
     static constexpr int RYH = TY + 6;       // rows y0-3 .. y0+TY+2
     static constexpr int PSTR = RYH * RXW;   // plane stride of the staged input
-    static constexpr int DXW = TX + 4;       // density frame: tile + 2
-    static constexpr int DYH = TY + 4;
-    static constexpr int GXW = TX + 2 * GO;  // geometry frame width (bytes)
-    static constexpr int GYH = TY + 6;
-    static constexpr int N1 = DXW * DYH;
-    static constexpr int N2 = (DXW - 2) * (DYH - 2);
-    static constexpr int N3 = TX * TY;
+    static constexpr int DXW = TableShape<TX, TY>::DXW;  // density frame: tile + 2
+    static constexpr int N1 = TableShape<TX, TY>::N1;
+    static constexpr int TW = TableShape<TX, TY>::words;
     static constexpr size_t in_bytes = (size_t)NPL * PSTR * sizeof(S);
     static constexpr size_t out_off = (in_bytes + 127) / 128 * 128;
     static constexpr size_t out_bytes = (size_t)NPL * TY * TX * sizeof(S);
-    static constexpr size_t geo_bytes = (size_t)GYH * GXW;
-    static constexpr size_t geo_off = (out_off + out_bytes + 127) / 128 * 128;  // two buffers
-    static constexpr size_t rho_off = (geo_off + 2 * geo_bytes + 127) / 128 * 128;
+    static constexpr size_t rho_off = (out_off + out_bytes + 127) / 128 * 128;
     static constexpr size_t rho_bytes = (size_t)2 * N1 * sizeof(R);
-    static constexpr size_t l1_off = (rho_off + rho_bytes + 15) / 16 * 16;
-    static constexpr size_t l2_off = l1_off + (size_t)N1 * 2;
-    static constexpr size_t l3_off = l2_off + (size_t)N2 * 2;
-    static constexpr size_t cnt_off = (l3_off + (size_t)N3 * 2 + 15) / 16 * 16;
-    static constexpr size_t bar_off = cnt_off + 16;
+    static constexpr size_t tab_off = (rho_off + rho_bytes + 127) / 128 * 128;  // two buffers
+    static constexpr size_t tab_bytes = (size_t)2 * TW * 4;
+    static constexpr size_t bar_off = tab_off + tab_bytes;
     static constexpr size_t total = bar_off + 8;
-    static constexpr uint32_t tx_bytes = (uint32_t)(in_bytes + geo_bytes);
     static_assert((RXW * sizeof(S)) % 16 == 0, "tensor box rows must be whole 16-byte chunks");
     static_assert((TX * sizeof(S)) % 16 == 0, "store box rows must be whole 16-byte chunks");
-    static_assert(GXW % 16 == 0 && geo_bytes % 16 == 0, "geometry box rows must be 16-byte chunks");
+    static_assert((TW * 4) % 16 == 0, "table copies must be whole 16-byte chunks");
     static_assert(HX >= 3, "halo must cover the stencil reach");
 };
-
-// Columns [0, store_cols) of a population row go by the tensor store: the
-// row up to the last whole 16-byte chunk that ends inside the lattice.
-__host__ __device__ constexpr int store_cols(int hx, int nx, int elem_bytes) {
-    return (hx + nx) / (16 / elem_bytes) * (16 / elem_bytes);
-}
-
-// Append val to a shared list when flag is set; all 32 lanes of the warp
-// must call it together.
-__device__ __forceinline__ void list_append(bool flag, uint16_t val, uint16_t *list, int *count) {
-    const unsigned m = __ballot_sync(0xffffffffu, flag);
-    if (m == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[base + __popc(m & ((1u << lane) - 1u))] = val;
-}
 
 // The lattices of a launch; every lattice's arguments and tensor descriptors
 // travel in the kernel parameters.
 struct BatchArgs {
     int ncases, total;
     int tiles_x[MAX_BATCH];
-    int first[MAX_BATCH + 1];  // first work item of each lattice
+    int first[MAX_BATCH + 1];     // first work item of each lattice
+    int tab_words[MAX_BATCH];     // table words copied per tile
+    const uint32_t *tab[MAX_BATCH];
     StepArgs a[MAX_BATCH];
     CUtensorMap tin[MAX_BATCH];   // input populations (whole padded array)
-    CUtensorMap tout[MAX_BATCH];  // output populations (extent ends at the lattice edge)
-    CUtensorMap tgeo[MAX_BATCH];  // padded geometry codes
+    CUtensorMap tout[MAX_BATCH];  // output populations (extent ends inside the lattice)
 };
 
-__device__ __forceinline__ int case_of(const BatchArgs &b, int w) {
-    int c = 0;
-    while (c + 1 < b.ncases && w >= b.first[c + 1]) ++c;
-    return c;
-}
-
-template <class P, int TX, int TY>
+// ONE: the launch holds a single lattice (its arguments at fixed offsets)
+template <class P, int TX, int TY, bool ONE>
 __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_constant__ BatchArgs b) {
     using L = TileLayout<P, TX, TY>;
     using S = typename P::store_t;
     using R = typename P::real_t;
     constexpr int NT = L::NT, HX = L::HX, RXW = L::RXW, PSTR = L::PSTR, DXW = L::DXW,
-                  GXW = L::GXW;
+                  N1 = L::N1, TW = L::TW;
 
     extern __shared__ __align__(128) unsigned char smem[];
     const S *in = reinterpret_cast<const S *>(smem);
     S *out = reinterpret_cast<S *>(smem + L::out_off);
     R *rho = reinterpret_cast<R *>(smem + L::rho_off);
-    uint16_t *l1 = reinterpret_cast<uint16_t *>(smem + L::l1_off);
-    uint16_t *l2 = reinterpret_cast<uint16_t *>(smem + L::l2_off);
-    uint16_t *l3 = reinterpret_cast<uint16_t *>(smem + L::l3_off);
-    int *cnt = reinterpret_cast<int *>(smem + L::cnt_off);
+    uint32_t *tabs = reinterpret_cast<uint32_t *>(smem + L::tab_off);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::bar_off);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
 
-    // stage tile w: populations into the input buffer, geometry into frame gb
-    auto issue = [&](int w, int gb) {
-        const int c = case_of(b, w);
+    auto case_of = [&](int w) -> int {
+        if constexpr (ONE) {
+            return 0;
+        } else {
+            int c = 0;
+            while (c + 1 < b.ncases && w >= b.first[c + 1]) ++c;
+            return c;
+        }
+    };
+
+    // stage tile w: populations into the input buffer, work table into buffer tb
+    auto issue = [&](int w, int tb) {
+        const int c = case_of(w);
         const int t = w - b.first[c];
         const int x0 = (t % b.tiles_x[c]) * TX, y0 = (t / b.tiles_x[c]) * TY;
+        const uint32_t tbytes = 4u * (uint32_t)b.tab_words[c];
         fence_proxy_async();
-        mbar_expect_tx(bar, L::tx_bytes);
+        mbar_expect_tx(bar, (uint32_t)L::in_bytes + tbytes);
         // element (x0 - HX, y0 - 3) is column x0, row y0 + HY - 3 in memory
         tma_load_3d(smem, &b.tin[c], x0, y0 + HY - 3, 0, bar);
-        // geometry (x0 - 16, y0 - 3) is column x0, row y0 + HY - 3 of the padded copy
-        tma_load_2d(smem + L::geo_off + gb * L::geo_bytes, &b.tgeo[c], x0, y0 + HY - 3, bar);
+        bulk_g2s(tabs + tb * TW, b.tab[c] + (size_t)t * TW, tbytes, bar);
     };
 
     if (tid == 0) {
@@ -156,17 +228,14 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
     if (tid == 0) issue(blockIdx.x, 0);
 
     uint32_t parity = 0;
-    int gb = 0;
+    int tb = 0;
     for (int w = blockIdx.x; w < b.total; w += gridDim.x) {
-        const int c = case_of(b, w);
+        const int c = case_of(w);
         const StepArgs &a = b.a[c];
         const Geometry &g = a.g;
         const int t = w - b.first[c];
         const int x0 = (t % b.tiles_x[c]) * TX, y0 = (t / b.tiles_x[c]) * TY;
-        const uint8_t *geo = smem + L::geo_off + gb * L::geo_bytes;
-        auto geo_s = [&](int r, int col) -> uint8_t { return geo[r * GXW + col]; };
 
-        if (tid == 0) cnt[0] = cnt[1] = cnt[2] = 0;
         const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
         if (__syncthreads_or(bad)) {
             if (tid == 0) {
@@ -177,87 +246,46 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
             }
             return;
         }
+        const uint32_t *T = tabs + tb * TW;
+        const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
+        const uint32_t *E = T + 4;
 
-        // ---- work lists (geometry only) --------------------------------------
-        for (int base = warp * 32; base < L::N1; base += NT) {
-            const int k = base + lane;
-            bool f = false;
-            if (k < L::N1) {
-                const int dr = k / DXW, dc = k % DXW;
-                const bool own = dr >= 2 && dr < TY + 2 && dc >= 2 && dc < TX + 2 &&
-                                 x0 - 2 + dc < g.nx && y0 - 2 + dr < g.ny;
-                const bool fl = geo_s(dr + 1, dc - 2 + GO) == GEO_FLUID;
-                if (!fl || own) {
-                    rho[k] = R(0);
-                    rho[L::N1 + k] = R(0);
-                }
-                // the 2-ring, and in a ragged edge tile the positions past the
-                // lattice edge (periodic images the edge nodes need)
-                f = fl && !own;
-            }
-            list_append(f, (uint16_t)k, l1, &cnt[0]);
-        }
-        for (int base = warp * 32; base < L::N2; base += NT) {
-            const int k = base + lane;
-            bool f = false;
-            int pos = 0;
-            if (k < L::N2) {
-                const int dr = 1 + k / (DXW - 2), dc = 1 + k % (DXW - 2);
-                const uint8_t code = geo_s(dr + 1, dc - 2 + GO);
-                f = code != GEO_FLUID && code != GEO_OUTSIDE;
-                pos = dr * DXW + dc;
-            }
-            list_append(f, (uint16_t)pos, l2, &cnt[1]);
-        }
-        for (int base = warp * 32; base < L::N3; base += NT) {
-            const int k = base + lane;
-            bool f = false;
-            if (k < L::N3) {
-                const int ty = k / TX, tx = k % TX;
-                f = x0 + tx < g.nx && y0 + ty < g.ny && geo_s(ty + 3, tx + GO) == GEO_FLUID;
-            }
-            list_append(f, (uint16_t)k, l3, &cnt[2]);
-        }
-        __syncthreads();
-
-        // populations of the node at staged row r, column c with lattice
-        // column x and wrapped row y (geometry frame row r, column c - HX + GO)
-        auto pull = [&](int r, int c, int x, int y, R f[2][9]) {
-            const int gc = c - HX + GO;
-            const bool at_in = a.p.open_x && x == 0;
-            const bool at_out = a.p.open_x && x == g.nx - 1;
-            auto dec = [&](int plane, int comp, int pos) -> R {
-                R v = to_real(in[(comp * 9 + plane) * PSTR + pos]);
-                if constexpr (P::ref) v += wgt<R>(plane) * to_real(in[(18 + comp) * PSTR + pos]);
-                return v;
-            };
-            const int own = r * RXW + c;
+        // population (plane, comp) of the staged node pos, w = its weight
+        auto dec = [&](int plane, int comp, int pos, R w) -> R {
+            R v = to_real(in[(comp * 9 + plane) * PSTR + pos]);
+            if constexpr (P::ref) v += w * to_real(in[(18 + comp) * PSTR + pos]);
+            return v;
+        };
+        // f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) where x - e_i is not fluid
+        // (half-way bounce-back), then Set-3 at the open ends; the node sits at
+        // staged row r, column cc, lattice column x and wrapped row y.  Where a
+        // source lies beyond an open end the bounce-back value is a placeholder
+        // that Set-3 replaces.
+        auto pull = [&](int r, int cc, uint32_t e, int x, int y, R f[2][9]) {
+            const uint32_t m = (e >> 12) & 0xffu;
+            const int own = r * RXW + cc;
+            f[0][0] = dec(0, 0, own, wgt<R>(0));
+            f[1][0] = dec(0, 1, own, wgt<R>(0));
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                if ((at_in && ex(i) == 1) || (at_out && ex(i) == -1)) {
-                    f[0][i] = R(0);
-                    f[1][i] = R(0);
-                    continue;
-                }
-                // half-way bounce-back reads the node's own opposite population
-                const bool solid_src = i != 0 && geo_s(r - ey(i), gc - ex(i)) != GEO_FLUID;
-                const int pos = solid_src ? own : own - ey(i) * RXW - ex(i);
-                const int pl = solid_src ? opp(i) : i;
-                f[0][i] = dec(pl, 0, pos);
-                f[1][i] = dec(pl, 1, pos);
+            for (int i = 1; i < 9; ++i) {
+                const bool sb = (m >> (opp(i) - 1)) & 1u;
+                const int pos = sb ? own : own - ey(i) * RXW - ex(i);
+                const int pl = sb ? opp(i) : i;
+                f[0][i] = dec(pl, 0, pos, wgt<R>(i));
+                f[1][i] = dec(pl, 1, pos, wgt<R>(i));
             }
-            apply_set3<R>(a, x, y, [&](int comp, int i) { return dec(i, comp, own); }, f);
+            if (e & SET3_BITS)
+                apply_set3<R>(a, x, y, [&](int comp, int i) { return dec(i, comp, own, wgt<R>(i)); },
+                              f);
         };
 
-        // ---- A: densities on the density frame -------------------------------
-        // (the frame reaches at most 2 rows past an edge and ny >= 3, so one
-        // period of wrap suffices)
-        const int n1 = cnt[0];
-        for (int k = tid; k < n1; k += NT) {
-            const int pos = l1[k];
-            const int dr = pos / DXW, dc = pos % DXW;
+        // ---- A: densities of the ring's fluid nodes, then of the tile's own --
+        for (int k = tid; k < n_ring; k += NT) {
+            const uint32_t e = E[n_own + k];
+            const int pos = (int)(e & 0xfffu);
+            const int dr = pos / DXW, dc = pos - dr * DXW;
             R f[2][9];
-            pull(dr + 1, dc - 2 + HX, x0 - 2 + dc, wrap(y0 - 2 + dr, g.ny), f);
+            pull(dr + 1, dc - 2 + HX, e, x0 - 2 + dc, wrap(y0 - 2 + dr, g.ny), f);
             R r1 = 0, r2 = 0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -265,57 +293,55 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
                 r2 += f[1][i];
             }
             rho[pos] = r1;
-            rho[L::N1 + pos] = r2;
+            rho[N1 + pos] = r2;
         }
-        // the tile's own fluid nodes: each thread pulls at most one and keeps
-        // its populations in registers for the collision
-        const int n3 = cnt[2];
-        const bool have = tid < n3;
-        int ty = 0, tx = 0;
+        // each thread pulls at most one tile node and keeps its populations
+        // in registers for the collision
+        const bool have = tid < n_own;
+        const uint32_t me = have ? E[tid] : 0u;
+        const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u);
         R f[2][9];
         R rho1 = 0, rho2 = 0;
         if (have) {
-            const int idx = l3[tid];
-            ty = idx / TX;
-            tx = idx % TX;
-            pull(ty + 3, tx + HX, x0 + tx, y0 + ty, f);
+            pull(ty + 3, tx + HX, me, x0 + tx, y0 + ty, f);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 rho1 += f[0][i];
                 rho2 += f[1][i];
             }
             rho[(ty + 2) * DXW + tx + 2] = rho1;
-            rho[L::N1 + (ty + 2) * DXW + tx + 2] = rho2;
+            rho[N1 + (ty + 2) * DXW + tx + 2] = rho2;
         }
         __syncthreads();
         // the staged input has been read: bring in the next tile meanwhile
-        if (tid == 0 && w + (int)gridDim.x < b.total) issue(w + gridDim.x, gb ^ 1);
+        if (tid == 0 && w + (int)gridDim.x < b.total) issue(w + gridDim.x, tb ^ 1);
 
-        // ---- B: virtual solid densities on the 1-ring ----------------------------
-        const int n2 = cnt[1];
-        for (int k = tid; k < n2; k += NT) {
-            const int pos = l2[k];
-            const int dr = pos / DXW, dc = pos % DXW;
-            const uint8_t code = geo_s(dr + 1, dc - 2 + GO);
+        // ---- B: virtual solid densities on the 1-ring (zero outside) -----------
+        const uint32_t *Es = E + n_own + n_ring;
+        for (int k = tid; k < n_sol; k += NT) {
+            const uint32_t e = Es[k];
+            const int pos = (int)(e & 0xfffu);
+            const int code = (int)((e >> 12) & 0xffu);
+            const uint32_t fm = e >> 20;
             R n1s = 0, n2s = 0, den = 0;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                if (geo_s(dr + 1 + ey(i), dc - 2 + GO + ex(i)) == GEO_FLUID) {
+                if ((fm >> (i - 1)) & 1u) {
                     const R w8 = wgt<R>(i);
                     const int q = pos + ey(i) * DXW + ex(i);
                     n1s += w8 * rho[q];
-                    n2s += w8 * rho[L::N1 + q];
+                    n2s += w8 * rho[N1 + q];
                     den += w8;
                 }
             }
             R s1 = 0, s2 = 0;
-            if (den > R(0)) {
+            if (den > R(0) && code != GEO_OUTSIDE) {
                 const R inv = R(1) / den;
-                s1 = R(g.chi[2 * code]) * n1s * inv;
-                s2 = R(g.chi[2 * code + 1]) * n2s * inv;
+                s1 = chi_at<R>(g, 2 * code) * n1s * inv;
+                s2 = chi_at<R>(g, 2 * code + 1) * n2s * inv;
             }
             rho[pos] = s1;
-            rho[L::N1 + pos] = s2;
+            rho[N1 + pos] = s2;
         }
         // the previous tile's output copy must have read the output buffer
         if (tid == 0) bulk_wait_read();
@@ -324,28 +350,37 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
         // ---- C: collision of the tile's fluid nodes --------------------------------
         if (have) {
             const int x = x0 + tx, y = y0 + ty;
-            const bool mirror_in = a.p.open_x && x == 0;
-            const bool mirror_out = a.p.open_x && x == g.nx - 1;
             const int dpos = (ty + 2) * DXW + tx + 2;
+            const uint32_t m = (me >> 12) & 0xffu;
             R fx1, fy1, fx2, fy2;
-            node_force<R>(a.p, rho1, rho2,
-                          [&](int i, uint8_t &code, R &s1, R &s2) {
-                              int dx = ex(i), dy = ey(i);
-                              // Sec. 2.1: a neighbour beyond an open end is
-                              // replaced by the one in the opposite direction
-                              if ((mirror_in && dx < 0) || (mirror_out && dx > 0)) {
-                                  dx = -dx;
-                                  dy = -dy;
-                              }
-                              code = geo_s(ty + 3 + dy, tx + GO + dx);
-                              s1 = rho[dpos + dy * DXW + dx];
-                              s2 = rho[L::N1 + dpos + dy * DXW + dx];
-                          },
-                          fx1, fy1, fx2, fy2);
+            if (me & SET3_BITS) {
+                // Sec. 2.1: a neighbour beyond an open end is replaced by the
+                // one in the opposite direction
+                const bool mir_in = me & AT_IN, mir_out = me & AT_OUT;
+                node_force<R, false>(a.p, rho1, rho2,
+                                     [&](int i, uint8_t &code, R &s1, R &s2) {
+                                         const bool mir = (mir_in && ex(i) < 0) || (mir_out && ex(i) > 0);
+                                         const int d = ey(i) * DXW + ex(i);
+                                         const int q = mir ? dpos - d : dpos + d;
+                                         const uint32_t bit = mir ? (m >> (opp(i) - 1)) : (m >> (i - 1));
+                                         code = (bit & 1u) ? 1 : GEO_FLUID;
+                                         s1 = rho[q];
+                                         s2 = rho[N1 + q];
+                                     },
+                                     fx1, fy1, fx2, fy2);
+            } else {
+                node_force<R, false>(a.p, rho1, rho2,
+                                     [&](int i, uint8_t &code, R &s1, R &s2) {
+                                         const int q = dpos + ey(i) * DXW + ex(i);
+                                         code = ((m >> (i - 1)) & 1u) ? 1 : GEO_FLUID;
+                                         s1 = rho[q];
+                                         s2 = rho[N1 + q];
+                                     },
+                                     fx1, fy1, fx2, fy2);
+            }
             R omega, ux, uy;
             node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
-            collide_component<R>(f[0], rho1, ux, uy, fx1, fy1, omega);
-            collide_component<R>(f[1], rho2, ux, uy, fx2, fy2, omega);
+            collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
             // output tile: planes of TY x TX in the layout of the store box
             const int o = ty * TX + tx;
             constexpr int OSTR = TX * TY;
@@ -380,13 +415,13 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
             bulk_commit();
         }
         parity ^= 1u;
-        gb ^= 1;
+        tb ^= 1;
     }
     if (tid == 0) bulk_wait_read();
 }
 
 // ---------------------------------------------------------------------------
-// Host side: tensor descriptors and launch.
+// Host side: tensor descriptors, work tables and launch.
 // ---------------------------------------------------------------------------
 static_assert(sizeof(BatchArgs) < 32000, "batch arguments must fit the kernel parameter space");
 
@@ -423,6 +458,10 @@ TileShape shape_of(mclbm_precision p, int shape = 0) {
     return {32, p == MCLBM_FP32_DEV ? 12 : 16, hx};
 }
 
+int tiles_of(const Lattice &L, const TileShape &sh) {
+    return ((L.nx + sh.tx - 1) / sh.tx) * ((L.ny + sh.ty - 1) / sh.ty);
+}
+
 CUtensorMapDataType dtype_of(mclbm_precision p) {
     switch (p) {
         case MCLBM_FP16_DEV: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -433,25 +472,37 @@ CUtensorMapDataType dtype_of(mclbm_precision p) {
 
 // descriptors of one lattice for one tile shape:
 // [0] input of buffer 0, [1] output into buffer 0, [2] input of buffer 1,
-// [3] output into buffer 1, [4] padded geometry
-constexpr int MAPS_PER_CASE = 5;
+// [3] output into buffer 1
+constexpr int MAPS_PER_CASE = 4;
 
-template <class P, int TX, int TY>
-cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, int grid,
-                       cudaStream_t stream, int *slots_out) {
+template <class P, int TX, int TY, bool ONE>
+int resident_slots() {
     using Lay = TileLayout<P, TX, TY>;
     static int slots = 0;
     if (slots == 0) {
-        cudaError_t e = cudaFuncSetAttribute(tma_tile_kernel<P, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Lay::total);
-        if (e != cudaSuccess) return e;
+        if (cudaFuncSetAttribute(tma_tile_kernel<P, TX, TY, ONE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Lay::total) != cudaSuccess)
+            return 0;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_tile_kernel<P, TX, TY>, TX * TY,
-                                                      Lay::total);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_tile_kernel<P, TX, TY, ONE>,
+                                                      TX * TY, Lay::total);
         slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
+    }
+    return slots;
+}
+
+template <class P, int TX, int TY>
+cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, int shape, int grid,
+                       cudaStream_t stream, int *slots_out) {
+    using Lay = TileLayout<P, TX, TY>;
+    const bool one = n == 1;
+    const int slots = one ? resident_slots<P, TX, TY, true>() : resident_slots<P, TX, TY, false>();
+    if (slots == 0) {
+        const cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? e : cudaErrorUnknown;
     }
     if (slots_out) *slots_out = slots;
     if (!cases) return cudaSuccess;  // query only
@@ -461,12 +512,16 @@ cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, in
     int total = 0;
     for (int c = 0; c < n; ++c) {
         const Lattice &L = *cases[c];
+        if (!L.tab[shape] || L.tab_words[shape] < 4) return cudaErrorInvalidValue;
         b.tiles_x[c] = (L.nx + TX - 1) / TX;
         b.first[c] = total;
         total += b.tiles_x[c] * ((L.ny + TY - 1) / TY);
+        b.tab[c] = L.tab[shape];
+        b.tab_words[c] = L.tab_words[shape];
         StepArgs &a = b.a[c];
         a.g = L.geometry();
         a.p = L.p;
+        a.p.round_fp32();
         a.fin = L.f[L.cur];
         a.fout = L.f[1 - L.cur];
         a.d5 = L.d5;
@@ -475,12 +530,14 @@ cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, in
         const CUtensorMap *m = maps + MAPS_PER_CASE * c;
         b.tin[c] = m[2 * L.cur];               // read the current buffer
         b.tout[c] = m[2 * (1 - L.cur) + 1];    // store into the other one
-        b.tgeo[c] = m[4];
     }
     b.first[n] = total;
     b.total = total;
     const int g = grid > 0 ? (grid < total ? grid : total) : (slots < total ? slots : total);
-    tma_tile_kernel<P, TX, TY><<<g, TX * TY, Lay::total, stream>>>(b);
+    if (one)
+        tma_tile_kernel<P, TX, TY, true><<<g, TX * TY, Lay::total, stream>>>(b);
+    else
+        tma_tile_kernel<P, TX, TY, false><<<g, TX * TY, Lay::total, stream>>>(b);
     count_launch();
     return cudaGetLastError();
 }
@@ -489,8 +546,8 @@ template <class P>
 cudaError_t launch_prec(Lattice *const *cases, int n, const CUtensorMap *maps, int shape,
                         int grid, cudaStream_t stream, int *slots) {
     constexpr bool dev32 = std::is_same<P, P32D>::value;
-    if (shape == 1) return launch_cfg<P, 32, 8>(cases, n, maps, grid, stream, slots);
-    return launch_cfg<P, 32, dev32 ? 12 : 16>(cases, n, maps, grid, stream, slots);
+    if (shape == 1) return launch_cfg<P, 32, 8>(cases, n, maps, shape, grid, stream, slots);
+    return launch_cfg<P, 32, dev32 ? 12 : 16>(cases, n, maps, shape, grid, stream, slots);
 }
 
 cudaError_t launch_any(mclbm_precision p, Lattice *const *cases, int n, const CUtensorMap *maps,
@@ -504,6 +561,18 @@ cudaError_t launch_any(mclbm_precision p, Lattice *const *cases, int n, const CU
     }
 }
 
+template <int TX, int TY>
+cudaError_t launch_build(const Lattice &L, int shape) {
+    const int tiles_x = (L.nx + TX - 1) / TX;
+    const int ntiles = tiles_x * ((L.ny + TY - 1) / TY);
+    const int blocks = (ntiles + 3) / 4;  // four warps (tiles) per block
+    build_tables_kernel<TX, TY><<<blocks, 128, 0, L.stream>>>(
+        L.geometry(), L.geo_pad, L.geo_pad_rows, L.p.open_x, tiles_x, ntiles, L.tab[shape],
+        L.tab_max + shape);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // Descriptors of one lattice for a tile shape (MAPS_PER_CASE of them).
@@ -511,8 +580,7 @@ int encode_tile_maps(const Lattice &L, int shape, void *out) {
     CUtensorMap *maps = static_cast<CUtensorMap *>(out);
     const TileShape sh = shape_of(L.prec, shape);
     EncodeTiledFn enc = encode_fn();
-    if (sh.tx == 0 || !enc || !L.geo_pad)
-        return fail(MCLBM_ERR_STATE, "TMA descriptors not available");
+    if (sh.tx == 0 || !enc) return fail(MCLBM_ERR_STATE, "TMA descriptors not available");
     const cuuint64_t sb = L.store_bytes;
     const cuuint32_t estr[3] = {1, 1, 1};
     for (int b = 0; b < 2; ++b) {
@@ -538,16 +606,6 @@ int encode_tile_maps(const Lattice &L, int shape, void *out) {
                                             std::to_string((int)r) + ", " +
                                             std::to_string((int)r2) + ")");
     }
-    // geometry: the padded byte array, box = the tile's geometry frame
-    const cuuint64_t gdim[2] = {(cuuint64_t)L.gpitch, (cuuint64_t)L.geo_pad_rows};
-    const cuuint64_t gstride[1] = {(cuuint64_t)L.gpitch};
-    const cuuint32_t gbox[2] = {(cuuint32_t)(sh.tx + 2 * GO), (cuuint32_t)(sh.ty + 6)};
-    CUresult r = enc(&maps[4], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, L.geo_pad, gdim, gstride, gbox,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-        return fail(MCLBM_ERR_CUDA, "cuTensorMapEncodeTiled (geometry) failed (" +
-                                        std::to_string((int)r) + ")");
     return MCLBM_OK;
 }
 
@@ -555,6 +613,20 @@ bool tma_supported(const Lattice &L) { return L.tmaps != nullptr; }
 
 int tma_prepare(Lattice &L) {
     if (shape_of(L.prec).tx == 0 || !encode_fn() || !L.geo_pad) return MCLBM_OK;  // other kernels serve
+    for (int s = 0; s < 2; ++s) {
+        const TileShape sh = shape_of(L.prec, s);
+        const size_t bytes = (size_t)tiles_of(L, sh) * table_words(sh.tx, sh.ty) * 4;
+        if (cudaMalloc((void **)&L.tab[s], bytes) != cudaSuccess ||
+            cudaMemsetAsync(L.tab[s], 0, bytes, L.stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MCLBM_ERR_NOMEM, "device allocation of the work tables failed");
+        }
+        L.device_bytes += bytes;
+    }
+    if (cudaMalloc((void **)&L.tab_max, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCLBM_ERR_NOMEM, "device allocation failed");
+    }
     CUtensorMap *maps = new (std::nothrow) CUtensorMap[MAPS_PER_CASE];
     if (!maps) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
     if (int rc = encode_tile_maps(L, 0, maps)) {
@@ -565,9 +637,35 @@ int tma_prepare(Lattice &L) {
     return MCLBM_OK;
 }
 
+// (Re)build the work tables of both tile shapes for the current geometry
+// ghosts and boundary mode, and read back the largest table of each.
+int tma_build_tables(Lattice &L) {
+    if (!L.tab[0] || !L.tab[1] || !L.tab_max) return MCLBM_OK;
+    cudaError_t e = cudaMemsetAsync(L.tab_max, 0, 2 * sizeof(int), L.stream);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+        const TileShape sh = shape_of(L.prec, s);
+        if (sh.ty == 16) e = launch_build<32, 16>(L, s);
+        else if (sh.ty == 12) e = launch_build<32, 12>(L, s);
+        else e = launch_build<32, 8>(L, s);
+    }
+    int mx[2] = {0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mx, L.tab_max, sizeof(mx), cudaMemcpyDeviceToHost, L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "work tables of the tile kernel");
+    for (int s = 0; s < 2; ++s) L.tab_words[s] = (mx[s] + 3) / 4 * 4;
+    return MCLBM_OK;
+}
+
 void tma_release(Lattice &L) {
     delete[] static_cast<CUtensorMap *>(L.tmaps);
     L.tmaps = nullptr;
+    for (int s = 0; s < 2; ++s) {
+        cudaFree(L.tab[s]);
+        L.tab[s] = nullptr;
+    }
+    cudaFree(L.tab_max);
+    L.tab_max = nullptr;
 }
 
 size_t tile_maps_bytes() { return MAPS_PER_CASE * sizeof(CUtensorMap); }
@@ -576,7 +674,7 @@ int tile_maps_for(const Lattice &L, int shape, void *out) { return encode_tile_m
 
 int batch_slots(mclbm_precision p, int shape) {
     int slots = 0;
-    launch_any(p, nullptr, 0, nullptr, shape, 0, 0, &slots);
+    launch_any(p, nullptr, 2, nullptr, shape, 0, 0, &slots);
     return slots;
 }
 

@@ -266,25 +266,45 @@ def test_boundary_mode_switch_keeps_parity(kernel):
     assert_fp64_parity(o, g, 60)
 
 
+# Agreement of two step formulations, relative to max|f|: one step from the
+# same developed state (a few units in the last place of the storage), and
+# 300 steps from the initial state (rounding differences of the FP32
+# arithmetic, flipped roundings of a 16-bit storage, carried along).
+AGREE = {"fp32": (1e-6, 4e-6), "fp32dev": (1e-6, 4e-6), "fp16dev": (1e-4, 1e-3),
+         "bf16dev": (1e-3, 4e-3)}
+
+
 @pytest.mark.parametrize("other", [2, 3])
 @pytest.mark.parametrize("prec", ["fp32", "fp32dev", "fp16dev", "bf16dev"])
 def test_step_kernels_agree(prec, other):
     """The formulations of the step (global-pull tile, strip, TMA tile)
-    compute the same update in every storage precision (same arithmetic,
-    different data movement)."""
+    compute the same update of Eqs. 1-29 in every storage precision; they
+    differ only in data movement and in how the compiler fuses the FP32
+    multiply-adds, so they agree to rounding."""
     m = media.make_disk_medium(200, 70, 11, radius="uniform", r_lo=3.0, r_hi=6.0,
                                porosity=0.7)
     xi = media.uniform_xi(m.solid, -0.4)
     rho1, rho2 = media.drainage_densities(m.solid)
     kw = dict(prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+    one, many = AGREE[prec]
+    base = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
+    base.init(rho1, rho2)
+    base.step(200)
+    f0 = base.populations()
     a = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
     b = mclbm.Lattice(m.solid, xi, kernel=other, **kw)
+    a.set_populations(f0)
+    b.set_populations(f0)
+    a.step(1)
+    b.step(1)
+    scale = np.max(np.abs(f0))
+    assert np.max(np.abs(a.populations() - b.populations())) <= one * scale
     a.init(rho1, rho2)
     b.init(rho1, rho2)
     a.step(300)
     b.step(300)
     fa, fb = a.populations(), b.populations()
-    assert np.max(np.abs(fa - fb)) <= 1e-6 * np.max(np.abs(fa))
+    assert np.max(np.abs(fa - fb)) <= many * np.max(np.abs(fa))
 
 
 @pytest.mark.parametrize("periodic_y,open_x", [(True, False), (True, True), (False, False)])
