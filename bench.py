@@ -150,7 +150,7 @@ def run_gpu(args, rank, world):
     kernel = {"auto": 0, "tile": 1, "strip": 2}[args.kernel]
     lat = mclbm.Lattice(c["solid"], c["xi"], prec=prec, nu1=c["nu1"], nu2=c["nu2"],
                         rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream,
-                        kernel=kernel)
+                        kernel=kernel, tile_shape=args.tile_shape)
     lat.init(c["rho1"], c["rho2"])
     n_all = c["nx"] * c["ny"]
     for _ in range(max(args.warmup, 3)):
@@ -211,7 +211,7 @@ def run_gpu(args, rank, world):
     c2 = workload(1024, 512, 1)
     lat2 = mclbm.Lattice(c2["solid"], c2["xi"], prec=prec, nu1=c2["nu1"], nu2=c2["nu2"],
                          rho_in1=c2["rho_in1"], rho_out2=c2["rho_out2"], stream=stream,
-                         kernel=kernel)
+                         kernel=kernel, tile_shape=args.tile_shape)
     lat2.init(c2["rho1"], c2["rho2"])
     lat2.step(20)
     lat2.sync()
@@ -242,7 +242,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{c['name']} seed 99 (drainage, M=10, theta=50 deg, "
                                f"rho_in=1.005, rho_out=1)",
                    "nx": c["nx"], "ny": c["ny"], "porosity": round(c["porosity"], 4),
-                   "storage": args.prec, "step_kernel": args.kernel,
+                   "storage": args.prec, "step_kernel": args.kernel, "tile_shape": args.tile_shape,
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 302 MB > 129 MB L2, no flush needed",
                    "mflups": round(value * (c["solid"] == 0).mean(), 1),
@@ -386,6 +386,8 @@ def main():
     ap.add_argument("--prec", choices=["fp64", "fp32", "fp32dev", "fp16dev", "bf16dev"],
                     default="fp32")
     ap.add_argument("--kernel", choices=["auto", "tile", "strip"], default="auto")
+    ap.add_argument("--tile-shape", type=int, choices=[0, 1], default=0,
+                    help="tile of the TMA kernel: 0 = 32x16 (32x12 fp32dev), 1 = 32x8")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-steps", type=int, default=400,
                     help="steps of the 24-case batched section (0: skip it)")

@@ -77,7 +77,10 @@ typedef enum {
      * kernel pulling straight from global memory; 2 the row-sweeping strip
      * kernel staging rows with bulk copies; 3 the 2-D tile kernel staging
      * the tile and its ring with one tensor copy (not for FP64). */
-    MCLBM_FLAG_KERNEL = 3
+    MCLBM_FLAG_KERNEL = 3,
+    /* Tile of kernel 3: 0 (default) 32 x 16 nodes (32 x 12 for FP32_DEV),
+     * two CTAs per SM; 1: 32 x 8 nodes, three CTAs per SM.  Same results. */
+    MCLBM_FLAG_TILE_SHAPE = 4
 } mclbm_flag;
 
 typedef struct mclbm_lattice mclbm_lattice;

@@ -346,6 +346,10 @@ int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
             if (value < 0 || value > 3) return fail(MCLBM_ERR_ARG, "kernel must be 0..3");
             lat->kernel = value;
             return MCLBM_OK;
+        case MCLBM_FLAG_TILE_SHAPE:
+            if (value < 0 || value > 1) return fail(MCLBM_ERR_ARG, "tile shape must be 0 or 1");
+            lat->tile_shape = (int)value;
+            return MCLBM_OK;
         case MCLBM_FLAG_DIAG_EVERY:
             if (value < 0) return fail(MCLBM_ERR_ARG, "diag_every must be >= 0");
             lat->diag_every = value;

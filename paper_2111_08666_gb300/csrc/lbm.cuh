@@ -189,7 +189,8 @@ struct Lattice {
     size_t device_bytes = 0;
     bool boundary_rows_solid = false;
     bool initialised = false;
-    void *tmaps = nullptr;     // host copies of the TMA descriptors (tile kernel)
+    void *tmaps = nullptr;     // host copies of the TMA descriptors (tile kernel), both shapes
+    int tile_shape = 0;        // tile shape of the tile kernel (0 or 1)
     // work tables of the tile kernel, per tile shape: for every tile a
     // header and the packed entries of its fluid nodes, ring pulls and ring
     // solids; rebuilt with the ghosts whenever the boundary mode changes

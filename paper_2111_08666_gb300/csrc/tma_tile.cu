@@ -279,8 +279,11 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
                               f);
         };
 
-        // ---- A: densities of the ring's fluid nodes, then of the tile's own --
-        for (int k = tid; k < n_ring; k += NT) {
+        // ---- A: densities of the ring's fluid nodes and of the tile's own ------
+        // Thread t pulls tile node t (t < n_own); ring entries go first to the
+        // threads without a tile node (entry j to thread n_own + j mod NT), so
+        // that most threads pull once.
+        for (int k = tid - n_own + (tid < n_own ? NT : 0); k < n_ring; k += NT) {
             const uint32_t e = E[n_own + k];
             const int pos = (int)(e & 0xfffu);
             const int dr = pos / DXW, dc = pos - dr * DXW;
@@ -627,12 +630,13 @@ int tma_prepare(Lattice &L) {
         cudaGetLastError();
         return fail(MCLBM_ERR_NOMEM, "device allocation failed");
     }
-    CUtensorMap *maps = new (std::nothrow) CUtensorMap[MAPS_PER_CASE];
+    CUtensorMap *maps = new (std::nothrow) CUtensorMap[2 * MAPS_PER_CASE];
     if (!maps) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
-    if (int rc = encode_tile_maps(L, 0, maps)) {
-        delete[] maps;
-        return rc;
-    }
+    for (int s = 0; s < 2; ++s)
+        if (int rc = encode_tile_maps(L, s, maps + s * MAPS_PER_CASE)) {
+            delete[] maps;
+            return rc;
+        }
     L.tmaps = maps;
     return MCLBM_OK;
 }
@@ -693,7 +697,9 @@ cudaError_t launch_step_batch(Lattice *const *cases, int n, const void *maps, in
 
 cudaError_t launch_step_tma(Lattice &L) {
     Lattice *one = &L;
-    return launch_step_batch(&one, 1, L.tmaps, 0, 0, L.stream);
+    const int s = L.tile_shape;
+    return launch_step_batch(&one, 1, static_cast<const CUtensorMap *>(L.tmaps) + s * MAPS_PER_CASE,
+                             s, 0, L.stream);
 }
 
 }  // namespace mclbm

@@ -33,6 +33,7 @@ MCLBM_FLAG_PERIODIC_Y = 0
 MCLBM_FLAG_VEL_SHIFT = 1
 MCLBM_FLAG_DIAG_EVERY = 2
 MCLBM_FLAG_KERNEL = 3
+MCLBM_FLAG_TILE_SHAPE = 4
 
 DIAG_FIELDS = ("mass1", "mass2", "sw_count", "sw_mass", "p_in", "p_out", "pc", "n_fluid")
 
@@ -348,7 +349,7 @@ class Lattice:
                  nu2: float = 1 / 6, g_coh: float = 3.5, g_ads: float | None = None,
                  rho_in1: float = -1.0, rho_out2: float = -1.0, periodic_y: bool = False,
                  vel_shift: bool = True, gx: float = 0.0, gy: float = 0.0, stream=None,
-                 kernel: int = 0):
+                 kernel: int = 0, tile_shape: int = 0):
         self.h = None
         if isinstance(prec, str):
             prec = PRECISIONS[prec]
@@ -363,6 +364,7 @@ class Lattice:
         mclbm_set_flag(self.h, MCLBM_FLAG_VEL_SHIFT, int(vel_shift))
         mclbm_set_body_force(self.h, gx, gy)
         mclbm_set_flag(self.h, MCLBM_FLAG_KERNEL, kernel)
+        mclbm_set_flag(self.h, MCLBM_FLAG_TILE_SHAPE, tile_shape)
 
     def close(self) -> None:
         if getattr(self, "h", None) is not None:

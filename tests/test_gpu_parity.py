@@ -327,3 +327,31 @@ def test_tma_kernel_ghost_frames_fp32(periodic_y, open_x):
     o.step(300)
     g.step(300)
     assert rel_err(g.populations(), o.f) < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32dev", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("open_x", [False, True])
+def test_tile_shapes_agree(prec, open_x):
+    """The two tile shapes of the TMA kernel (32 x 16 or 32 x 12, and 32 x 8)
+    cut the lattice differently but compute the same update, on a lattice
+    off every tile multiple."""
+    nx, ny = 75, 41
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0] = solid[-1] = 1
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    solid[(xx - 50) ** 2 + (yy - 20) ** 2 <= 30] = 1
+    xi = media.uniform_xi(solid, -0.3)
+    kw = dict(prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), kernel=3)
+    if open_x:
+        rho1, rho2 = media.drainage_densities(solid)
+        kw.update(rho_in1=1.01, rho_out2=1.0)
+    else:
+        rho1, rho2 = media.droplet_densities(nx, ny, 20, 20, 9, solid=solid)
+    a = mclbm.Lattice(solid, xi, tile_shape=0, **kw)
+    b = mclbm.Lattice(solid, xi, tile_shape=1, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(200)
+    b.step(200)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= AGREE[prec][1] * np.max(np.abs(fa))
