@@ -287,6 +287,61 @@ int mclbm_batch_info(mclbm_batch *b, int64_t out[8]);
  * per tile). */
 int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[4]);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (spec extension of the quasi-static protocol of
+ * Sec. 4.2): a U-Net predicts the phase field of the next equilibrium.
+ *
+ * Network: levels L, base channels C0 (multiple of 32, at most 64),
+ * C_l = C0 2^l.  Encoder level l: conv3x3 + ReLU twice = e_l, 2x2 average
+ * pooling between levels.  Decoder level l = L-2..0: concat(e_l, nearest
+ * 2x upsampling of d_(l+1)) with the skip first (d_(L-1) = e_(L-1)), conv3x3
+ * + ReLU twice = d_l.  Head: 1x1 conv C0 -> 1, tanh.  Zero padding.
+ *
+ * Parameters: one flat FP32 vector in this order: enc0a, enc0b, ...,
+ * enc(L-1)a, enc(L-1)b, dec(L-2)a, dec(L-2)b, ..., dec0a, dec0b, head; each
+ * conv as weights [C_out][3][3][C_in] (head [1][1][1][C0]) then its bias
+ * [C_out]; C_in of enc0a is 8 (channels 4..7 of the input are zero).
+ *
+ * Inputs x [B][H][W][4] (FP32, NHWC): solid indicator (1 solid, 0 fluid),
+ * wettability xi (solid nodes, 0 elsewhere), current phase field
+ * (rho1 - rho2)/(rho1 + rho2), pressure step.  Output phi [B][H][W] in
+ * [-1, 1].  Loss: mean over the pixels with mask = 1 of (phi - target)^2.
+ * H and W are multiples of 2^(L-1).  Arithmetic: BF16 operands on the
+ * tensor cores with FP32 accumulation; FP32 master parameters and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * Buffers may be host or device memory.  Calls synchronise the network's
+ * stream before returning.
+ * ------------------------------------------------------------------------ */
+typedef struct mclbm_unet mclbm_unet;
+
+/* Network for batches up to max_batch of images up to max_h x max_w,
+ * parameters zero until mclbm_unet_set_params.  cuda_stream NULL: own
+ * stream. */
+int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w, void *cuda_stream,
+                      mclbm_unet **out);
+int mclbm_unet_destroy(mclbm_unet *u);
+int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n);
+/* Copy the parameter vector in (resets the Adam moments) or out. */
+int mclbm_unet_set_params(mclbm_unet *u, const float *theta);
+int mclbm_unet_get_params(mclbm_unet *u, float *theta);
+/* phi = network(x). */
+int mclbm_unet_infer(mclbm_unet *u, int batch, int h, int w, const float *x, float *phi);
+/* Loss and its gradient with respect to the parameters (no update); grad
+ * may be NULL. */
+int mclbm_unet_gradient(mclbm_unet *u, int batch, int h, int w, const float *x, const float *target,
+                        const float *mask, double *loss, float *grad);
+/* One Adam step with learning rate lr; *loss = the loss before the step. */
+int mclbm_unet_train_step(mclbm_unet *u, int batch, int h, int w, const float *x, const float *target,
+                          const float *mask, double lr, double *loss);
+
+/* Initialise the lattice at rest from a phase field phi [ny][nx] (FP32,
+ * host or device; read at fluid nodes): rho1 = rho_lo + (rho_hi -
+ * rho_lo)(1 + phi)/2, rho2 = rho_lo + (rho_hi - rho_lo)(1 - phi)/2 with
+ * rho_hi = 1 and rho_lo = 0.027 (the minority density of the separated
+ * phases at G = 3.5, Sec. 3.1), phi clamped to [-1, 1]; then as
+ * mclbm_init_densities. */
+int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi);
+
 /* Kernel launches enqueued by this library since it was loaded (all
  * lattices); used to count the GPU work inside a timed region. */
 int64_t mclbm_launch_count(void);

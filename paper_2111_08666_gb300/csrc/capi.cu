@@ -460,6 +460,34 @@ int mclbm_init_densities(mclbm_lattice *lat, const double *rho1, const double *r
     return MCLBM_OK;
 }
 
+int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi) {
+    if (int rc = check_lat(lat)) return rc;
+    if (!phi) return fail(MCLBM_ERR_ARG, "phi is NULL");
+    if (int rc = make_current(*lat)) return rc;
+    const size_t n = (size_t)lat->nx * lat->ny;
+    DeviceView vp;
+    if (int rc = view_in(*lat, phi, n * sizeof(float), vp)) return rc;
+    double *r = nullptr;
+    cudaError_t e = cudaMalloc((void **)&r, 2 * n * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+    // rho_hi = 1, rho_lo = 0.027: the separated phases at G = 3.5 (Sec. 3.1)
+    e = launch_phase_densities(*lat, static_cast<const float *>(vp.ptr), 1.0, 0.027, r, r + n);
+    if (e == cudaSuccess) {
+        lat->ghost_mode = -1;
+        if (int rc = refresh_ghosts(*lat)) {
+            cudaFree(r);
+            return rc;
+        }
+        e = launch_init_equilibrium(*lat, r, r + n);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    cudaFree(r);
+    if (e != cudaSuccess) return cuda_fail(e, "init from phase");
+    lat->initialised = true;
+    lat->steps = 0;
+    return MCLBM_OK;
+}
+
 int mclbm_set_populations(mclbm_lattice *lat, const double *f) {
     if (int rc = check_lat(lat)) return rc;
     if (!f) return fail(MCLBM_ERR_ARG, "f is NULL");

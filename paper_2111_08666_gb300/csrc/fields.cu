@@ -427,6 +427,25 @@ int diag_blocks_for(const Lattice &L) {
     return b < 1 ? 1 : (b > 1216 ? 1216 : b);
 }
 
+// Component densities from a phase field: rho1 = lo + (hi - lo)(1 + phi)/2,
+// rho2 = lo + (hi - lo)(1 - phi)/2, phi clamped to [-1, 1].
+__global__ void phase_densities_kernel(const float *phi, long long n, double hi, double lo, double *r1,
+                                       double *r2) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double p = fmin(1.0, fmax(-1.0, (double)phi[k]));
+    r1[k] = lo + (hi - lo) * (1.0 + p) * 0.5;
+    r2[k] = lo + (hi - lo) * (1.0 - p) * 0.5;
+}
+
+cudaError_t launch_phase_densities(Lattice &L, const float *phi, double hi, double lo, double *r1,
+                                   double *r2) {
+    const long long n = (long long)L.nx * L.ny;
+    phase_densities_kernel<<<blocks_for(n), BLK, 0, L.stream>>>(phi, n, hi, lo, r1, r2);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2) {
     const Geometry g = geometry_of(L);
     return dispatch(L, [&](auto tag) {

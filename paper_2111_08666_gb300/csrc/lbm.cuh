@@ -228,6 +228,8 @@ cudaError_t launch_step_batch(Lattice *const *cases, int n, const void *maps, in
 int batch_slots(mclbm_precision p, int shape);
 cudaError_t launch_geo_ghosts(Lattice &L);
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
+cudaError_t launch_phase_densities(Lattice &L, const float *phi, double hi, double lo, double *r1,
+                                   double *r2);
 cudaError_t launch_set_populations(Lattice &L, const double *f);
 cudaError_t launch_get_populations(Lattice &L, double *f);
 cudaError_t launch_diagnostics(Lattice &L);

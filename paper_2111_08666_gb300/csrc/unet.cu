@@ -1,0 +1,1043 @@
+// Learned warm start: a U-Net that predicts the phase field of the next
+// quasi-static equilibrium of a drainage step from (solid indicator,
+// wettability xi, current phase field, pressure step), trained on LBM
+// equilibria and used to initialise the next LBM relaxation.
+//
+// Network (levels L, base channels C0, C_l = C0 2^l), NHWC, BF16 storage of
+// weights and activations, FP32 accumulation and FP32 master weights:
+//   encoder l:  conv3x3 + ReLU, conv3x3 + ReLU = e_l; 2x2 average pooling
+//   decoder l:  concat(e_l, nearest-upsample(d_{l+1})) (skip first),
+//               conv3x3 + ReLU, conv3x3 + ReLU = d_l   (d_{L-1} = e_{L-1})
+//   head:       1x1 conv C0 -> 1, tanh
+// Loss: mean over the masked (fluid) pixels of (phi_hat - phi)^2; Adam.
+//
+// The three passes of every 3x3 convolution are implicit GEMMs on the
+// tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32):
+//   forward  C[pixel][co] = sum_(tap,ci) X[pixel + d_tap][ci] W[co][tap][ci]
+//   dgrad    C[pixel][ci] = sum_(tap,co) dZ[pixel - d_tap][co] W[co][tap][ci]
+//   wgrad    C[co][ci]    = sum_pixel dZ[pixel][co] X[pixel + d_tap][ci]  (per tap)
+// with operands gathered into shared memory by cp.async (zero fill at the
+// image border; the decoder's concat and upsampling are folded into the
+// gather) and fragments read with ldmatrix.  Pooling, the head, the loss and
+// Adam are elementwise kernels.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "async_copy.cuh"
+#include "lbm.cuh"
+
+using namespace mclbm;
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void ldsm4(uint32_t r[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t r[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+// c += a (16x16, row) * b (16x8, col)
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// 64-byte shared rows (32 BF16) of 4 16-byte chunks, XOR-swizzled so that
+// the 8 rows an ldmatrix reads fall in distinct banks
+__device__ __forceinline__ int sw64(int row, int chunk) {
+    return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
+}
+// 128-byte shared rows (64 BF16) of 8 chunks
+__device__ __forceinline__ int sw128(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
+
+// ---------------------------------------------------------------------------
+// Forward and data-gradient convolution: C[m][n] = sum_k A[m][k] B[n][k],
+// m = pixel (b, y, x), k = (tap, channel), n = output channel.
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const bf16 *x0, *x1;  // gathered input: x0 [B][H][W][c0]; x1 [B][H/2][W/2][c1] upsampled
+    int c0, c1;
+    int B, H, W, M;       // M = B H W
+    int sign;             // +1: taps read pixel + d; -1: pixel - d
+    const bf16 *w;        // [N][9][c0 + c1]
+    int N;
+    const float *bias;    // [N] or null
+    bf16 *ybf;            // ReLU(C + bias) as BF16 [M][N], or null
+    float *yf;            // C as FP32 [M][N], or null
+};
+
+constexpr int CBM = 128, CBK = 32;
+
+template <int BN>
+__global__ void __launch_bounds__(256) conv_kernel(const ConvArgs a) {
+    constexpr int WN = BN / 32;       // warps along n (warp tile n = 32)
+    constexpr int WMW = 8 / WN;       // warps along m
+    constexpr int WTM = CBM / WMW;    // warp tile m
+    constexpr int MT = WTM / 16;
+    __shared__ __align__(128) unsigned char sA[2][CBM * 64];
+    __shared__ __align__(128) unsigned char sB[2][BN * 64];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp % WMW, wn = warp / WMW;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+    const int K0 = a.c0 + a.c1;
+    const int kchunks = K0 / CBK;
+    const int ksteps = 9 * kchunks;
+
+    // rows of A this thread copies: tid/4 and tid/4 + 64, chunk tid % 4
+    int ab[2], ay[2], ax[2];
+    bool am[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int m = m0 + (tid >> 2) + j * 64;
+        am[j] = m < a.M;
+        const int mm = am[j] ? m : 0;
+        ax[j] = mm % a.W;
+        const int t = mm / a.W;
+        ay[j] = t % a.H;
+        ab[j] = t / a.H;
+    }
+    const int ach = tid & 3;
+    const int brow = tid >> 2, bch = tid & 3;
+    const bool bload = brow < BN;
+    const bool bvalid = bload && n0 + brow < a.N;
+
+    auto load = [&](int ks, int buf) {
+        const int tap = ks / kchunks, kc = ks - tap * kchunks;
+        const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
+        const int ci = kc * CBK + ach * 8;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int yy = ay[j] + dy, xx = ax[j] + dx;
+            const bool v = am[j] && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = a.x0;
+            if (v) {
+                if (ci < a.c0)
+                    src = a.x0 + ((size_t)(ab[j] * a.H + yy) * a.W + xx) * a.c0 + ci;
+                else
+                    src = a.x1 + ((size_t)(ab[j] * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
+                          (ci - a.c0);
+            }
+            cp_async16(sA[buf] + sw64((tid >> 2) + j * 64, ach), src, v);
+        }
+        if (bload) {
+            const bf16 *src = bvalid ? a.w + ((size_t)(n0 + brow) * 9 + tap) * K0 + kc * CBK + bch * 8 : a.w;
+            cp_async16(sB[buf] + sw64(brow, bch), src, bvalid);
+        }
+        cp_async_commit();
+    };
+
+    float acc[MT][4][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+    load(0, 0);
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < ksteps) {
+            load(ks + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            uint32_t af[MT][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+                ldsm4(af[mt], sA[buf] + sw64(wm * WTM + mt * 16 + (lane & 15), kk * 2 + (lane >> 4)));
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {
+                uint32_t r[4];
+                ldsm4(r, sB[buf] + sw64(wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3),
+                                        kk * 2 + ((lane >> 3) & 1)));
+                bfr[2 * np][0] = r[0];
+                bfr[2 * np][1] = r[1];
+                bfr[2 * np + 1][0] = r[2];
+                bfr[2 * np + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+        }
+        __syncthreads();
+    }
+
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm * WTM + mt * 16 + g + h * 8;
+                const int n = n0 + wn * 32 + nt * 8 + 2 * t4;
+                if (m >= a.M || n >= a.N) continue;
+                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
+                if (a.yf) *reinterpret_cast<float2 *>(a.yf + (size_t)m * a.N + n) = make_float2(v0, v1);
+                if (a.ybf) {
+                    if (a.bias) {
+                        v0 += a.bias[n];
+                        v1 += a.bias[n + 1];
+                    }
+                    *reinterpret_cast<__nv_bfloat162 *>(a.ybf + (size_t)m * a.N + n) =
+                        __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                }
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of one tap: dW[co][tap][ci] += sum_pixel dZ[p][co] X[p + d][ci]
+// over a chunk of pixels per CTA (atomic FP32 accumulation of the chunks).
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+    const bf16 *dz;
+    int co;
+    const bf16 *x0, *x1;
+    int c0, c1;
+    int B, H, W, M;
+    int chunk;
+    float *dw;  // [co][9][c0 + c1]
+};
+
+__global__ void __launch_bounds__(256) wgrad_kernel(const WgradArgs a) {
+    __shared__ __align__(128) unsigned char sA[2][32 * 128];  // [pixel][64 co]
+    __shared__ __align__(128) unsigned char sB[2][32 * 128];  // [pixel][64 ci]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;  // 2 x 4 warps, warp tile 32 x 16
+    const int tap = blockIdx.z % 9, part = blockIdx.z / 9;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    const int ci_all = a.c0 + a.c1;
+    const int p_begin = part * a.chunk;
+    const int p_end = min(a.M, p_begin + a.chunk);
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int row = tid >> 3, ch = tid & 7;
+    const bool a_col = m0 + ch * 8 < a.co;
+    const int cin = n0 + ch * 8;
+    const bool b_col = cin < ci_all;
+    const int ksteps = (p_end - p_begin + 31) / 32;
+
+    auto load = [&](int ks, int buf) {
+        const int p = p_begin + ks * 32 + row;
+        const bool pv = p < p_end;
+        const bool va = pv && a_col;
+        cp_async16(sA[buf] + sw128(row, ch), va ? a.dz + (size_t)p * a.co + m0 + ch * 8 : a.dz, va);
+        bool vb = pv && b_col;
+        const bf16 *src = a.x0;
+        if (vb) {
+            const int x = p % a.W, t = p / a.W, y = t % a.H, b = t / a.H;
+            const int yy = y + dy, xx = x + dx;
+            vb = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            if (vb) {
+                if (cin < a.c0)
+                    src = a.x0 + ((size_t)(b * a.H + yy) * a.W + xx) * a.c0 + cin;
+                else
+                    src = a.x1 + ((size_t)(b * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
+                          (cin - a.c0);
+            }
+        }
+        cp_async16(sB[buf] + sw128(row, ch), src, vb);
+        cp_async_commit();
+    };
+
+    float acc[2][2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+    if (ksteps > 0) load(0, 0);
+    for (int ks = 0; ks < ksteps; ++ks) {
+        const int buf = ks & 1;
+        if (ks + 1 < ksteps) {
+            load(ks + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const int bi = lane >> 3, r = lane & 7;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            uint32_t af[2][4], bq[4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+                ldsm4t(af[mt], sA[buf] + sw128(kk * 16 + (bi >> 1) * 8 + r, (wm * 32 + mt * 16 + (bi & 1) * 8) >> 3));
+            ldsm4t(bq, sB[buf] + sw128(kk * 16 + (bi & 1) * 8 + r, (wn * 16 + (bi >> 1) * 8) >> 3));
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                mma_bf16(acc[mt][0], af[mt], bq[0], bq[1]);
+                mma_bf16(acc[mt][1], af[mt], bq[2], bq[3]);
+            }
+        }
+        __syncthreads();
+    }
+
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm * 32 + mt * 16 + g + h * 8;
+                const int n = n0 + wn * 16 + nt * 8 + 2 * t4;
+                if (m >= a.co || n >= ci_all) continue;
+                float *d = a.dw + ((size_t)m * 9 + tap) * ci_all + n;
+                atomicAdd(d, acc[mt][nt][2 * h]);
+                atomicAdd(d + 1, acc[mt][nt][2 * h + 1]);
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise kernels
+// ---------------------------------------------------------------------------
+#define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
+                                i += (long long)gridDim.x * blockDim.x)
+
+// network input: 4 FP32 channels per pixel -> BF16 padded to cpad channels
+__global__ void pack_input_kernel(const float *x, bf16 *out, long long P, int cpad) {
+    GRID_STRIDE(i, P * cpad) {
+        const long long p = i / cpad;
+        const int c = (int)(i % cpad);
+        out[i] = __float2bfloat16_rn(c < 4 ? x[p * 4 + c] : 0.f);
+    }
+}
+
+// 2x2 average pooling, NHWC
+__global__ void pool_kernel(const bf16 *in, bf16 *out, int B, int H, int W, int C) {
+    const int h2 = H / 2, w2 = W / 2;
+    GRID_STRIDE(i, (long long)B * h2 * w2 * C) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int x = (int)(t % w2);
+        t /= w2;
+        const int y = (int)(t % h2);
+        const int b = (int)(t / h2);
+        auto at = [&](int yy, int xx) {
+            return __bfloat162float(in[(((long long)b * H + yy) * W + xx) * C + c]);
+        };
+        const float s = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
+        out[i] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// head: phi = tanh(d . w + b)
+__global__ void head_forward_kernel(const bf16 *d, const float *wb, int C, long long P, float *phi) {
+    GRID_STRIDE(p, P) {
+        float z = wb[C];
+        for (int c = 0; c < C; ++c) z += __bfloat162float(d[p * C + c]) * wb[c];
+        phi[p] = tanhf(z);
+    }
+}
+
+// per-block partial sums of (mask, mask (phi - t)^2) for the loss (pass 1)
+__global__ void loss_partial_kernel(const float *phi, const float *t, const float *mask, long long P,
+                                    double *part) {
+    __shared__ double s0[256], s1[256];
+    double a = 0, b = 0;
+    GRID_STRIDE(p, P) {
+        const double m = mask[p];
+        const double r = (double)phi[p] - (double)t[p];
+        a += m;
+        b += m * r * r;
+    }
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            s0[threadIdx.x] += s0[threadIdx.x + s];
+            s1[threadIdx.x] += s1[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s0[0];
+        part[2 * blockIdx.x + 1] = s1[0];
+    }
+}
+
+// pass 2: out[0] = number of masked pixels (at least 1), out[1] = loss
+__global__ void loss_final_kernel(const double *part, int nblocks, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0, b = 0;
+    for (int k = 0; k < nblocks; ++k) {
+        a += part[2 * k];
+        b += part[2 * k + 1];
+    }
+    const double n = a > 1.0 ? a : 1.0;
+    out[0] = n;
+    out[1] = b / n;
+}
+
+// head backward: dz = dL/dphi (1 - phi^2) with dL/dphi = 2 mask (phi - t) / n;
+// dd[p][c] = dz w[c]; gradients of the head weights and bias (block sums)
+__global__ void head_backward_kernel(const float *phi, const float *t, const float *mask, const double *stat,
+                                     const bf16 *d, const float *wb, int C, long long P, float *dd,
+                                     float *gwb) {
+    const float inv_n = (float)(1.0 / stat[0]);
+    float acc[65];
+    for (int c = 0; c <= C; ++c) acc[c] = 0.f;
+    GRID_STRIDE(p, P) {
+        const float f = phi[p];
+        const float dz = 2.f * mask[p] * (f - t[p]) * inv_n * (1.f - f * f);
+        for (int c = 0; c < C; ++c) {
+            dd[p * C + c] = dz * wb[c];
+            acc[c] += dz * __bfloat162float(d[p * C + c]);
+        }
+        acc[C] += dz;
+    }
+    // warp sums, then one atomic per warp and value
+    for (int c = 0; c <= C; ++c) {
+        float v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(gwb + c, v);
+    }
+}
+
+// dz = g (h > 0), as BF16 (h: the ReLU output the gradient flows into)
+__global__ void relu_mask_kernel(const float *g, const bf16 *h, bf16 *dz, long long n) {
+    GRID_STRIDE(i, n) dz[i] = __float2bfloat16_rn(__bfloat162float(h[i]) > 0.f ? g[i] : 0.f);
+}
+
+// decoder concat backward: de [P][cs] += dcat[:, :cs]; dd (coarse
+// [B][H/2][W/2][cu]) = sum over the 2x2 block of dcat[:, cs:]
+__global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, int H, int W, float *de,
+                                    float *dd) {
+    const int ct = cs + cu;
+    GRID_STRIDE(i, (long long)B * H * W * cs) {
+        const long long p = i / cs;
+        const int c = (int)(i % cs);
+        de[i] += dcat[p * ct + c];
+    }
+    const int h2 = H / 2, w2 = W / 2;
+    GRID_STRIDE(i, (long long)B * h2 * w2 * cu) {
+        const int c = (int)(i % cu);
+        long long t = i / cu;
+        const int x = (int)(t % w2);
+        t /= w2;
+        const int y = (int)(t % h2);
+        const int b = (int)(t / h2);
+        float s = 0.f;
+        for (int a = 0; a < 2; ++a)
+            for (int e = 0; e < 2; ++e)
+                s += dcat[(((long long)b * H + 2 * y + a) * W + 2 * x + e) * ct + cs + c];
+        dd[i] = s;
+    }
+}
+
+// encoder pooling backward: de_fine [B][H][W][C] += dx_coarse / 4
+__global__ void pool_backward_add_kernel(const float *dx, int B, int H, int W, int C, float *de) {
+    GRID_STRIDE(i, (long long)B * H * W * C) {
+        const int c = (int)(i % C);
+        long long t = i / C;
+        const int x = (int)(t % W);
+        t /= W;
+        const int y = (int)(t % H);
+        const int b = (int)(t / H);
+        de[i] += 0.25f * dx[(((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+    }
+}
+
+__global__ void add_kernel(float *a, const float *b, long long n) {
+    GRID_STRIDE(i, n) a[i] += b[i];
+}
+
+// FP32 master weights [co][3][3][ci] -> BF16 [co][9][cpad] (forward) and
+// [cpad][9][co] (data gradient), zero in the padded channels
+__global__ void weights_bf16_kernel(const float *w, int co, int ci, int cpad, bf16 *wf, bf16 *wt) {
+    GRID_STRIDE(i, (long long)co * 9 * cpad) {
+        const int c = (int)(i % cpad);
+        const long long t = i / cpad;
+        const int tap = (int)(t % 9);
+        const int o = (int)(t / 9);
+        const float v = c < ci ? w[((long long)o * 9 + tap) * ci + c] : 0.f;
+        const bf16 h = __float2bfloat16_rn(v);
+        wf[i] = h;
+        if (wt) wt[((long long)c * 9 + tap) * co + o] = h;
+    }
+}
+
+// padded weight gradient [co][9][cpad] -> flat [co][3][3][ci]
+__global__ void grad_pack_kernel(const float *dw, int co, int ci, int cpad, float *g) {
+    GRID_STRIDE(i, (long long)co * 9 * ci) {
+        const int c = (int)(i % ci);
+        const long long t = i / ci;
+        g[i] = dw[t * cpad + c];
+    }
+}
+
+// per-channel sums of a BF16 [P][C] gradient (bias gradient)
+__global__ void bias_grad_kernel(const bf16 *dz, long long P, int C, float *gb) {
+    // thread handles channel threadIdx.x % C over a strided set of pixels
+    const int c = threadIdx.x % C;
+    const int lanes = blockDim.x / C;
+    const int sub = threadIdx.x / C;
+    if (sub >= lanes) return;
+    float s = 0.f;
+    for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes)
+        s += __bfloat162float(dz[p * C + c]);
+    atomicAdd(gb + c, s);
+}
+
+// Adam (bias-corrected), in place on the FP32 master parameters
+__global__ void adam_kernel(float *theta, const float *g, float *m, float *v, long long n, float lr, float b1,
+                            float b2, float eps, float bc1, float bc2) {
+    GRID_STRIDE(i, n) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+int blocks_for(long long n, int per = 256) {
+    long long b = (n + per - 1) / per;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The network object
+// ---------------------------------------------------------------------------
+constexpr int UNET_IN = 8;     // input channels of the parameter layout (4 used, 4 zero)
+constexpr int UNET_PAD0 = 32;  // input channels on the device (multiple of the GEMM k-chunk)
+
+struct UnetLayer {
+    int co, ci, cpad, k;     // k = 3 (conv3x3) or 1 (head)
+    long long off;           // offset of the weights in the flat parameter vector; bias follows
+    bf16 *wf = nullptr, *wt = nullptr;
+    float *dw = nullptr;     // [co][9][cpad]
+};
+
+struct mclbm_unet {
+    int levels = 0, base = 0, max_b = 0, max_h = 0, max_w = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<UnetLayer> layers;  // parameter order
+    long long nparam = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    long long adam_t = 0;
+    std::vector<bf16 *> a_in, e_ha, e_out, d_ha, d_out;  // per level
+    std::vector<float *> de;                              // per level
+    float *phi = nullptr, *s1 = nullptr, *s2 = nullptr, *dd = nullptr;
+    bf16 *z = nullptr;
+    float *xin_f = nullptr, *t_f = nullptr, *mask_f = nullptr;  // staging of host inputs
+    double *loss_part = nullptr, *loss_stat = nullptr;
+    std::vector<void *> allocs;
+    int cur_b = 0, cur_h = 0, cur_w = 0;
+};
+
+namespace {
+
+constexpr int LOSS_BLOCKS = 256;
+
+int ch(const mclbm_unet &u, int l) { return u.base << l; }
+
+int ualloc(mclbm_unet &u, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(unet)");
+    u.allocs.push_back(*p);
+    return MCLBM_OK;
+}
+
+void unet_release(mclbm_unet *u) {
+    if (!u) return;
+    if (u->stream) cudaStreamSynchronize(u->stream);
+    for (void *p : u->allocs) cudaFree(p);
+    if (u->own_stream && u->stream) cudaStreamDestroy(u->stream);
+    delete u;
+}
+
+cudaError_t launch_conv(const mclbm_unet &u, const ConvArgs &a) {
+    const dim3 grid((a.M + CBM - 1) / CBM, a.N % 64 == 0 ? a.N / 64 : (a.N + 31) / 32);
+    if (a.N % 64 == 0)
+        conv_kernel<64><<<grid, 256, 0, u.stream>>>(a);
+    else
+        conv_kernel<32><<<grid, 256, 0, u.stream>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(const mclbm_unet &u, WgradArgs a) {
+    a.chunk = 4096;
+    const int parts = (a.M + a.chunk - 1) / a.chunk;
+    const dim3 grid((a.co + 63) / 64, (a.c0 + a.c1 + 63) / 64, 9 * parts);
+    wgrad_kernel<<<grid, 256, 0, u.stream>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// conv input description: x0 (c0 channels) and optionally the upsampled x1
+struct In {
+    const bf16 *x0, *x1;
+    int c0, c1;
+};
+
+// forward of conv layer li on input `in` at (B, H, W): y = ReLU(conv + b)
+cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W, bf16 *y) {
+    const UnetLayer &L = u.layers[li];
+    ConvArgs a{};
+    a.x0 = in.x0;
+    a.x1 = in.x1;
+    a.c0 = in.c0;
+    a.c1 = in.c1;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.M = B * H * W;
+    a.sign = 1;
+    a.w = L.wf;
+    a.N = L.co;
+    a.bias = u.theta + L.off + (long long)L.co * 9 * L.ci;
+    a.ybf = y;
+    a.yf = nullptr;
+    return launch_conv(u, a);
+}
+
+// backward of conv layer li: dz (BF16 [P][co]) -> weight and bias gradients,
+// and, if dx, the input gradient (FP32 [P][cpad])
+cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, const bf16 *dz, float *dx) {
+    UnetLayer &L = u.layers[li];
+    const int M = B * H * W;
+    cudaError_t e = cudaMemsetAsync(L.dw, 0, (size_t)L.co * 9 * L.cpad * sizeof(float), u.stream);
+    if (e != cudaSuccess) return e;
+    WgradArgs w{};
+    w.dz = dz;
+    w.co = L.co;
+    w.x0 = in.x0;
+    w.x1 = in.x1;
+    w.c0 = in.c0;
+    w.c1 = in.c1;
+    w.B = B;
+    w.H = H;
+    w.W = W;
+    w.M = M;
+    w.dw = L.dw;
+    if ((e = launch_wgrad(u, w)) != cudaSuccess) return e;
+    float *gw = u.grad + L.off;
+    grad_pack_kernel<<<blocks_for((long long)L.co * 9 * L.ci), 256, 0, u.stream>>>(L.dw, L.co, L.ci, L.cpad, gw);
+    float *gb = gw + (long long)L.co * 9 * L.ci;
+    e = cudaMemsetAsync(gb, 0, L.co * sizeof(float), u.stream);
+    if (e != cudaSuccess) return e;
+    bias_grad_kernel<<<256, 256, 0, u.stream>>>(dz, M, L.co, gb);
+    count_launch(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!dx) return cudaSuccess;
+    ConvArgs a{};
+    a.x0 = dz;
+    a.x1 = nullptr;
+    a.c0 = L.co;
+    a.c1 = 0;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.M = M;
+    a.sign = -1;
+    a.w = L.wt;
+    a.N = L.cpad;
+    a.bias = nullptr;
+    a.ybf = nullptr;
+    a.yf = dx;
+    return launch_conv(u, a);
+}
+
+cudaError_t refresh_weights(mclbm_unet &u) {
+    for (auto &L : u.layers) {
+        if (L.k != 3) continue;
+        weights_bf16_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
+            u.theta + L.off, L.co, L.ci, L.cpad, L.wf, L.wt);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t forward(mclbm_unet &u, int B, int H, int W) {
+    const int Lv = u.levels;
+    cudaError_t e = cudaSuccess;
+    // encoder
+    for (int l = 0; l < Lv && e == cudaSuccess; ++l) {
+        const int h = H >> l, w = W >> l;
+        if (l > 0) {
+            pool_kernel<<<blocks_for((long long)B * h * w * ch(u, l - 1)), 256, 0, u.stream>>>(
+                u.e_out[l - 1], u.a_in[l], B, 2 * h, 2 * w, ch(u, l - 1));
+            count_launch();
+        }
+        const In ina{u.a_in[l], nullptr, l == 0 ? UNET_PAD0 : ch(u, l - 1), 0};
+        if ((e = conv_forward(u, 2 * l, ina, B, h, w, u.e_ha[l])) != cudaSuccess) break;
+        const In inb{u.e_ha[l], nullptr, ch(u, l), 0};
+        e = conv_forward(u, 2 * l + 1, inb, B, h, w, u.e_out[l]);
+    }
+    // decoder, coarse to fine
+    int li = 2 * Lv;
+    for (int l = Lv - 2; l >= 0 && e == cudaSuccess; --l, li += 2) {
+        const int h = H >> l, w = W >> l;
+        const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
+        const In ina{u.e_out[l], coarse, ch(u, l), ch(u, l + 1)};
+        if ((e = conv_forward(u, li, ina, B, h, w, u.d_ha[l])) != cudaSuccess) break;
+        const In inb{u.d_ha[l], nullptr, ch(u, l), 0};
+        e = conv_forward(u, li + 1, inb, B, h, w, u.d_out[l]);
+    }
+    if (e != cudaSuccess) return e;
+    const UnetLayer &hd = u.layers.back();
+    const long long P = (long long)B * H * W;
+    const bf16 *d0 = Lv > 1 ? u.d_out[0] : u.e_out[0];
+    head_forward_kernel<<<blocks_for(P), 256, 0, u.stream>>>(d0, u.theta + hd.off, u.base, P, u.phi);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
+    const int Lv = u.levels;
+    const long long P = (long long)B * H * W;
+    const UnetLayer &hd = u.layers.back();
+    cudaError_t e = cudaMemsetAsync(u.grad + hd.off, 0, (u.base + 1) * sizeof(float), u.stream);
+    if (e != cudaSuccess) return e;
+    const bf16 *d0 = Lv > 1 ? u.d_out[0] : u.e_out[0];
+    head_backward_kernel<<<blocks_for(P), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
+                                                              u.theta + hd.off, u.base, P, u.dd,
+                                                              u.grad + hd.off);
+    count_launch();
+    for (int l = 0; l < Lv; ++l) {
+        const long long n = (P >> (2 * l)) * ch(u, l);
+        if ((e = cudaMemsetAsync(u.de[l], 0, n * sizeof(float), u.stream)) != cudaSuccess) return e;
+    }
+    // decoder, fine to coarse: the layer index of dec(l)a is 2L + 2 (L - 2 - l)
+    for (int l = 0; l <= Lv - 2; ++l) {
+        const int h = H >> l, w = W >> l;
+        const long long Pl = (long long)B * h * w;
+        const int cl = ch(u, l), cu = ch(u, l + 1);
+        const int li = 2 * Lv + 2 * (Lv - 2 - l);
+        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.dd, u.d_out[l], u.z, Pl * cl);
+        count_launch();
+        if ((e = conv_backward(u, li + 1, In{u.d_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
+            return e;
+        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s2, u.d_ha[l], u.z, Pl * cl);
+        count_launch();
+        const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
+        if ((e = conv_backward(u, li, In{u.e_out[l], coarse, cl, cu}, B, h, w, u.z, u.s1)) != cudaSuccess)
+            return e;
+        split_concat_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l], u.dd);
+        count_launch();
+    }
+    if (Lv > 1) {
+        const long long n = (P >> (2 * (Lv - 1))) * ch(u, Lv - 1);
+        add_kernel<<<blocks_for(n), 256, 0, u.stream>>>(u.de[Lv - 1], u.dd, n);
+        count_launch();
+    } else {
+        const long long n = P * ch(u, 0);
+        add_kernel<<<blocks_for(n), 256, 0, u.stream>>>(u.de[0], u.dd, n);
+        count_launch();
+    }
+    // encoder, coarse to fine
+    for (int l = Lv - 1; l >= 0; --l) {
+        const int h = H >> l, w = W >> l;
+        const long long Pl = (long long)B * h * w;
+        const int cl = ch(u, l);
+        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.de[l], u.e_out[l], u.z, Pl * cl);
+        count_launch();
+        if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
+            return e;
+        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s2, u.e_ha[l], u.z, Pl * cl);
+        count_launch();
+        const int cin = l == 0 ? UNET_PAD0 : ch(u, l - 1);
+        if ((e = conv_backward(u, 2 * l, In{u.a_in[l], nullptr, cin, 0}, B, h, w, u.z, l > 0 ? u.s1 : nullptr)) !=
+            cudaSuccess)
+            return e;
+        if (l > 0) {
+            const int cp = ch(u, l - 1);
+            pool_backward_add_kernel<<<blocks_for(4 * Pl * cp), 256, 0, u.stream>>>(u.s1, B, 2 * h, 2 * w, cp,
+                                                                                  u.de[l - 1]);
+            count_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
+bool dev_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// copy a caller buffer (host or device) into a device staging buffer
+cudaError_t stage_in(const mclbm_unet &u, float *dst, const float *src, size_t n) {
+    return cudaMemcpyAsync(dst, src, n * sizeof(float), dev_ptr(src) ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyHostToDevice,
+                           u.stream);
+}
+cudaError_t stage_out(const mclbm_unet &u, float *dst, const float *src, size_t n) {
+    return cudaMemcpyAsync(dst, src, n * sizeof(float), dev_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                                      : cudaMemcpyDeviceToHost,
+                           u.stream);
+}
+
+int check_shape(const mclbm_unet *u, int B, int H, int W) {
+    if (!u) return fail(MCLBM_ERR_ARG, "network is NULL");
+    const int q = 1 << (u->levels - 1);
+    if (B < 1 || H < q || W < q || B > u->max_b || H > u->max_h || W > u->max_w)
+        return fail(MCLBM_ERR_ARG, "batch or image size outside the sizes the network was created for");
+    if (H % q || W % q) return fail(MCLBM_ERR_ARG, "image sides must be multiples of 2^(levels-1)");
+    if ((long long)B * H * W > (long long)u->max_b * u->max_h * u->max_w)
+        return fail(MCLBM_ERR_ARG, "too many pixels");
+    return MCLBM_OK;
+}
+
+// stage inputs, pack, forward (and the loss when targets are given)
+int run_forward(mclbm_unet *u, int B, int H, int W, const float *x, const float *target, const float *mask) {
+    const long long P = (long long)B * H * W;
+    cudaError_t e = stage_in(*u, u->xin_f, x, (size_t)P * 4);
+    if (e == cudaSuccess && target) e = stage_in(*u, u->t_f, target, (size_t)P);
+    if (e == cudaSuccess && target) e = stage_in(*u, u->mask_f, mask, (size_t)P);
+    if (e != cudaSuccess) return cuda_fail(e, "unet input copy");
+    pack_input_kernel<<<blocks_for(P * UNET_PAD0), 256, 0, u->stream>>>(u->xin_f, u->a_in[0], P, UNET_PAD0);
+    count_launch();
+    if ((e = forward(*u, B, H, W)) != cudaSuccess) return cuda_fail(e, "unet forward");
+    if (target) {
+        loss_partial_kernel<<<LOSS_BLOCKS, 256, 0, u->stream>>>(u->phi, u->t_f, u->mask_f, P, u->loss_part);
+        loss_final_kernel<<<1, 32, 0, u->stream>>>(u->loss_part, LOSS_BLOCKS, u->loss_stat);
+        count_launch(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "unet loss");
+    }
+    return MCLBM_OK;
+}
+
+int read_loss(mclbm_unet *u, double *loss) {
+    double st[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(st, u->loss_stat, sizeof(st), cudaMemcpyDeviceToHost, u->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "unet loss read-back");
+    if (loss) *loss = st[1];
+    return MCLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w, void *cuda_stream,
+                      mclbm_unet **out) {
+    if (!out) return fail(MCLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (levels < 1 || levels > 6) return fail(MCLBM_ERR_ARG, "levels must be 1..6");
+    if (base < 32 || base % 32 || (base << (levels - 1)) > 1024)
+        return fail(MCLBM_ERR_ARG, "base channels must be a multiple of 32 (and C0 2^(L-1) <= 1024)");
+    if (base > 64) return fail(MCLBM_ERR_ARG, "base channels above 64 are not supported by the head");
+    const int q = 1 << (levels - 1);
+    if (max_batch < 1 || max_h < q || max_w < q || max_h % q || max_w % q)
+        return fail(MCLBM_ERR_ARG, "maximum sizes must be positive multiples of 2^(levels-1)");
+    mclbm_unet *u = new (std::nothrow) mclbm_unet;
+    if (!u) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
+    u->levels = levels;
+    u->base = base;
+    u->max_b = max_batch;
+    u->max_h = max_h;
+    u->max_w = max_w;
+    if (cuda_stream) {
+        u->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&u->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete u;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        u->own_stream = true;
+    }
+    // layers in parameter order
+    long long off = 0;
+    auto add = [&](int co, int ci, int k) {
+        UnetLayer L;
+        L.co = co;
+        L.ci = ci;
+        L.cpad = ci == UNET_IN ? UNET_PAD0 : ci;
+        L.k = k;
+        L.off = off;
+        off += (long long)co * k * k * ci + co;
+        u->layers.push_back(L);
+    };
+    for (int l = 0; l < levels; ++l) {
+        add(base << l, l == 0 ? UNET_IN : base << (l - 1), 3);
+        add(base << l, base << l, 3);
+    }
+    for (int l = levels - 2; l >= 0; --l) {
+        add(base << l, (base << l) + (base << (l + 1)), 3);
+        add(base << l, base << l, 3);
+    }
+    add(1, base, 1);
+    u->nparam = off;
+    const long long P = (long long)max_batch * max_h * max_w;
+    int rc = MCLBM_OK;
+    auto A = [&](void **p, size_t bytes) {
+        if (rc == MCLBM_OK) rc = ualloc(*u, p, bytes);
+    };
+    A((void **)&u->theta, u->nparam * 4);
+    A((void **)&u->grad, u->nparam * 4);
+    A((void **)&u->m, u->nparam * 4);
+    A((void **)&u->v, u->nparam * 4);
+    for (auto &L : u->layers) {
+        if (L.k != 3) continue;
+        A((void **)&L.wf, (size_t)L.co * 9 * L.cpad * 2);
+        A((void **)&L.wt, (size_t)L.co * 9 * L.cpad * 2);
+        A((void **)&L.dw, (size_t)L.co * 9 * L.cpad * 4);
+    }
+    u->a_in.assign(levels, nullptr);
+    u->e_ha.assign(levels, nullptr);
+    u->e_out.assign(levels, nullptr);
+    u->d_ha.assign(levels, nullptr);
+    u->d_out.assign(levels, nullptr);
+    u->de.assign(levels, nullptr);
+    for (int l = 0; l < levels; ++l) {
+        const long long Pl = P >> (2 * l);
+        const int cl = base << l;
+        A((void **)&u->a_in[l], (size_t)Pl * (l == 0 ? UNET_PAD0 : base << (l - 1)) * 2);
+        A((void **)&u->e_ha[l], (size_t)Pl * cl * 2);
+        A((void **)&u->e_out[l], (size_t)Pl * cl * 2);
+        A((void **)&u->de[l], (size_t)Pl * cl * 4);
+        if (l < levels - 1) {
+            A((void **)&u->d_ha[l], (size_t)Pl * cl * 2);
+            A((void **)&u->d_out[l], (size_t)Pl * cl * 2);
+        }
+    }
+    A((void **)&u->phi, P * 4);
+    A((void **)&u->s1, (size_t)P * 3 * base * 4);
+    A((void **)&u->s2, (size_t)P * UNET_PAD0 * 4 + (size_t)P * base * 4);
+    A((void **)&u->dd, (size_t)P * base * 4);
+    A((void **)&u->z, (size_t)P * base * 2);
+    A((void **)&u->xin_f, (size_t)P * 4 * 4);
+    A((void **)&u->t_f, (size_t)P * 4);
+    A((void **)&u->mask_f, (size_t)P * 4);
+    A((void **)&u->loss_part, LOSS_BLOCKS * 2 * sizeof(double));
+    A((void **)&u->loss_stat, 2 * sizeof(double));
+    if (rc == MCLBM_OK) {
+        cudaError_t e = cudaMemsetAsync(u->theta, 0, u->nparam * 4, u->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, u->nparam * 4, u->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "unet initialisation");
+    }
+    if (rc != MCLBM_OK) {
+        unet_release(u);
+        return rc;
+    }
+    *out = u;
+    return MCLBM_OK;
+}
+
+int mclbm_unet_destroy(mclbm_unet *u) {
+    unet_release(u);
+    return MCLBM_OK;
+}
+
+int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n) {
+    if (!u || !n) return fail(MCLBM_ERR_ARG, "NULL argument");
+    *n = u->nparam;
+    return MCLBM_OK;
+}
+
+int mclbm_unet_set_params(mclbm_unet *u, const float *theta) {
+    if (!u || !theta) return fail(MCLBM_ERR_ARG, "NULL argument");
+    cudaError_t e = stage_in(*u, u->theta, theta, (size_t)u->nparam);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, u->nparam * 4, u->stream);
+    if (e == cudaSuccess) e = refresh_weights(*u);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "unet parameters");
+    u->adam_t = 0;
+    return MCLBM_OK;
+}
+
+int mclbm_unet_get_params(mclbm_unet *u, float *theta) {
+    if (!u || !theta) return fail(MCLBM_ERR_ARG, "NULL argument");
+    cudaError_t e = stage_out(*u, theta, u->theta, (size_t)u->nparam);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "unet parameters");
+    return MCLBM_OK;
+}
+
+int mclbm_unet_infer(mclbm_unet *u, int batch, int h, int w, const float *x, float *phi) {
+    if (int rc = check_shape(u, batch, h, w)) return rc;
+    if (!x || !phi) return fail(MCLBM_ERR_ARG, "NULL argument");
+    if (int rc = run_forward(u, batch, h, w, x, nullptr, nullptr)) return rc;
+    cudaError_t e = stage_out(*u, phi, u->phi, (size_t)batch * h * w);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "unet output");
+    return MCLBM_OK;
+}
+
+int mclbm_unet_gradient(mclbm_unet *u, int batch, int h, int w, const float *x, const float *target,
+                        const float *mask, double *loss, float *grad) {
+    if (int rc = check_shape(u, batch, h, w)) return rc;
+    if (!x || !target || !mask) return fail(MCLBM_ERR_ARG, "NULL argument");
+    if (int rc = run_forward(u, batch, h, w, x, target, mask)) return rc;
+    cudaError_t e = backward(*u, batch, h, w);
+    if (e != cudaSuccess) return cuda_fail(e, "unet backward");
+    if (grad && (e = stage_out(*u, grad, u->grad, (size_t)u->nparam)) != cudaSuccess)
+        return cuda_fail(e, "unet gradient copy");
+    return read_loss(u, loss);
+}
+
+int mclbm_unet_train_step(mclbm_unet *u, int batch, int h, int w, const float *x, const float *target,
+                          const float *mask, double lr, double *loss) {
+    if (int rc = check_shape(u, batch, h, w)) return rc;
+    if (!x || !target || !mask) return fail(MCLBM_ERR_ARG, "NULL argument");
+    if (!(lr > 0) || !std::isfinite(lr)) return fail(MCLBM_ERR_ARG, "learning rate must be positive");
+    if (int rc = run_forward(u, batch, h, w, x, target, mask)) return rc;
+    cudaError_t e = backward(*u, batch, h, w);
+    if (e != cudaSuccess) return cuda_fail(e, "unet backward");
+    ++u->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)u->adam_t));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)u->adam_t));
+    adam_kernel<<<blocks_for(u->nparam), 256, 0, u->stream>>>(u->theta, u->grad, u->m, u->v, u->nparam, (float)lr,
+                                                             b1, b2, 1e-8f, bc1, bc2);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = refresh_weights(*u)) != cudaSuccess)
+        return cuda_fail(e, "unet update");
+    return read_loss(u, loss);
+}
+
+}  // extern "C"

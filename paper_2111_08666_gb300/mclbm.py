@@ -89,6 +89,17 @@ _SIGS = {
     "mclbm_batch_tuning": (C.c_int, [_vp, _vp]),
     "mclbm_diagnostics_noalloc": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_double, C.c_int,
                                             _vp, _vp]),
+    "mclbm_unet_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _P(_vp)]),
+    "mclbm_unet_destroy": (C.c_int, [_vp]),
+    "mclbm_unet_param_count": (C.c_int, [_vp, _P(_i64)]),
+    "mclbm_unet_set_params": (C.c_int, [_vp, _vp]),
+    "mclbm_unet_get_params": (C.c_int, [_vp, _vp]),
+    "mclbm_unet_infer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "mclbm_unet_gradient": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
+                                      _P(C.c_double), _vp]),
+    "mclbm_unet_train_step": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
+                                        C.c_double, _P(C.c_double)]),
+    "mclbm_init_from_phase": (C.c_int, [_vp, _vp]),
     "mclbm_launch_count": (_i64, []),
     "mclbm_last_error": (C.c_char_p, []),
 }
@@ -202,6 +213,10 @@ def mclbm_set_stream(h, stream) -> None:
 
 def mclbm_init_densities(h, rho1, rho2) -> None:
     _check(load().mclbm_init_densities(h, _addr(rho1, np.float64), _addr(rho2, np.float64)))
+
+
+def mclbm_init_from_phase(h, phi) -> None:
+    _check(load().mclbm_init_from_phase(h, _addr(phi, np.float32)))
 
 
 def mclbm_set_populations(h, f) -> None:
@@ -443,3 +458,103 @@ class LatticeView(Lattice):
 
     def step(self, n: int = 1) -> None:
         raise RuntimeError("a batch case is stepped with mclbm_batch_step")
+
+
+# --- learned warm start ----------------------------------------------------------
+
+def mclbm_unet_create(levels: int, base: int, max_batch: int, max_h: int, max_w: int, stream=None):
+    h = _vp()
+    _check(load().mclbm_unet_create(levels, base, max_batch, max_h, max_w, _stream_handle(stream),
+                                    C.byref(h)))
+    return h
+
+
+def mclbm_unet_destroy(h) -> None:
+    _check(load().mclbm_unet_destroy(h))
+
+
+def mclbm_unet_param_count(h) -> int:
+    n = _i64()
+    _check(load().mclbm_unet_param_count(h, C.byref(n)))
+    return n.value
+
+
+def mclbm_unet_set_params(h, theta) -> None:
+    _check(load().mclbm_unet_set_params(h, _addr(theta, np.float32)))
+
+
+def mclbm_unet_get_params(h, theta) -> None:
+    _check(load().mclbm_unet_get_params(h, _addr(theta, np.float32)))
+
+
+def mclbm_unet_infer(h, batch: int, height: int, width: int, x, phi) -> None:
+    _check(load().mclbm_unet_infer(h, batch, height, width, _addr(x, np.float32),
+                                   _addr(phi, np.float32)))
+
+
+def mclbm_unet_gradient(h, batch: int, height: int, width: int, x, target, mask, grad=None) -> float:
+    loss = C.c_double()
+    _check(load().mclbm_unet_gradient(h, batch, height, width, _addr(x, np.float32),
+                                      _addr(target, np.float32), _addr(mask, np.float32),
+                                      C.byref(loss), _addr(grad, np.float32)))
+    return loss.value
+
+
+def mclbm_unet_train_step(h, batch: int, height: int, width: int, x, target, mask,
+                          lr: float) -> float:
+    loss = C.c_double()
+    _check(load().mclbm_unet_train_step(h, batch, height, width, _addr(x, np.float32),
+                                        _addr(target, np.float32), _addr(mask, np.float32),
+                                        float(lr), C.byref(loss)))
+    return loss.value
+
+
+class UNet:
+    """Owning handle of a warm-start network (arrays NHWC, FP32)."""
+
+    def __init__(self, levels: int = 4, base: int = 32, max_batch: int = 1, max_h: int = 256,
+                 max_w: int = 256, stream=None):
+        self.h = None
+        self.levels, self.base = levels, base
+        self.h = mclbm_unet_create(levels, base, max_batch, max_h, max_w, stream)
+        self.n = mclbm_unet_param_count(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            mclbm_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, theta) -> None:
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        if theta.size != self.n:
+            raise ValueError(f"expected {self.n} parameters, got {theta.size}")
+        mclbm_unet_set_params(self.h, theta)
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n, np.float32)
+        mclbm_unet_get_params(self.h, out)
+        return out
+
+    def infer(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        b, hh, ww, _ = x.shape
+        out = np.empty((b, hh, ww), np.float32)
+        mclbm_unet_infer(self.h, b, hh, ww, x, out)
+        return out
+
+    def gradient(self, x, target, mask):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        b, hh, ww, _ = x.shape
+        g = np.empty(self.n, np.float32)
+        loss = mclbm_unet_gradient(self.h, b, hh, ww, x, np.ascontiguousarray(target, np.float32),
+                                   np.ascontiguousarray(mask, np.float32), g)
+        return loss, g
+
+    def train_step(self, x, target, mask, lr: float) -> float:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        b, hh, ww, _ = x.shape
+        return mclbm_unet_train_step(self.h, b, hh, ww, x, np.ascontiguousarray(target, np.float32),
+                                     np.ascontiguousarray(mask, np.float32), lr)
