@@ -287,6 +287,14 @@ int mclbm_batch_info(mclbm_batch *b, int64_t out[8]);
  * per tile). */
 int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[4]);
 
+/* Checkpoint: write the current state (populations as stored, the outlet
+ * record of Eq. 26, the parameters and the step count) to a file, and read
+ * it back into a lattice of the same size and precision; the restored run
+ * continues bit for bit.  The file is raw device bytes of this build
+ * (same machine byte order). */
+int mclbm_save(mclbm_lattice *lat, const char *path);
+int mclbm_load(mclbm_lattice *lat, const char *path);
+
 /* ------------------------------------------------------------------------
  * Learned warm start (spec extension of the quasi-static protocol of
  * Sec. 4.2): a U-Net predicts the phase field of the next equilibrium.

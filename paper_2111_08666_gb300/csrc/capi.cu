@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <new>
@@ -514,6 +515,88 @@ int mclbm_get_populations(mclbm_lattice *lat, double *f) {
     cudaError_t e = launch_get_populations(*lat, static_cast<double *>(v.ptr));
     if (e != cudaSuccess) return cuda_fail(e, "export kernel");
     return finish_out(*lat, f, bytes, v);
+}
+
+// Checkpoint file: header, Params, then the current population buffer and
+// the outlet record of Eq. 26 as raw device bytes (bit-exact restore).
+namespace {
+struct CheckpointHeader {
+    char magic[8];
+    int32_t version, nx, ny, prec;
+    int64_t pop_bytes, d5_bytes, steps;
+};
+constexpr char CKPT_MAGIC[8] = {'M', 'C', 'L', 'B', 'M', 'C', 'K', '1'};
+}  // namespace
+
+int mclbm_save(mclbm_lattice *lat, const char *path) {
+    if (int rc = check_lat(lat)) return rc;
+    if (!path) return fail(MCLBM_ERR_ARG, "path is NULL");
+    if (!lat->initialised) return fail(MCLBM_ERR_STATE, "nothing to save: lattice not initialised");
+    if (int rc = make_current(*lat)) return rc;
+    CheckpointHeader h{};
+    std::memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = 1;
+    h.nx = lat->nx;
+    h.ny = lat->ny;
+    h.prec = (int32_t)lat->prec;
+    h.pop_bytes = (int64_t)lat->planes * lat->plane * (int64_t)lat->store_bytes;
+    h.d5_bytes = 3 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
+    h.steps = lat->steps;
+    std::vector<unsigned char> buf((size_t)(h.pop_bytes + h.d5_bytes));
+    cudaError_t e = cudaMemcpyAsync(buf.data(), lat->f[lat->cur], (size_t)h.pop_bytes,
+                                    cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(buf.data() + h.pop_bytes, lat->d5, (size_t)h.d5_bytes, cudaMemcpyDeviceToHost,
+                            lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint read-back");
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(MCLBM_ERR_ARG, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(&lat->p, sizeof(Params), 1, fp) == 1 &&
+              std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? MCLBM_OK : fail(MCLBM_ERR_ARG, std::string("write to ") + path + " failed");
+}
+
+int mclbm_load(mclbm_lattice *lat, const char *path) {
+    if (int rc = check_lat(lat)) return rc;
+    if (!path) return fail(MCLBM_ERR_ARG, "path is NULL");
+    if (int rc = make_current(*lat)) return rc;
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(MCLBM_ERR_ARG, std::string("cannot open ") + path);
+    CheckpointHeader h{};
+    Params p;
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(&p, sizeof(Params), 1, fp) == 1;
+    const int64_t pop_bytes = (int64_t)lat->planes * lat->plane * (int64_t)lat->store_bytes;
+    const int64_t d5_bytes = 3 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
+    ok = ok && std::memcmp(h.magic, CKPT_MAGIC, 8) == 0 && h.version == 1;
+    if (ok && (h.nx != lat->nx || h.ny != lat->ny || h.prec != (int32_t)lat->prec ||
+               h.pop_bytes != pop_bytes || h.d5_bytes != d5_bytes)) {
+        std::fclose(fp);
+        return fail(MCLBM_ERR_ARG, "checkpoint is of another lattice size or precision");
+    }
+    std::vector<unsigned char> buf;
+    if (ok) {
+        buf.resize((size_t)(pop_bytes + d5_bytes));
+        ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    }
+    std::fclose(fp);
+    if (!ok) return fail(MCLBM_ERR_ARG, std::string(path) + " is not a complete checkpoint");
+    lat->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(lat->f[0], buf.data(), (size_t)pop_bytes, cudaMemcpyHostToDevice,
+                                    lat->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(lat->d5, buf.data() + pop_bytes, (size_t)d5_bytes, cudaMemcpyHostToDevice,
+                            lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint upload");
+    lat->p = p;
+    lat->p.round_fp32();
+    lat->steps = h.steps;
+    lat->initialised = true;
+    lat->ghost_mode = -1;  // boundary mode of the restored parameters
+    ++lat->version;
+    return MCLBM_OK;
 }
 
 int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {

@@ -167,21 +167,25 @@ struct TileLayout {
 };
 
 // The lattices of a launch; every lattice's arguments and tensor descriptors
-// travel in the kernel parameters.
+// travel in the kernel parameters.  Sized by the number of lattices a launch
+// may hold (1 or MAX_BATCH): the parameter block is copied at every launch,
+// and a single lattice's launch stays small.
+template <int N>
 struct BatchArgs {
+    CUtensorMap tin[N];   // input populations (whole padded array)
+    CUtensorMap tout[N];  // output populations (extent ends inside the lattice)
+    StepArgs a[N];
+    const uint32_t *tab[N];
     int ncases, total;
-    int tiles_x[MAX_BATCH];
-    int first[MAX_BATCH + 1];     // first work item of each lattice
-    int tab_words[MAX_BATCH];     // table words copied per tile
-    const uint32_t *tab[MAX_BATCH];
-    StepArgs a[MAX_BATCH];
-    CUtensorMap tin[MAX_BATCH];   // input populations (whole padded array)
-    CUtensorMap tout[MAX_BATCH];  // output populations (extent ends inside the lattice)
+    int tiles_x[N];
+    int first[N + 1];     // first work item of each lattice
+    int tab_words[N];     // table words copied per tile
 };
 
-// ONE: the launch holds a single lattice (its arguments at fixed offsets)
-template <class P, int TX, int TY, bool ONE>
-__global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_constant__ BatchArgs b) {
+// N = 1: the launch holds a single lattice (its arguments at fixed offsets)
+template <class P, int TX, int TY, int N>
+__global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_constant__ BatchArgs<N> b) {
+    constexpr bool ONE = N == 1;
     using L = TileLayout<P, TX, TY>;
     using S = typename P::store_t;
     using R = typename P::real_t;
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 // Host side: tensor descriptors, work tables and launch.
 // ---------------------------------------------------------------------------
-static_assert(sizeof(BatchArgs) < 32000, "batch arguments must fit the kernel parameter space");
+static_assert(sizeof(BatchArgs<MAX_BATCH>) < 32000, "batch arguments must fit the kernel parameter space");
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
@@ -478,38 +482,31 @@ CUtensorMapDataType dtype_of(mclbm_precision p) {
 // [3] output into buffer 1
 constexpr int MAPS_PER_CASE = 4;
 
-template <class P, int TX, int TY, bool ONE>
+template <class P, int TX, int TY, int N>
 int resident_slots() {
     using Lay = TileLayout<P, TX, TY>;
     static int slots = 0;
     if (slots == 0) {
-        if (cudaFuncSetAttribute(tma_tile_kernel<P, TX, TY, ONE>,
+        if (cudaFuncSetAttribute(tma_tile_kernel<P, TX, TY, N>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Lay::total) != cudaSuccess)
             return 0;
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_tile_kernel<P, TX, TY, ONE>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tma_tile_kernel<P, TX, TY, N>,
                                                       TX * TY, Lay::total);
         slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
     }
     return slots;
 }
 
-template <class P, int TX, int TY>
-cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, int shape, int grid,
-                       cudaStream_t stream, int *slots_out) {
+// fill the parameter block of n lattices and launch
+template <class P, int TX, int TY, int N>
+cudaError_t launch_args(Lattice *const *cases, int n, const CUtensorMap *maps, int shape, int grid,
+                        int slots, cudaStream_t stream) {
     using Lay = TileLayout<P, TX, TY>;
-    const bool one = n == 1;
-    const int slots = one ? resident_slots<P, TX, TY, true>() : resident_slots<P, TX, TY, false>();
-    if (slots == 0) {
-        const cudaError_t e = cudaGetLastError();
-        return e != cudaSuccess ? e : cudaErrorUnknown;
-    }
-    if (slots_out) *slots_out = slots;
-    if (!cases) return cudaSuccess;  // query only
-    static BatchArgs b;  // host staging of the parameter block
+    static BatchArgs<N> b;  // host staging of the parameter block
     std::memset(&b, 0, sizeof(b));
     b.ncases = n;
     int total = 0;
@@ -537,12 +534,24 @@ cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, in
     b.first[n] = total;
     b.total = total;
     const int g = grid > 0 ? (grid < total ? grid : total) : (slots < total ? slots : total);
-    if (one)
-        tma_tile_kernel<P, TX, TY, true><<<g, TX * TY, Lay::total, stream>>>(b);
-    else
-        tma_tile_kernel<P, TX, TY, false><<<g, TX * TY, Lay::total, stream>>>(b);
+    tma_tile_kernel<P, TX, TY, N><<<g, TX * TY, Lay::total, stream>>>(b);
     count_launch();
     return cudaGetLastError();
+}
+
+template <class P, int TX, int TY>
+cudaError_t launch_cfg(Lattice *const *cases, int n, const CUtensorMap *maps, int shape, int grid,
+                       cudaStream_t stream, int *slots_out) {
+    const bool one = n == 1;
+    const int slots = one ? resident_slots<P, TX, TY, 1>() : resident_slots<P, TX, TY, MAX_BATCH>();
+    if (slots == 0) {
+        const cudaError_t e = cudaGetLastError();
+        return e != cudaSuccess ? e : cudaErrorUnknown;
+    }
+    if (slots_out) *slots_out = slots;
+    if (!cases) return cudaSuccess;  // query only
+    if (one) return launch_args<P, TX, TY, 1>(cases, n, maps, shape, grid, slots, stream);
+    return launch_args<P, TX, TY, MAX_BATCH>(cases, n, maps, shape, grid, slots, stream);
 }
 
 template <class P>

@@ -100,6 +100,8 @@ _SIGS = {
     "mclbm_unet_train_step": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
                                         C.c_double, _P(C.c_double)]),
     "mclbm_init_from_phase": (C.c_int, [_vp, _vp]),
+    "mclbm_save": (C.c_int, [_vp, C.c_char_p]),
+    "mclbm_load": (C.c_int, [_vp, C.c_char_p]),
     "mclbm_launch_count": (_i64, []),
     "mclbm_last_error": (C.c_char_p, []),
 }
@@ -213,6 +215,14 @@ def mclbm_set_stream(h, stream) -> None:
 
 def mclbm_init_densities(h, rho1, rho2) -> None:
     _check(load().mclbm_init_densities(h, _addr(rho1, np.float64), _addr(rho2, np.float64)))
+
+
+def mclbm_save(h, path) -> None:
+    _check(load().mclbm_save(h, str(path).encode()))
+
+
+def mclbm_load(h, path) -> None:
+    _check(load().mclbm_load(h, str(path).encode()))
 
 
 def mclbm_init_from_phase(h, phi) -> None:

@@ -67,3 +67,198 @@ def network_input(solid, xi, phase, dp: float) -> np.ndarray:
     x[..., 2] = np.where(solid != 0, 0.0, np.asarray(phase, np.float32))
     x[..., 3] = dp
     return x
+
+
+# --- training pairs from the batched LBM -----------------------------------------
+
+DP_SCALE = 100.0  # input channel 3 = pressure step (inlet density increment) x DP_SCALE
+
+
+def training_case(seed: int, size: int = 256) -> dict:
+    """Medium of the training set: lognormal disks (mean radius 10, sigma_log
+    0.4), porosity 0.6, contact angle drawn from U[30, 150] deg with the
+    seed, viscosity ratio 10; primary drainage set-up at equal pressures."""
+    from . import media
+    theta = float(np.random.default_rng(seed).uniform(30.0, 150.0))
+    m = media.make_disk_medium(size, size, seed, radius="lognormal", r_mean=10.0, sigma_log=0.4,
+                               porosity=0.6)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    return dict(solid=m.solid, xi=media.uniform_xi(m.solid, media.theta_to_xi(theta)), rho1=rho1,
+                rho2=rho2, nu1=(1.7 - 0.5) / 3.0, nu2=(0.62 - 0.5) / 3.0, g_coh=3.5,
+                rho_in1=1.0, rho_out2=1.0, theta=theta)
+
+
+def relax(step, saturation, window: int = 1000, tol: float = 1e-6, max_steps: int = 40000):
+    """Step until S_w (by mass) changes by less than tol over one window
+    (the convergence reading of Sec. 4.2.1).  Returns (steps, S_w, converged)."""
+    prev = saturation()
+    n = 0
+    while n < max_steps:
+        step(window)
+        n += window
+        cur = saturation()
+        if abs(cur - prev) < tol:
+            return n, cur, True
+        prev = cur
+    return n, prev, False
+
+
+def drainage_pairs(seeds, size: int = 256, levels: int = 6, d_rho: float = 0.004,
+                   window: int = 1000, tol: float = 1e-6, max_steps: int = 30000, batch: int = 24):
+    """Quasi-static primary drainage of the training media with the batched
+    kernel: relax at equal pressures, then raise the inlet density of
+    component 1 by d_rho per level and relax again.  Returns the network
+    inputs [N][size][size][4], targets (phase field after the level) and
+    fluid masks, and the relaxation steps of every (case, level)."""
+    xs, ts, ms, steps = [], [], [], []
+    seeds = list(seeds)
+    for c0 in range(0, len(seeds), batch):
+        cases = [training_case(s, size) for s in seeds[c0:c0 + batch]]
+        b = mclbm.mclbm_batch_create(cases, mclbm.MCLBM_FP32)
+        try:
+            views = [mclbm.LatticeView(b, k, size, size, mclbm.MCLBM_FP32) for k in range(len(cases))]
+            fluid = [(c["solid"] == 0).astype(np.float32) for c in cases]
+
+            def run_level():
+                prev = [v.diagnostics()["sw_mass"] for v in views]
+                done = [0] * len(views)
+                n = 0
+                while n < max_steps and not all(done):
+                    mclbm.mclbm_batch_step(b, window)
+                    n += window
+                    cur = [v.diagnostics()["sw_mass"] for v in views]
+                    for k in range(len(views)):
+                        if not done[k] and abs(cur[k] - prev[k]) < tol:
+                            done[k] = n
+                    prev = cur
+                return [d if d else n for d in done]
+
+            run_level()
+            phase = [v.phase() for v in views]
+            for lev in range(1, levels + 1):
+                for v in views:
+                    v.set_pressure_bc(1.0 + lev * d_rho, 1.0)
+                st = run_level()
+                new = [v.phase() for v in views]
+                for k, c in enumerate(cases):
+                    xs.append(network_input(c["solid"], c["xi"], phase[k], d_rho * DP_SCALE))
+                    ts.append(new[k])
+                    ms.append(fluid[k])
+                    steps.append(st[k])
+                phase = new
+        finally:
+            mclbm.mclbm_batch_destroy(b)
+    return (np.stack(xs).astype(np.float32), np.stack(ts).astype(np.float32),
+            np.stack(ms).astype(np.float32), np.array(steps))
+
+
+def train(net, x, t, m, epochs: int = 10, batch: int = 16, lr: float = 1e-3, seed: int = 0):
+    """Adam on the masked MSE, shuffled mini-batches; returns the mean loss
+    of every epoch."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    n = x.shape[0]
+    for _ in range(epochs):
+        order = rng.permutation(n)
+        losses = []
+        for i in range(0, n - batch + 1, batch):
+            idx = order[i:i + batch]
+            losses.append(net.train_step(x[idx], t[idx], m[idx], lr))
+        hist.append(float(np.mean(losses)))
+    return hist
+
+
+def compare_warm_cold(net, case: dict, levels: int = 20, d_rho: float = 0.002, window: int = 1000,
+                      tol: float = 1e-6, max_steps: int = 40000, stream=None):
+    """Quasi-static drainage of one lattice, each pressure level relaxed twice
+    from the same equilibrium: cold (the previous equilibrium under the new
+    boundary densities, the protocol of Sec. 4.2) and warm (the lattice
+    re-initialised from the network's predicted phase field).  The cold
+    branch carries the protocol forward.  Returns one record per level."""
+    import time
+
+    def make():
+        lat = mclbm.Lattice(case["solid"], case["xi"], prec="fp32", nu1=case["nu1"],
+                            nu2=case["nu2"], rho_in1=case["rho_in1"], rho_out2=case["rho_out2"],
+                            stream=stream)
+        return lat
+
+    cold, warm = make(), make()
+    cold.init(case["rho1"], case["rho2"])
+
+    def sw(l):
+        return l.diagnostics()["sw_mass"]
+
+    relax(cold.step, lambda: sw(cold), window, tol, max_steps)
+    out = []
+    for lev in range(1, levels + 1):
+        rho_in = case["rho_in1"] + lev * d_rho
+        phase = cold.phase()
+        sw0 = sw(cold)
+        # warm: predicted phase field as the initial state
+        t0 = time.perf_counter()
+        x = network_input(case["solid"], case["xi"], phase, d_rho * DP_SCALE)[None]
+        phi = net.infer(x)[0]
+        t_inf = time.perf_counter() - t0
+        warm.set_pressure_bc(rho_in, case["rho_out2"])
+        mclbm.mclbm_init_from_phase(warm.h, phi)
+        t0 = time.perf_counter()
+        n_w, sw_w, ok_w = relax(warm.step, lambda: sw(warm), window, tol, max_steps)
+        t_w = time.perf_counter() - t0
+        # cold: continue from the previous equilibrium
+        cold.set_pressure_bc(rho_in, case["rho_out2"])
+        t0 = time.perf_counter()
+        n_c, sw_c, ok_c = relax(cold.step, lambda: sw(cold), window, tol, max_steps)
+        t_c = time.perf_counter() - t0
+        out.append(dict(level=lev, rho_in1=rho_in, sw_before=sw0, steps_cold=n_c, steps_warm=n_w,
+                        sw_cold=sw_c, sw_warm=sw_w, converged_cold=ok_c, converged_warm=ok_w,
+                        sec_cold=t_c, sec_warm=t_w, sec_infer=t_inf))
+    cold.close()
+    warm.close()
+    return out
+
+
+def main(argv=None) -> None:
+    """Generate training pairs, train, and compare warm and cold relaxation
+    on a large lattice; prints one JSON line."""
+    import argparse
+    import json
+    import time
+
+    from . import media
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-media", type=int, default=48)
+    ap.add_argument("--train-levels", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--eval-nx", type=int, default=2048)
+    ap.add_argument("--eval-ny", type=int, default=1024)
+    ap.add_argument("--eval-levels", type=int, default=20)
+    ap.add_argument("--max-steps", type=int, default=40000)
+    ap.add_argument("--d-rho", type=float, default=0.002)
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
+                                 d_rho=a.d_rho, max_steps=a.max_steps)
+    t_data = time.perf_counter() - t0
+    net = mclbm.UNet(4, 32, max_batch=16, max_h=256, max_w=256)
+    net.set_params(init_params(4, 32, 0))
+    t0 = time.perf_counter()
+    hist = train(net, x, t, m, epochs=a.epochs)
+    t_train = time.perf_counter() - t0
+    big = mclbm.UNet(4, 32, max_batch=1, max_h=a.eval_ny, max_w=a.eval_nx)
+    big.set_params(net.params())
+    net.close()
+    case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
+    rec = compare_warm_cold(big, case, levels=a.eval_levels, d_rho=a.d_rho, max_steps=a.max_steps)
+    summary = dict(train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train, loss=hist,
+                   pair_steps_mean=float(st.mean()),
+                   steps_cold=int(sum(r["steps_cold"] for r in rec)),
+                   steps_warm=int(sum(r["steps_warm"] for r in rec)),
+                   max_abs_dsw=float(max(abs(r["sw_cold"] - r["sw_warm"]) for r in rec)),
+                   levels=rec)
+    print(json.dumps(summary))
+    big.close()
+
+
+if __name__ == "__main__":
+    main()

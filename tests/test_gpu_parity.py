@@ -355,3 +355,27 @@ def test_tile_shapes_agree(prec, open_x):
     b.step(200)
     fa, fb = a.populations(), b.populations()
     assert np.max(np.abs(fa - fb)) <= AGREE[prec][1] * np.max(np.abs(fa))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16dev", "fp64"])
+def test_checkpoint_restores_bit_for_bit(prec, tmp_path):
+    """A run saved and loaded into another lattice (created with other
+    parameters) continues exactly as the original."""
+    m = media.make_disk_medium(96, 48, 4, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.3)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    a = mclbm.Lattice(m.solid, xi, prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
+                      rho_in1=1.01, rho_out2=1.0)
+    a.init(rho1, rho2)
+    a.step(40)
+    path = tmp_path / "state.ckpt"
+    mclbm.mclbm_save(a.h, path)
+    b = mclbm.Lattice(m.solid, xi, prec=prec)  # default parameters, periodic x
+    mclbm.mclbm_load(b.h, path)
+    assert b.info()["steps"] == a.info()["steps"] == 40
+    a.step(40)
+    b.step(40)
+    assert np.array_equal(a.populations(), b.populations())
+    other = mclbm.Lattice(m.solid[:, :64], xi[:, :64], prec=prec)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_load(other.h, path)
