@@ -147,7 +147,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.Stream()
     prec = mclbm.PRECISIONS[args.prec]
     c = workload()
-    kernel = {"auto": 0, "tile": 1, "strip": 2}[args.kernel]
+    kernel = {"auto": 0, "tile": 1, "strip": 2, "tma": 3, "fluid": 4}[args.kernel]
     lat = mclbm.Lattice(c["solid"], c["xi"], prec=prec, nu1=c["nu1"], nu2=c["nu2"],
                         rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream,
                         kernel=kernel, tile_shape=args.tile_shape)
@@ -385,7 +385,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", choices=["fp64", "fp32", "fp32dev", "fp16dev", "bf16dev"],
                     default="fp32")
-    ap.add_argument("--kernel", choices=["auto", "tile", "strip"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "tile", "strip", "tma", "fluid"], default="auto")
     ap.add_argument("--tile-shape", type=int, choices=[0, 1], default=0,
                     help="tile of the TMA kernel: 0 = 32x16 (32x12 fp32dev), 1 = 32x8")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -76,7 +76,10 @@ typedef enum {
      * for the FP32 and deviation storages and 1 for FP64; 1 the 2-D tile
      * kernel pulling straight from global memory; 2 the row-sweeping strip
      * kernel staging rows with bulk copies; 3 the 2-D tile kernel staging
-     * the tile and its ring with one tensor copy (not for FP64). */
+     * the tile and its ring with one tensor copy (not for FP64); 4 the
+     * fluid-only kernel: the populations of the fluid nodes only, tile by
+     * tile, staged with bulk copies (FP32, FP16 and BF16 deviation storage;
+     * the dense buffers are rebuilt whenever a read-out needs them). */
     MCLBM_FLAG_KERNEL = 3,
     /* Tile of kernel 3: 0 (default) 32 x 16 nodes (32 x 12 for FP32_DEV),
      * two CTAs per SM; 1: 32 x 8 nodes, three CTAs per SM.  Same results. */

@@ -109,6 +109,7 @@ void release(Lattice *L) {
     cudaFree(L->err);
     cudaFree(L->geo_pad);
     tma_release(*L);
+    sparse_release(*L);
     if (L->host_diag) cudaFreeHost(L->host_diag);
     if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     L->own_stream = false;
@@ -126,6 +127,7 @@ int dev_alloc(Lattice &L, void **p, size_t bytes) {
 }
 
 int run_diagnostics(Lattice &L, double out[8]) {
+    if (int rc = sparse_to_dense(L)) return rc;
     cudaError_t e = launch_diagnostics(L);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics kernel");
     e = cudaMemcpyAsync(L.host_diag, L.diag_out, 8 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -171,9 +173,23 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// the dense buffers current, with their ghost copies
+int dense_current(Lattice &L) {
+    if (int rc = sparse_to_dense(L)) return rc;
+    if (L.pop_ghosts_stale && L.ghost_mode == L.ghost_key()) {
+        cudaError_t e = launch_geo_ghosts(L);
+        if (e != cudaSuccess) return cuda_fail(e, "ghost columns");
+    }
+    L.pop_ghosts_stale = false;
+    return MCLBM_OK;
+}
+
 int lattice_prepare_step(Lattice &L) {
     if (int rc = check_ready(L)) return rc;
-    return refresh_ghosts(L);
+    if (int rc = dense_current(L)) return rc;
+    if (int rc = refresh_ghosts(L)) return rc;
+    L.sparse_state = 0;  // the batched kernel steps the dense buffers
+    return MCLBM_OK;
 }
 
 }  // namespace mclbm
@@ -344,7 +360,7 @@ int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
             ++lat->version;
             return MCLBM_OK;
         case MCLBM_FLAG_KERNEL:
-            if (value < 0 || value > 3) return fail(MCLBM_ERR_ARG, "kernel must be 0..3");
+            if (value < 0 || value > 4) return fail(MCLBM_ERR_ARG, "kernel must be 0..4");
             lat->kernel = value;
             return MCLBM_OK;
         case MCLBM_FLAG_TILE_SHAPE:
@@ -456,6 +472,8 @@ int mclbm_init_densities(mclbm_lattice *lat, const double *rho1, const double *r
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     e = cudaStreamSynchronize(lat->stream);  // staging buffers are freed on return
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    lat->sparse_state = 0;
+    lat->pop_ghosts_stale = false;
     lat->initialised = true;
     lat->steps = 0;
     return MCLBM_OK;
@@ -484,6 +502,8 @@ int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     cudaFree(r);
     if (e != cudaSuccess) return cuda_fail(e, "init from phase");
+    lat->sparse_state = 0;
+    lat->pop_ghosts_stale = false;
     lat->initialised = true;
     lat->steps = 0;
     return MCLBM_OK;
@@ -501,6 +521,8 @@ int mclbm_set_populations(mclbm_lattice *lat, const double *f) {
     if (e != cudaSuccess) return cuda_fail(e, "import kernel");
     e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    lat->sparse_state = 0;
+    lat->pop_ghosts_stale = false;
     lat->initialised = true;
     return MCLBM_OK;
 }
@@ -509,6 +531,7 @@ int mclbm_get_populations(mclbm_lattice *lat, double *f) {
     if (int rc = check_lat(lat)) return rc;
     if (!f) return fail(MCLBM_ERR_ARG, "f is NULL");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     const size_t bytes = (size_t)18 * lat->nx * lat->ny * sizeof(double);
     DeviceView v;
     if (int rc = view_out(f, bytes, v)) return rc;
@@ -533,6 +556,7 @@ int mclbm_save(mclbm_lattice *lat, const char *path) {
     if (!path) return fail(MCLBM_ERR_ARG, "path is NULL");
     if (!lat->initialised) return fail(MCLBM_ERR_STATE, "nothing to save: lattice not initialised");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     CheckpointHeader h{};
     std::memcpy(h.magic, CKPT_MAGIC, 8);
     h.version = 1;
@@ -590,6 +614,8 @@ int mclbm_load(mclbm_lattice *lat, const char *path) {
                             lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "checkpoint upload");
+    lat->sparse_state = 0;
+    lat->pop_ghosts_stale = false;
     lat->p = p;
     lat->p.round_fp32();
     lat->steps = h.steps;
@@ -611,13 +637,24 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
         return fail(MCLBM_ERR_ARG, "the TMA tile kernel is not available for this precision");
     if (which == 2 && !sweep_supported(*lat))
         return fail(MCLBM_ERR_ARG, "the strip kernel is not available for this lattice");
+    if (which == 4) {
+        if (!sparse_precision(lat->prec))
+            return fail(MCLBM_ERR_ARG, "the fluid-only kernel is not available for this precision");
+        if (int rc = sparse_prepare(*lat, lat->tile_shape == 1 ? 8 : 12)) return rc;
+        if (int rc = dense_to_sparse(*lat)) return rc;
+    } else if (nsteps > 0) {
+        if (int rc = dense_current(*lat)) return rc;
+    }
     for (int64_t t = 0; t < nsteps; ++t) {
-        cudaError_t e = which == 3   ? launch_step_tma(*lat)
+        cudaError_t e = which == 4   ? launch_step_sparse(*lat)
+                        : which == 3 ? launch_step_tma(*lat)
                         : which == 2 ? launch_step_sweep(*lat)
                                      : launch_step_tile(*lat, 0);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel");
+        if (which != 4) lat->sparse_state = 0;
         ++lat->steps;
         if (lat->diag_every > 0 && lat->steps % lat->diag_every == 0) {
+            if (int rc = sparse_to_dense(*lat)) return rc;
             e = launch_diagnostics(*lat);
             if (e != cudaSuccess) return cuda_fail(e, "divergence check");
         }
@@ -653,6 +690,7 @@ int mclbm_read_density(mclbm_lattice *lat, int comp, double *out) {
     if (comp != 1 && comp != 2) return fail(MCLBM_ERR_ARG, "comp must be 1 or 2");
     if (!out) return fail(MCLBM_ERR_ARG, "out is NULL");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     const size_t bytes = (size_t)lat->nx * lat->ny * sizeof(double);
     DeviceView v;
     if (int rc = view_out(out, bytes, v)) return rc;
@@ -665,6 +703,7 @@ int mclbm_read_pressure(mclbm_lattice *lat, double *out) {
     if (int rc = check_lat(lat)) return rc;
     if (!out) return fail(MCLBM_ERR_ARG, "out is NULL");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     const size_t bytes = (size_t)lat->nx * lat->ny * sizeof(double);
     DeviceView v;
     if (int rc = view_out(out, bytes, v)) return rc;
@@ -677,6 +716,7 @@ int mclbm_read_phase(mclbm_lattice *lat, float *out) {
     if (int rc = check_lat(lat)) return rc;
     if (!out) return fail(MCLBM_ERR_ARG, "out is NULL");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     const size_t bytes = (size_t)lat->nx * lat->ny * sizeof(float);
     DeviceView v;
     if (int rc = view_out(out, bytes, v)) return rc;
@@ -689,6 +729,7 @@ int mclbm_read_velocity(mclbm_lattice *lat, double *ux, double *uy) {
     if (int rc = check_lat(lat)) return rc;
     if (!ux || !uy) return fail(MCLBM_ERR_ARG, "ux/uy is NULL");
     if (int rc = make_current(*lat)) return rc;
+    if (int rc = sparse_to_dense(*lat)) return rc;
     const size_t bytes = (size_t)lat->nx * lat->ny * sizeof(double);
     DeviceView vx, vy;
     if (int rc = view_out(ux, bytes, vx)) return rc;

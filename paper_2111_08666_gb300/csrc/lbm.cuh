@@ -197,6 +197,21 @@ struct Lattice {
     uint32_t *tab[2] = {nullptr, nullptr};
     int tab_words[2] = {0, 0};  // words copied per tile (largest table, 16-byte multiple)
     int *tab_max = nullptr;     // device scratch of the table build
+    // fluid-only step (kernel 4): populations of the fluid nodes only, tile by
+    // tile; the dense buffers stay the interchange format and the two are
+    // converted lazily
+    void *fs[2] = {nullptr, nullptr};  // [planes][nfp] each
+    long long nfp = 0;                 // fluid slots (padded), 0 = kernel 4 unavailable
+    int scur = 0;
+    int sparse_state = 0;              // 0 dense current, 1 fluid-only current, 2 both
+    bool pop_ghosts_stale = false;     // dense ghost copies need rebuilding
+    int sparse_mode = -1;              // boundary mode the sparse tables were built for
+    uint32_t *stab = nullptr;          // per-tile tables of kernel 4
+    int stab_words = 0;                // words per tile table (stride and copy size)
+    int socap = 0, sscap = 0;          // largest own block and staged set of any tile
+    int sparse_ty = 0;                 // tile height of the layout
+    uint32_t *scopy = nullptr;         // per-tile copy records of kernel 4
+    int *snode = nullptr;              // [nfp]: lattice node y * nx + x of each slot, -1 padding
     uint64_t version = 0;      // bumped whenever a parameter changes
     int ghost_key() const { return p.open_x * 2 + p.periodic_y; }
     Geometry geometry() const {
@@ -218,6 +233,13 @@ cudaError_t launch_step_tma(Lattice &L);
 bool tma_supported(const Lattice &L);
 int tma_prepare(Lattice &L);      // builds the TMA descriptors; MCLBM_OK or error
 int tma_build_tables(Lattice &L); // work tables for the current boundary mode (synchronises)
+// fluid-only step (sparse.cu)
+bool sparse_precision(mclbm_precision p);
+int sparse_prepare(Lattice &L, int tile_height);  // layout and tables (tile 32 x 12 or 32 x 8)
+cudaError_t launch_step_sparse(Lattice &L);
+int sparse_to_dense(Lattice &L);      // make the dense buffers current (no-op if they are)
+int dense_to_sparse(Lattice &L);      // make the fluid-only buffers current
+void sparse_release(Lattice &L);
 void tma_release(Lattice &L);
 // batched persistent launch over several lattices (tma_tile.cu)
 constexpr int MAX_BATCH = 32;

@@ -1,0 +1,770 @@
+// Fluid-only step (kernel 4): the populations of the fluid nodes only, so
+// that a step reads and writes 2 x 9 x 2 populations per fluid node and no
+// solid node costs memory traffic.
+//
+// Storage: fs[b] = [nfp][planes] (a node's populations contiguous, so that
+// a range of nodes is one bulk copy), the fluid nodes tile by tile (TX x TY
+// tiles in row-major order); inside a tile in border bands of width 3 --
+// top-left corner, top edge, top-right corner, right edge, bottom-right
+// corner, bottom edge, bottom-left corner, left edge -- then the interior,
+// each band padded to a 16-byte multiple.  A neighbour's halo band is then
+// one or two contiguous ranges of its block.
+//
+// Per tile, built on the host from the geometry and validated against every
+// buffer bound before the kernel may run:
+//   copy record  the ranges (source slot, length, destination slot) whose
+//                bulk copies stage the tile's own block and the fluid nodes
+//                of its 3-node ring, all planes, into shared memory
+//   table        the work lists of the dense tile kernel (own nodes with
+//                their block index, ring pulls, ring non-fluid nodes) and
+//                the staged slot of every position of the staged frame
+// The step per tile: stage (bulk copies on one mbarrier), then the phases
+// of the dense tile kernel, reading staged nodes through the slot map --
+// pull + Set-3 + densities (Eq. 3), virtual solid densities (Eqs. 16-17),
+// forces (Eqs. 12-15), tau_s, u (Eqs. 6-9), collision (Eqs. 1, 2, 11) --
+// and one bulk store per plane of the tile's block.  Periodic edges need no
+// ghost copies: a ring node across an edge is staged from its own tile.
+//
+// The dense buffers stay the interchange format of the library; the two
+// layouts are converted lazily (dense_to_sparse / sparse_to_dense).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "async_copy.cuh"
+#include "lbm_device.cuh"
+
+namespace mclbm {
+
+namespace {
+
+constexpr int STX = 32;                  // tile width; height 12 (shape 0) or 8 (shape 1)
+constexpr int SFW = STX + 6;             // staged frame: tile + 3-node ring
+constexpr int SDXW = STX + 4;            // density frame: tile + 2-node ring
+constexpr int MAXR = 24;                 // ranges per tile (own block included)
+constexpr int REC_WORDS = 4 + 3 * MAXR;  // copy record: n, bytes, own_len, start, ranges
+constexpr int HDR = 8;                   // table header words
+constexpr uint32_t SET3 = 3u << 20, IN_BIT = 1u << 20, OUT_BIT = 2u << 20;
+static_assert((REC_WORDS * 4) % 16 == 0, "copy records are copied in 16-byte chunks");
+
+template <class P, int STY>
+struct SLayout {
+    using S = typename P::store_t;
+    using R = typename P::real_t;
+    static constexpr int SFH = STY + 6, SN1 = SDXW * (STY + 4);
+    static_assert(SFW * SFH < 65535, "frame positions are 16-bit");
+    static constexpr int NPL = P::planes;
+    // slots per 16-byte multiple (a node is NPL * sizeof(S) = 72 or 40 bytes)
+    static constexpr int Q = 16 / ((NPL * (int)sizeof(S)) & 15 ? ((NPL * (int)sizeof(S)) & 15) : 16);
+    static constexpr int OCAP = (STX * STY + 9 * (Q - 1) + Q - 1) / Q * Q;  // own block
+    // staged slots: the own block, the ring's nodes (at most the staged
+    // frame outside the tile) and the 16-byte rounding of every range
+    static constexpr int SCAP = (OCAP + SFW * SFH - STX * STY + 2 * MAXR * (Q - 1) + 15) / 16 * 16;
+    // table: header, own + ring + ring non-fluid entries (disjoint positions
+    // of the density frame), then the staged slot of every frame position
+    // (16 bits each)
+    static constexpr int TABW = (HDR + SN1 + (SFW * SFH + 1) / 2 + 3) / 4 * 4;
+    static constexpr size_t stg_bytes = (size_t)SCAP * NPL * sizeof(S);  // [slot][plane]
+    static constexpr size_t out_off = (stg_bytes + 127) / 128 * 128;
+    static constexpr size_t out_bytes = (size_t)OCAP * NPL * sizeof(S);  // [slot][plane]
+    static constexpr size_t rho_off = (out_off + out_bytes + 127) / 128 * 128;
+    static constexpr size_t rho_bytes = (size_t)2 * SN1 * sizeof(R);
+    static constexpr size_t tab_off = (rho_off + rho_bytes + 127) / 128 * 128;  // two buffers
+    static constexpr size_t tab_bytes = (size_t)2 * TABW * 4;
+    static constexpr size_t rec_off = tab_off + tab_bytes;
+    static constexpr size_t bar_off = (rec_off + REC_WORDS * 4 + 15) / 16 * 16;
+    static constexpr size_t total = bar_off + 8;
+    static_assert(OCAP <= 1023, "own-block index is 10 bits");
+    static_assert((TABW * 4) % 16 == 0 && (Q * NPL * sizeof(S)) % 16 == 0, "bulk copy granularity");
+};
+
+}  // namespace
+
+// kernel 4 serves FP32 and the 16-bit deviation storages (FP32 deviation
+// storage, 20 planes of 4 bytes, does not fit two CTAs per SM)
+bool sparse_precision(mclbm_precision p) {
+    return p == MCLBM_FP32 || p == MCLBM_FP16_DEV || p == MCLBM_BF16_DEV;
+}
+
+namespace {
+
+int table_capacity(mclbm_precision p, int sty) {
+    if (sty == 8) return p == MCLBM_FP32 ? SLayout<P32, 8>::TABW : SLayout<P16D, 8>::TABW;
+    return p == MCLBM_FP32 ? SLayout<P32, 12>::TABW : SLayout<P16D, 12>::TABW;
+}
+int staged_capacity(mclbm_precision p, int sty) {
+    if (sty == 8) return p == MCLBM_FP32 ? SLayout<P32, 8>::SCAP : SLayout<P16D, 8>::SCAP;
+    return p == MCLBM_FP32 ? SLayout<P32, 12>::SCAP : SLayout<P16D, 12>::SCAP;
+}
+
+struct SArgs {
+    StepArgs a;
+    const void *fin;  // [nfp][planes]
+    void *fout;
+    long long nfp;
+    const uint32_t *tab;   // [ntiles][tab_words]
+    const uint32_t *rec;   // [ntiles][REC_WORDS]
+    int tab_words, tiles_x, ntiles;
+    // shared-memory layout, sized by the lattice's largest tile
+    uint32_t out_off, rho_off, tab_off, rec_off, bar_off;
+};
+
+// offsets of the shared-memory regions for staged slots scap, own slots
+// ocap and table words tabw; returns the total bytes
+template <class P, int STY>
+size_t smem_layout(int scap, int ocap, int tabw, SArgs &s) {
+    constexpr int SFH = STY + 6, SN1 = SDXW * (STY + 4);
+    using S = typename P::store_t;
+    using R = typename P::real_t;
+    auto up = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
+    const size_t stg = (size_t)scap * P::planes * sizeof(S);
+    s.out_off = (uint32_t)up(stg, 128);
+    s.rho_off = (uint32_t)up(s.out_off + (size_t)ocap * P::planes * sizeof(S), 128);
+    s.tab_off = (uint32_t)up(s.rho_off + (size_t)2 * SN1 * sizeof(R), 128);
+    s.rec_off = (uint32_t)(s.tab_off + (size_t)2 * tabw * 4);
+    s.bar_off = (uint32_t)up(s.rec_off + REC_WORDS * 4, 16);
+    return s.bar_off + 8;
+}
+
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+}
+
+template <class P, int STY>
+__global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs s) {
+    using L = SLayout<P, STY>;
+    constexpr int SFH = L::SFH, SN1 = L::SN1;
+    using S = typename P::store_t;
+    using R = typename P::real_t;
+    constexpr int NT = STX * STY, NPL = L::NPL;
+    // the copy warp: issues the bulk copies and the output store, takes no
+    // part in phase B (it is the last warp, usually without a node in C)
+    constexpr int DW = NT / 32 - 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const S *stg = reinterpret_cast<const S *>(smem);
+    S *out = reinterpret_cast<S *>(smem + s.out_off);
+    R *rho = reinterpret_cast<R *>(smem + s.rho_off);
+    uint32_t *tabs = reinterpret_cast<uint32_t *>(smem + s.tab_off);
+    uint32_t *rec = reinterpret_cast<uint32_t *>(smem + s.rec_off);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + s.bar_off);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const StepArgs &a = s.a;
+    const Geometry &g = a.g;
+    const S *fin = static_cast<const S *>(s.fin);
+    S *fout = static_cast<S *>(s.fout);
+
+    // copy warp: start the copy of tile w's record into shared memory
+    auto fetch_record = [&](int w) {
+        if (lane < REC_WORDS / 4) {
+            const uint32_t *src = s.rec + (size_t)w * REC_WORDS + 4 * lane;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + 4 * lane)), "l"(src)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // copy warp: stage tile w (record already in shared memory) into table buffer tb
+    auto issue = [&](int w, int tb) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        const int nr = (int)rec[0];
+        const uint32_t tbytes = 4u * (uint32_t)s.tab_words;
+        fence_proxy_async();
+        if (lane == 0) {
+            mbar_expect_tx(bar, rec[1] + tbytes);
+            bulk_g2s(tabs + tb * s.tab_words, s.tab + (size_t)w * s.tab_words, tbytes, bar);
+        }
+        __syncwarp();
+        for (int r = lane; r < nr; r += 32) {
+            const uint32_t src = rec[4 + 3 * r], len = rec[5 + 3 * r], dst = rec[6 + 3 * r];
+            bulk_g2s(const_cast<S *>(stg) + (size_t)dst * NPL, fin + (size_t)src * NPL,
+                     len * (uint32_t)(NPL * sizeof(S)), bar);
+        }
+        __syncwarp();
+    };
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if ((int)blockIdx.x >= s.ntiles) return;
+    if (warp == DW) {
+        fetch_record(blockIdx.x);
+        issue(blockIdx.x, 0);
+        if ((int)blockIdx.x + (int)gridDim.x < s.ntiles) fetch_record(blockIdx.x + gridDim.x);
+    }
+
+    uint32_t parity = 0;
+    int tb = 0;
+    for (int w = blockIdx.x; w < s.ntiles; w += gridDim.x) {
+        const int x0 = (w % s.tiles_x) * STX, y0 = (w / s.tiles_x) * STY;
+        const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) {
+                atomicExch(a.err, MCLBM_ERR_TIMEOUT);
+                mbar_wait(bar, parity, DRAIN_LIMIT_NS);
+            }
+            if (warp == DW) bulk_wait_read();
+            return;
+        }
+        const uint32_t *T = tabs + tb * s.tab_words;
+        const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
+        const uint32_t *E = T + HDR;
+        // staged slot of every frame position (0 where nothing is staged)
+        const uint16_t *slot_of = reinterpret_cast<const uint16_t *>(E + n_own + n_ring + n_sol);
+        const bool have = tid < n_own;
+        const uint32_t me = have ? E[tid] : 0u;
+        const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u), bidx = (int)(me >> 22);
+
+        auto val = [&](int plane, int comp, int slot, R wt) -> R {
+            R v = to_real(stg[slot * NPL + comp * 9 + plane]);
+            if constexpr (P::ref) v += wt * to_real(stg[slot * NPL + 18 + comp]);
+            return v;
+        };
+        // f_i = f*_i(x - e_i), or the node's own f*_opp(i) where x - e_i is not
+        // fluid (half-way bounce-back), then Set-3 at the open ends
+        auto pull = [&](int fpos, int oslot, uint32_t e, int x, int y, R f[2][9]) {
+            const uint32_t m = (e >> 12) & 0xffu;
+            f[0][0] = val(0, 0, oslot, wgt<R>(0));
+            f[1][0] = val(0, 1, oslot, wgt<R>(0));
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const bool sb = (m >> (opp(i) - 1)) & 1u;
+                const int slot = sb ? oslot : (int)slot_of[fpos - ey(i) * SFW - ex(i)];
+                const int pl = sb ? opp(i) : i;
+                f[0][i] = val(pl, 0, slot, wgt<R>(i));
+                f[1][i] = val(pl, 1, slot, wgt<R>(i));
+            }
+            if (e & SET3)
+                apply_set3<R>(a, x, y, [&](int comp, int i) { return val(i, comp, oslot, wgt<R>(i)); }, f);
+        };
+
+        // ---- A: densities of the ring's fluid nodes and of the tile's own ------
+        for (int k = tid - n_own + (tid < n_own ? NT : 0); k < n_ring; k += NT) {
+            const uint32_t e = E[n_own + k];
+            const int pos = (int)(e & 0xfffu);
+            const int dr = pos / SDXW, dc = pos - dr * SDXW;
+            const int fpos = (dr + 1) * SFW + dc + 1;
+            R f[2][9];
+            pull(fpos, slot_of[fpos], e, x0 - 2 + dc, wrap(y0 - 2 + dr, g.ny), f);
+            R r1 = 0, r2 = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                r1 += f[0][i];
+                r2 += f[1][i];
+            }
+            rho[pos] = r1;
+            rho[SN1 + pos] = r2;
+        }
+        R f[2][9];
+        R rho1 = 0, rho2 = 0;
+        if (have) {
+            pull((ty + 3) * SFW + tx + 3, bidx, me, x0 + tx, y0 + ty, f);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                rho1 += f[0][i];
+                rho2 += f[1][i];
+            }
+            rho[(ty + 2) * SDXW + tx + 2] = rho1;
+            rho[SN1 + (ty + 2) * SDXW + tx + 2] = rho2;
+        }
+        __syncthreads();
+        // the staged populations have been read.  The copy warp lets the
+        // others start C once the previous tile's output copy has read the
+        // output buffer (named barrier 1: it arrives, the others wait), then
+        // stages the next tile while they compute B and C.
+        // (When the copy warp owns tile nodes itself, all warps meet after B.)
+        const int wn = w + (int)gridDim.x;
+        const bool dw_busy = n_own > NT - 32;
+        if (warp == DW) {
+            bulk_wait_read();
+            if (!dw_busy) asm volatile("bar.arrive 1, %0;" ::"n"(NT) : "memory");
+            if (wn < s.ntiles) {
+                issue(wn, tb ^ 1);
+                if (wn + (int)gridDim.x < s.ntiles) fetch_record(wn + gridDim.x);
+            }
+        }
+
+        // ---- B: virtual solid densities on the 1-ring (zero outside) -----------
+        const uint32_t *Es = E + n_own + n_ring;
+        for (int k = warp == DW ? n_sol : tid; k < n_sol; k += NT - 32) {
+            const uint32_t e = Es[k];
+            const int pos = (int)(e & 0xfffu);
+            const int code = (int)((e >> 12) & 0xffu);
+            const uint32_t fm = e >> 20;
+            R n1s = 0, n2s = 0, den = 0;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if ((fm >> (i - 1)) & 1u) {
+                    const R w8 = wgt<R>(i);
+                    const int q = pos + ey(i) * SDXW + ex(i);
+                    n1s += w8 * rho[q];
+                    n2s += w8 * rho[SN1 + q];
+                    den += w8;
+                }
+            }
+            R s1 = 0, s2 = 0;
+            if (den > R(0) && code != GEO_OUTSIDE) {
+                const R inv = R(1) / den;
+                s1 = chi_at<R>(g, 2 * code) * n1s * inv;
+                s2 = chi_at<R>(g, 2 * code + 1) * n2s * inv;
+            }
+            rho[pos] = s1;
+            rho[SN1 + pos] = s2;
+        }
+        if (dw_busy)
+            __syncthreads();
+        else if (warp != DW)
+            asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+
+        // ---- C: collision of the tile's fluid nodes --------------------------------
+        if (have) {
+            const int dpos = (ty + 2) * SDXW + tx + 2;
+            const uint32_t m = (me >> 12) & 0xffu;
+            R fx1, fy1, fx2, fy2;
+            if (me & SET3) {
+                // Sec. 2.1: a neighbour beyond an open end is replaced by the
+                // one in the opposite direction
+                const bool mir_in = me & IN_BIT, mir_out = me & OUT_BIT;
+                node_force<R, false>(a.p, rho1, rho2,
+                                     [&](int i, uint8_t &code, R &s1, R &s2) {
+                                         const bool mir = (mir_in && ex(i) < 0) || (mir_out && ex(i) > 0);
+                                         const int d = ey(i) * SDXW + ex(i);
+                                         const int q = mir ? dpos - d : dpos + d;
+                                         const uint32_t bit = mir ? (m >> (opp(i) - 1)) : (m >> (i - 1));
+                                         code = (bit & 1u) ? 1 : GEO_FLUID;
+                                         s1 = rho[q];
+                                         s2 = rho[SN1 + q];
+                                     },
+                                     fx1, fy1, fx2, fy2);
+            } else {
+                node_force<R, false>(a.p, rho1, rho2,
+                                     [&](int i, uint8_t &code, R &s1, R &s2) {
+                                         const int q = dpos + ey(i) * SDXW + ex(i);
+                                         code = ((m >> (i - 1)) & 1u) ? 1 : GEO_FLUID;
+                                         s1 = rho[q];
+                                         s2 = rho[SN1 + q];
+                                     },
+                                     fx1, fy1, fx2, fy2);
+            }
+            R omega, ux, uy;
+            node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
+            collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+            S *o = out + bidx * NPL;
+            if constexpr (P::ref) {
+                const S h1 = from_real<S>(rho1), h2 = from_real<S>(rho2);
+                o[18] = h1;
+                o[19] = h2;
+                const R q1 = to_real(h1), q2 = to_real(h2);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    o[i] = from_real<S>(f[0][i] - wgt<R>(i) * q1);
+                    o[9 + i] = from_real<S>(f[1][i] - wgt<R>(i) * q2);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    o[i] = from_real<S>(f[0][i]);
+                    o[9 + i] = from_real<S>(f[1][i]);
+                }
+            }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (warp == DW) {
+            // the tile's block (length and start in table words 4 and 5), one
+            // bulk store
+            const uint32_t own_len = T[4], start = T[5];
+            if (lane == 0 && own_len > 0)
+                bulk_s2g(fout + (size_t)start * NPL, out, own_len * (uint32_t)(NPL * sizeof(S)));
+            bulk_commit();
+        }
+        parity ^= 1u;
+        tb ^= 1;
+    }
+    if (warp == DW) bulk_wait_read();
+}
+
+// dense <-> fluid-only conversion, one thread per (slot, plane)
+template <class P>
+__global__ void to_sparse_kernel(Geometry g, const typename P::store_t *f, typename P::store_t *fs,
+                                 const int *snode, long long nfp) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nfp * P::planes) return;
+    const long long sl = k / P::planes;
+    const int pl = (int)(k - sl * P::planes);
+    const int node = snode[sl];
+    typename P::store_t v = typename P::store_t(0.f);
+    if (node >= 0) v = f[(long long)pl * g.plane + site_of(g, node % g.nx, node / g.nx)];
+    fs[k] = v;
+}
+
+template <class P>
+__global__ void to_dense_kernel(Geometry g, const typename P::store_t *fs, typename P::store_t *f,
+                                const int *snode, long long nfp) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nfp * P::planes) return;
+    const long long sl = k / P::planes;
+    const int pl = (int)(k - sl * P::planes);
+    const int node = snode[sl];
+    if (node >= 0) f[(long long)pl * g.plane + site_of(g, node % g.nx, node / g.nx)] = fs[k];
+}
+
+template <class F>
+cudaError_t dispatch_prec(mclbm_precision p, F fn) {
+    switch (p) {
+        case MCLBM_FP32: return fn(P32{});
+        case MCLBM_FP16_DEV: return fn(P16D{});
+        case MCLBM_BF16_DEV: return fn(PB16D{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host: layout and tables
+// ---------------------------------------------------------------------------
+int sparse_prepare(Lattice &L, int STY) {
+    if (!sparse_precision(L.prec) || !L.geo_pad) return MCLBM_OK;  // kernel 4 unavailable
+    if (L.sparse_mode == L.ghost_key() && L.nfp > 0 && L.sparse_ty == STY) return MCLBM_OK;
+    if (L.nfp > 0 && L.sparse_ty != STY) {
+        // another slot order: bring the state back to the dense buffers first
+        if (int rc = sparse_to_dense(L)) return rc;
+        L.sparse_state = 0;
+        L.sparse_mode = -1;
+    }
+    const int SFH = STY + 6, SN1 = SDXW * (STY + 4);
+    const int nx = L.nx, ny = L.ny;
+    const int node_bytes = L.planes * (int)L.store_bytes;
+    const int Q = 16 / ((node_bytes & 15) ? (node_bytes & 15) : 16);  // slots per 16-byte multiple
+    if ((Q * node_bytes) % 16) return MCLBM_OK;  // no 16-byte multiple of nodes: kernel 4 unavailable
+    const int planes = L.planes;
+    std::vector<uint8_t> pad((size_t)L.geo_pad_rows * L.gpitch);
+    cudaError_t e = cudaMemcpyAsync(pad.data(), L.geo_pad, pad.size(), cudaMemcpyDeviceToHost, L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "geometry read-back (fluid-only layout)");
+    // the geometry as the step sees it (ghosts per the boundary mode), up to
+    // 3 nodes past an edge: the step's reach (own nodes need forces from the
+    // 1-ring, virtual solid densities from the 2-ring, pulls from the 3-ring)
+    auto code_at = [&](int x, int y) -> int {
+        if (x < -3 || x >= nx + 3 || y < -3 || y >= ny + 3) return GEO_OUTSIDE;
+        const int r = y + HY, col = GEO_HX + x;
+        if (r < 0 || r >= L.geo_pad_rows || col < 0 || col >= L.gpitch) return GEO_OUTSIDE;
+        return pad[(size_t)r * L.gpitch + col];
+    };
+    const int tiles_x = (nx + STX - 1) / STX, tiles_y = (ny + STY - 1) / STY;
+    const int ntiles = tiles_x * tiles_y;
+    const bool open_x = L.p.open_x != 0;
+
+    // 1. blocks: own fluid nodes of every tile in band order, bands padded
+    std::vector<long long> start(ntiles + 1, 0);
+    std::vector<std::vector<int>> blk(ntiles);  // node y*nx+x per slot, -1 padding
+    // bands against the tile's extent inside the lattice (ragged edge tiles
+    // are narrower), so that what a neighbour stages stays contiguous
+    auto band = [&](int tx, int ty, int tw, int th) {
+        const bool l = tx < 3, r = tx >= tw - 3, t = ty < 3, b = ty >= th - 3;
+        if (t && l) return 0;
+        if (t && !r) return 1;
+        if (t) return 2;
+        if (r && !b) return 3;
+        if (r) return 4;
+        if (b && !l) return 5;
+        if (b) return 6;
+        if (l) return 7;
+        return 8;
+    };
+    for (int t = 0; t < ntiles; ++t) {
+        const int x0 = (t % tiles_x) * STX, y0 = (t / tiles_x) * STY;
+        std::vector<int> &B = blk[t];
+        const int tw = std::min(STX, nx - x0), th = std::min(STY, ny - y0);
+        for (int bnd = 0; bnd < 9; ++bnd) {
+            for (int ty = 0; ty < th; ++ty)
+                for (int tx = 0; tx < tw; ++tx) {
+                    const int x = x0 + tx, y = y0 + ty;
+                    if (band(tx, ty, tw, th) != bnd) continue;
+                    if (code_at(x, y) == GEO_FLUID) B.push_back(y * nx + x);
+                }
+            while (B.size() % Q) B.push_back(-1);
+        }
+        start[t + 1] = start[t] + (long long)B.size();
+    }
+    const long long nfp = std::max<long long>(start[ntiles], Q);
+    if (nfp >= (1LL << 31)) return fail(MCLBM_ERR_ARG, "lattice too large for the fluid-only layout");
+    std::vector<int> gidx((size_t)nx * ny, -1), snode((size_t)nfp, -1), bpos((size_t)nx * ny, -1);
+    for (int t = 0; t < ntiles; ++t)
+        for (size_t i = 0; i < blk[t].size(); ++i) {
+            const int n = blk[t][i];
+            snode[(size_t)(start[t] + (long long)i)] = n;
+            if (n >= 0) {
+                gidx[n] = (int)(start[t] + (long long)i);
+                bpos[n] = (int)i;
+            }
+        }
+    auto src_of = [&](int x, int y) -> int {  // slot of lattice position (x, y), wrapped
+        if (x < 0 || x >= nx) x = ((x % nx) + nx) % nx;
+        if (y < 0 || y >= ny) y = ((y % ny) + ny) % ny;
+        return gidx[(size_t)y * nx + x];
+    };
+    auto fluid_mask = [&](int x, int y) {
+        uint32_t m = 0;
+        for (int i = 1; i < 9; ++i)
+            if (code_at(x + ex(i), y + ey(i)) == GEO_FLUID) m |= 1u << (i - 1);
+        return m;
+    };
+    auto set3 = [&](int x) -> uint32_t {
+        return (open_x && x == 0 ? IN_BIT : 0u) | (open_x && x == nx - 1 ? OUT_BIT : 0u);
+    };
+
+    // 2. tables and copy records
+    const int tabcap = table_capacity(L.prec, STY), scap = staged_capacity(L.prec, STY);
+    std::vector<std::vector<uint32_t>> tabs(ntiles);
+    std::vector<uint32_t> recs((size_t)ntiles * REC_WORDS, 0);
+    int maxw = HDR;
+    long long max_own = Q, max_stage = Q;
+    for (int t = 0; t < ntiles; ++t) {
+        const int x0 = (t % tiles_x) * STX, y0 = (t / tiles_x) * STY;
+        std::vector<uint32_t> own, ring, sol;
+        std::vector<uint16_t> smap((size_t)SFW * SFH, 0);
+        for (size_t i = 0; i < blk[t].size(); ++i) {
+            const int n = blk[t][i];
+            if (n < 0) continue;
+            const int x = n % nx, y = n / nx;
+            own.push_back((uint32_t)(x - x0) | (uint32_t)(y - y0) << 6 | (~fluid_mask(x, y) & 0xffu) << 12 |
+                          set3(x) | (uint32_t)i << 22);
+            smap[(size_t)(y - y0 + 3) * SFW + (x - x0 + 3)] = (uint16_t)i;
+        }
+        for (int k = 0; k < SN1; ++k) {
+            const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
+            const bool in_tile = dr >= 2 && dr < STY + 2 && dc >= 2 && dc < STX + 2 && x < nx && y < ny;
+            if (!in_tile && code_at(x, y) == GEO_FLUID)
+                ring.push_back((uint32_t)k | (~fluid_mask(x, y) & 0xffu) << 12 | set3(x));
+        }
+        for (int k = 0; k < SN1; ++k) {
+            const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
+            if (dr < 1 || dr > STY + 2 || dc < 1 || dc > STX + 2) continue;
+            const int c = code_at(x, y);
+            if (c != GEO_FLUID) sol.push_back((uint32_t)k | (uint32_t)c << 12 | fluid_mask(x, y) << 20);
+        }
+        // ring nodes to stage: fluid positions of the staged frame outside the tile
+        std::vector<std::pair<int, int>> need;  // (slot, frame position)
+        for (int r = 0; r < SFH; ++r)
+            for (int c = 0; c < SFW; ++c) {
+                const int x = x0 - 3 + c, y = y0 - 3 + r;
+                const bool in_tile = x >= x0 && x < x0 + STX && y >= y0 && y < y0 + STY && x < nx && y < ny;
+                if (in_tile || code_at(x, y) != GEO_FLUID) continue;
+                const int gsl = src_of(x, y);
+                if (gsl < 0) return fail(MCLBM_ERR_STATE, "fluid-only layout: ring node without a slot");
+                need.push_back({gsl, r * SFW + c});
+            }
+        std::sort(need.begin(), need.end());
+        // ranges: the own block first, then runs of the ring's slots
+        const long long own_len = (long long)blk[t].size();
+        uint32_t *R = &recs[(size_t)t * REC_WORDS];
+        int nr = 0;
+        long long bytes = 0;
+        auto add_range = [&](long long src, long long len, long long dst) {
+            if (nr >= MAXR) return false;
+            R[4 + 3 * nr] = (uint32_t)src;
+            R[5 + 3 * nr] = (uint32_t)len;
+            R[6 + 3 * nr] = (uint32_t)dst;
+            ++nr;
+            bytes += len * planes * (long long)L.store_bytes;
+            return true;
+        };
+        bool ok = own_len == 0 || add_range(start[t], own_len, 0);
+        long long cursor = own_len;
+        size_t i = 0;
+        while (ok && i < need.size()) {
+            const long long a = need[i].first / Q * Q;
+            size_t j = i;
+            while (j + 1 < need.size() && need[j + 1].first - need[j].first <= Q) ++j;
+            const long long b = (need[j].first / Q + 1) * Q;  // exclusive, 16-byte multiple
+            if (b > nfp || cursor + (b - a) > scap) {
+                ok = false;
+                break;
+            }
+            for (size_t k = i; k <= j; ++k)
+                smap[(size_t)need[k].second] = (uint16_t)(cursor + need[k].first - a);
+            ok = add_range(a, b - a, cursor);
+            cursor += b - a;
+            i = j + 1;
+        }
+        const long long words = HDR + (long long)own.size() + ring.size() + sol.size() + (smap.size() + 1) / 2;
+        if (!ok || words > tabcap || own.size() > (size_t)STX * STY)
+            return fail(MCLBM_ERR_STATE, "fluid-only layout: tile " + std::to_string(t) +
+                                             " exceeds the staging capacity");
+        max_own = std::max(max_own, own_len);
+        max_stage = std::max(max_stage, cursor);
+        R[0] = (uint32_t)nr;
+        R[1] = (uint32_t)bytes;
+        R[2] = (uint32_t)own_len;
+        R[3] = (uint32_t)start[t];
+        std::vector<uint32_t> &T = tabs[t];
+        T.assign(HDR, 0);
+        T[0] = (uint32_t)own.size();
+        T[1] = (uint32_t)ring.size();
+        T[2] = (uint32_t)sol.size();
+        T[3] = 0;
+        T[4] = (uint32_t)own_len;
+        T[5] = (uint32_t)start[t];
+        T.insert(T.end(), own.begin(), own.end());
+        T.insert(T.end(), ring.begin(), ring.end());
+        T.insert(T.end(), sol.begin(), sol.end());
+        for (size_t k = 0; k < smap.size(); k += 2)
+            T.push_back((uint32_t)smap[k] | (k + 1 < smap.size() ? (uint32_t)smap[k + 1] << 16 : 0u));
+        maxw = std::max(maxw, (int)T.size());
+    }
+    const int tab_words = (maxw + 3) / 4 * 4;
+    if (tab_words > tabcap) return fail(MCLBM_ERR_STATE, "fluid-only layout: tables too large");
+    std::vector<uint32_t> flat((size_t)ntiles * tab_words, 0);
+    for (int t = 0; t < ntiles; ++t) std::copy(tabs[t].begin(), tabs[t].end(), flat.begin() + (size_t)t * tab_words);
+
+    // 3. device buffers (the populations only when the slot count changed)
+    auto realloc = [&](void **p, size_t bytes) -> cudaError_t {
+        cudaFree(*p);
+        *p = nullptr;
+        return cudaMalloc(p, bytes);
+    };
+    if (L.nfp != nfp || L.sparse_ty != STY) {
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+            e = realloc(&L.fs[b], (size_t)planes * nfp * L.store_bytes);
+        if (e == cudaSuccess) e = realloc((void **)&L.snode, (size_t)nfp * sizeof(int));
+        L.sparse_state = 0;
+    }
+    if (e == cudaSuccess) e = realloc((void **)&L.stab, flat.size() * 4);
+    if (e == cudaSuccess) e = realloc((void **)&L.scopy, recs.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.snode, snode.data(), snode.size() * sizeof(int),
+                                              cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.stab, flat.data(), flat.size() * 4, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L.scopy, recs.data(), recs.size() * 4, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        L.nfp = 0;
+        return cuda_fail(e, "fluid-only layout buffers");
+    }
+    L.nfp = nfp;
+    L.stab_words = tab_words;
+    L.sparse_ty = STY;
+    L.socap = (int)max_own;
+    L.sscap = (int)((max_stage + 15) / 16 * 16);
+    L.sparse_mode = L.ghost_key();
+    return MCLBM_OK;
+}
+
+void sparse_release(Lattice &L) {
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(L.fs[b]);
+        L.fs[b] = nullptr;
+    }
+    cudaFree(L.stab);
+    cudaFree(L.scopy);
+    cudaFree(L.snode);
+    L.stab = nullptr;
+    L.scopy = nullptr;
+    L.snode = nullptr;
+    L.nfp = 0;
+}
+
+int dense_to_sparse(Lattice &L) {
+    if (L.sparse_state != 0) return MCLBM_OK;
+    if (L.nfp <= 0) return fail(MCLBM_ERR_STATE, "the fluid-only layout is not prepared");
+    const Geometry g = L.geometry();
+    cudaError_t e = dispatch_prec(L.prec, [&](auto tag) {
+        using P = decltype(tag);
+        const long long n = L.nfp * P::planes;
+        to_sparse_kernel<P><<<(unsigned)((n + 255) / 256), 256, 0, L.stream>>>(
+            g, static_cast<const typename P::store_t *>(L.f[L.cur]), static_cast<typename P::store_t *>(L.fs[0]),
+            L.snode, L.nfp);
+        count_launch();
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "dense to fluid-only conversion");
+    L.scur = 0;
+    L.sparse_state = 2;
+    return MCLBM_OK;
+}
+
+int sparse_to_dense(Lattice &L) {
+    if (L.sparse_state != 1) return MCLBM_OK;
+    const Geometry g = L.geometry();
+    cudaError_t e = dispatch_prec(L.prec, [&](auto tag) {
+        using P = decltype(tag);
+        const long long n = L.nfp * P::planes;
+        to_dense_kernel<P><<<(unsigned)((n + 255) / 256), 256, 0, L.stream>>>(
+            g, static_cast<const typename P::store_t *>(L.fs[L.scur]), static_cast<typename P::store_t *>(L.f[L.cur]),
+            L.snode, L.nfp);
+        count_launch();
+        return cudaGetLastError();
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "fluid-only to dense conversion");
+    L.sparse_state = 2;
+    L.pop_ghosts_stale = true;  // rebuilt before the next dense step
+    return MCLBM_OK;
+}
+
+namespace {
+template <class P, int STY>
+cudaError_t launch_sparse(Lattice &L) {
+    {
+        using Lay = SLayout<P, STY>;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(sparse_kernel<P, STY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)Lay::total);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        SArgs s{};
+        const size_t bytes = smem_layout<P, STY>(L.sscap, L.socap, L.stab_words, s);
+        if (bytes > Lay::total) return cudaErrorInvalidValue;
+        // resident CTAs per SM for this size (cached per size)
+        static size_t last_bytes = 0;
+        static int slots = 0;
+        if (bytes != last_bytes) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY>, STX * STY, bytes);
+            slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
+            last_bytes = bytes;
+        }
+        s.a.g = L.geometry();
+        s.a.p = L.p;
+        s.a.p.round_fp32();
+        s.a.d5 = L.d5;
+        s.a.err = L.err;
+        s.fin = L.fs[L.scur];
+        s.fout = L.fs[1 - L.scur];
+        s.nfp = L.nfp;
+        s.tab = L.stab;
+        s.rec = L.scopy;
+        s.tab_words = L.stab_words;
+        s.tiles_x = (L.nx + STX - 1) / STX;
+        s.ntiles = s.tiles_x * ((L.ny + STY - 1) / STY);
+        const int grid = slots < s.ntiles ? slots : s.ntiles;
+        sparse_kernel<P, STY><<<grid, STX * STY, bytes, L.stream>>>(s);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) {
+            L.scur = 1 - L.scur;
+            L.sparse_state = 1;
+        }
+        return e;
+    }
+}
+}  // namespace
+
+cudaError_t launch_step_sparse(Lattice &L) {
+    return dispatch_prec(L.prec, [&](auto tag) {
+        using P = decltype(tag);
+        return L.sparse_ty == 8 ? launch_sparse<P, 8>(L) : launch_sparse<P, 12>(L);
+    });
+}
+
+}  // namespace mclbm

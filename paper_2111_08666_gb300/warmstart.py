@@ -235,10 +235,11 @@ def main(argv=None) -> None:
     ap.add_argument("--eval-levels", type=int, default=20)
     ap.add_argument("--max-steps", type=int, default=40000)
     ap.add_argument("--d-rho", type=float, default=0.002)
+    ap.add_argument("--tol", type=float, default=1e-6)
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
-                                 d_rho=a.d_rho, max_steps=a.max_steps)
+                                 d_rho=a.d_rho, tol=a.tol, max_steps=a.max_steps)
     t_data = time.perf_counter() - t0
     net = mclbm.UNet(4, 32, max_batch=16, max_h=256, max_w=256)
     net.set_params(init_params(4, 32, 0))
@@ -249,7 +250,8 @@ def main(argv=None) -> None:
     big.set_params(net.params())
     net.close()
     case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
-    rec = compare_warm_cold(big, case, levels=a.eval_levels, d_rho=a.d_rho, max_steps=a.max_steps)
+    rec = compare_warm_cold(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
+                            max_steps=a.max_steps)
     summary = dict(train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train, loss=hist,
                    pair_steps_mean=float(st.mean()),
                    steps_cold=int(sum(r["steps_cold"] for r in rec)),

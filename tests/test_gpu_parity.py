@@ -274,13 +274,15 @@ AGREE = {"fp32": (1e-6, 4e-6), "fp32dev": (1e-6, 4e-6), "fp16dev": (1e-4, 1e-3),
          "bf16dev": (1e-3, 4e-3)}
 
 
-@pytest.mark.parametrize("other", [2, 3])
+@pytest.mark.parametrize("other", [2, 3, 4])
 @pytest.mark.parametrize("prec", ["fp32", "fp32dev", "fp16dev", "bf16dev"])
 def test_step_kernels_agree(prec, other):
-    """The formulations of the step (global-pull tile, strip, TMA tile)
-    compute the same update of Eqs. 1-29 in every storage precision; they
-    differ only in data movement and in how the compiler fuses the FP32
-    multiply-adds, so they agree to rounding."""
+    """The formulations of the step (global-pull tile, strip, TMA tile,
+    fluid-only) compute the same update of Eqs. 1-29 in every storage
+    precision; they differ only in data movement and in how the compiler
+    fuses the FP32 multiply-adds, so they agree to rounding."""
+    if other == 4 and prec == "fp32dev":
+        pytest.skip("the fluid-only kernel serves FP32 and the 16-bit storages")
     m = media.make_disk_medium(200, 70, 11, radius="uniform", r_lo=3.0, r_hi=6.0,
                                porosity=0.7)
     xi = media.uniform_xi(m.solid, -0.4)
@@ -379,3 +381,87 @@ def test_checkpoint_restores_bit_for_bit(prec, tmp_path):
     other = mclbm.Lattice(m.solid[:, :64], xi[:, :64], prec=prec)
     with pytest.raises(mclbm.MclbmError):
         mclbm.mclbm_load(other.h, path)
+
+
+
+@pytest.mark.parametrize("tile_shape", [0, 1])
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("periodic_y,open_x", [(True, False), (True, True), (False, False),
+                                               (False, True)])
+def test_fluid_only_kernel_ragged_lattice(prec, periodic_y, open_x, tile_shape):
+    """Kernel 4 stages ring nodes across periodic edges from their own tiles
+    (no ghost copies); a lattice off every tile multiple, against kernel 1."""
+    nx, ny = 75, 41
+    solid = np.zeros((ny, nx), np.uint8)
+    if not periodic_y:
+        solid[0] = solid[-1] = 1
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    solid[(xx - 50) ** 2 + (yy - 20) ** 2 <= 30] = 1
+    solid[(xx - 8) ** 2 + (yy - 31) ** 2 <= 12] = 1
+    xi = media.uniform_xi(solid, -0.3)
+    kw = dict(prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), periodic_y=periodic_y)
+    if open_x:
+        rho1, rho2 = media.drainage_densities(solid)
+        kw.update(rho_in1=1.01, rho_out2=1.0)
+    else:
+        rho1, rho2 = media.droplet_densities(nx, ny, 70, 20, 9, solid=solid)
+    a = mclbm.Lattice(solid, xi, kernel=1, **kw)
+    b = mclbm.Lattice(solid, xi, kernel=4, tile_shape=tile_shape, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(1)
+    b.step(1)
+    scale = np.max(np.abs(a.populations()))
+    assert np.max(np.abs(a.populations() - b.populations())) <= AGREE[prec][0] * scale
+    a.step(199)
+    b.step(199)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= AGREE[prec][1] * np.max(np.abs(fa))
+
+
+def test_fluid_only_readouts_and_kernel_switches():
+    """Read-outs between fluid-only steps convert the layouts without loss,
+    and switching kernels mid-run continues the same trajectory."""
+    m = media.make_disk_medium(150, 70, 5, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.3)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    kw = dict(prec="fp32", nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+    a = mclbm.Lattice(m.solid, xi, kernel=4, **kw)
+    b = mclbm.Lattice(m.solid, xi, kernel=4, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(100)
+    for _ in range(10):
+        b.step(10)
+        b.diagnostics()
+        b.density()
+    assert np.array_equal(a.populations(), b.populations())
+    assert a.diagnostics() == b.diagnostics()
+    # kernel 4 -> 3 -> 4 against kernel 3 throughout
+    c = mclbm.Lattice(m.solid, xi, kernel=3, **kw)
+    c.init(rho1, rho2)
+    c.step(100)
+    mclbm.mclbm_set_flag(a.h, mclbm.MCLBM_FLAG_KERNEL, 3)
+    a.step(50)
+    c.step(50)
+    mclbm.mclbm_set_flag(a.h, mclbm.MCLBM_FLAG_KERNEL, 4)
+    a.step(50)
+    c.step(50)
+    fa, fc = a.populations(), c.populations()
+    assert np.max(np.abs(fa - fc)) <= AGREE["fp32"][1] * np.max(np.abs(fc))
+
+
+def test_fluid_only_kernel_paper_scale_medium():
+    """The heterogeneous lognormal disk medium at 1024x512 (many tiles,
+    mixed band sizes) against the dense tile kernel."""
+    c = media.config_paper_scale(1024, 512, 1)
+    kw = dict(prec="fp32", nu1=c["nu1"], nu2=c["nu2"], rho_in1=1.005, rho_out2=1.0)
+    a = mclbm.Lattice(c["solid"], c["xi"], kernel=3, **kw)
+    b = mclbm.Lattice(c["solid"], c["xi"], kernel=4, **kw)
+    a.init(c["rho1"], c["rho2"])
+    b.init(c["rho1"], c["rho2"])
+    a.step(50)
+    b.step(50)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= AGREE["fp32"][1] * np.max(np.abs(fa))
+    assert a.diagnostics()["mass1"] == pytest.approx(b.diagnostics()["mass1"], rel=1e-6)
