@@ -39,19 +39,39 @@ from paper_2111_08666_gb300 import media, replicas  # noqa: E402
 METRIC = "2-comp D2Q9 MLUPS (fused step, FP32 storage)"
 UNIT = "MLUPS"
 FALLBACK_HBM_GBS = 6800.0
-# DRAM bytes per fused-step launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum) on the workload below, and the hash of the kernel
-# sources they were taken with; reported only while the sources match.
-NCU_TRAFFIC = {"bytes_per_launch": 268262144, "source_sha": "127f58da57dc516e"}
-KERNEL_SOURCES = ["paper_2111_08666_gb300/csrc/tma_tile.cu",
-                  "paper_2111_08666_gb300/csrc/async_copy.cuh",
-                  "paper_2111_08666_gb300/csrc/lbm_device.cuh",
-                  "paper_2111_08666_gb300/csrc/lbm.cuh"]
+# The step kernels: their sources, and the DRAM bytes per launch from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the workload below with
+# the hash of the sources they were taken with; reported only while the
+# sources match.
+_COMMON = ["paper_2111_08666_gb300/csrc/async_copy.cuh",
+           "paper_2111_08666_gb300/csrc/lbm_device.cuh",
+           "paper_2111_08666_gb300/csrc/lbm.cuh"]
+STEP_KERNELS = {
+    "sparse_kernel": {"sources": ["paper_2111_08666_gb300/csrc/sparse.cu"] + _COMMON,
+                      "ncu_bytes": None, "ncu_sha": None},
+    "tma_tile_kernel": {"sources": ["paper_2111_08666_gb300/csrc/tma_tile.cu"] + _COMMON,
+                        "ncu_bytes": 268262144, "ncu_sha": "127f58da57dc516e"},
+    "fused_step_kernel": {"sources": ["paper_2111_08666_gb300/csrc/step.cu"] + _COMMON,
+                          "ncu_bytes": None, "ncu_sha": None},
+    "sweep_kernel": {"sources": ["paper_2111_08666_gb300/csrc/sweep.cu"] + _COMMON,
+                     "ncu_bytes": None, "ncu_sha": None},
+}
+FLUID_ONLY_PRECISIONS = ("fp32", "fp16dev", "bf16dev")
 
 
-def kernel_sha() -> str:
+def step_kernel(kernel: str, prec: str) -> str:
+    """Name of the kernel a step runs (the library's automatic choice for 'auto')."""
+    if kernel == "auto":
+        if prec in FLUID_ONLY_PRECISIONS:
+            return "sparse_kernel"
+        return "fused_step_kernel" if prec == "fp64" else "tma_tile_kernel"
+    return {"tile": "fused_step_kernel", "strip": "sweep_kernel", "tma": "tma_tile_kernel",
+            "fluid": "sparse_kernel"}[kernel]
+
+
+def kernel_sha(name: str = "sparse_kernel") -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in STEP_KERNELS[name]["sources"]:
         h.update((ROOT / p).read_bytes())
     return h.hexdigest()[:16]
 
@@ -183,8 +203,10 @@ def run_gpu(args, rank, world):
     peak, peak_kind = measured_peaks()
     achieved = abytes / per_launch / 1e9
     traffic = None
-    if NCU_TRAFFIC["source_sha"] == kernel_sha() and NCU_TRAFFIC["bytes_per_launch"]:
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    kname = step_kernel(args.kernel, args.prec)
+    rec = STEP_KERNELS[kname]
+    if rec["ncu_bytes"] and rec["ncu_sha"] == kernel_sha(kname):
+        traffic = rec["ncu_bytes"]
 
     # end to end through the public API with host buffers: upload the
     # initial densities, step, read back the water density and diagnostics
@@ -250,7 +272,7 @@ def run_gpu(args, rank, world):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": abytes,
-                     "kernel": "tma_tile_kernel", "launch_us": round(per_launch * 1e6, 3)},
+                     "kernel": kname, "launch_us": round(per_launch * 1e6, 3)},
         "e2e": {"value": round(e2e_units / e2e_job / 1e6, 1), "unit": UNIT,
                 "h2d_bytes_per_step": round(h2d / e2e_steps, 1),
                 "d2h_bytes_per_step": round(d2h / e2e_steps, 1)},
@@ -291,27 +313,34 @@ def batched_section(args, stream) -> dict:
         tuning = mclbm.mclbm_batch_tuning(b)
     finally:
         mclbm.mclbm_batch_destroy(b)
-    lats = []
-    for c in cases:
-        lat = mclbm.Lattice(c["solid"], c["xi"], prec="fp32", nu1=c["nu1"], nu2=c["nu2"],
-                            rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream)
-        lat.init(c["rho1"], c["rho2"])
-        lat.step(3)
-        lats.append(lat)
-    torch.cuda.synchronize()
-    start.record(stream)
-    for lat in lats:
-        lat.step(k_steps)
-    end.record(stream)
-    torch.cuda.synchronize()
-    t_seq = start.elapsed_time(end) / 1e3
-    for lat in lats:
-        lat.close()
+    def one_at_a_time(kernel):
+        lats = []
+        for c in cases:
+            lat = mclbm.Lattice(c["solid"], c["xi"], prec="fp32", nu1=c["nu1"], nu2=c["nu2"],
+                                rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream,
+                                kernel=kernel)
+            lat.init(c["rho1"], c["rho2"])
+            lat.step(3)
+            lats.append(lat)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for lat in lats:
+            lat.step(k_steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        t = start.elapsed_time(end) / 1e3
+        for lat in lats:
+            lat.close()
+        return t
+
+    t_seq = one_at_a_time(3)       # the batch's kernel, one launch per lattice
+    t_fluid = one_at_a_time(4)     # the fluid-only kernel, one lattice at a time
     return {"workload": "24 disk media 256x256..1024x512, seeds 10-33, theta 30-150 deg, "
                         "M=1/10/50, FP32, drainage rho_in=1.005",
             "nodes": nodes, "steps": k_steps,
             "mlups_batched": round(nodes * k_steps / t_batch / 1e6, 1),
             "mlups_one_at_a_time": round(nodes * k_steps / t_seq / 1e6, 1),
+            "mlups_one_at_a_time_fluid_only": round(nodes * k_steps / t_fluid / 1e6, 1),
             "launches": int(launches), "tile_shape": info["shape"],
             "grid": "persistent" if info["grid"] == 0 else "one CTA per tile",
             "tuner_ms_per_step": [round(x, 4) for x in tuning]}

@@ -72,8 +72,9 @@ typedef enum {
      * or negative density); a hit is reported by the next synchronising
      * call as MCLBM_ERR_DIVERGED.  0 (default): off. */
     MCLBM_FLAG_DIAG_EVERY = 2,
-    /* Step kernel, all computing the same update: 0 (default) chooses 3
-     * for the FP32 and deviation storages and 1 for FP64; 1 the 2-D tile
+    /* Step kernel, all computing the same update: 0 (default) chooses 4
+     * for FP32 and the 16-bit deviation storages, 3 for FP32 deviation
+     * storage (or where 4 cannot stage a tile) and 1 for FP64; 1 the 2-D tile
      * kernel pulling straight from global memory; 2 the row-sweeping strip
      * kernel staging rows with bulk copies; 3 the 2-D tile kernel staging
      * the tile and its ring with one tensor copy (not for FP64); 4 the

@@ -632,7 +632,14 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
     if (int rc = make_current(*lat)) return rc;
     if (int rc = refresh_ghosts(*lat)) return rc;
     int which = (int)lat->kernel;
-    if (which == 0) which = tma_supported(*lat) ? 3 : 1;
+    if (which == 0) {
+        // the fluid-only kernel where it serves this precision and geometry,
+        // else the TMA tile kernel, else (FP64) the global-memory tile kernel
+        which = tma_supported(*lat) ? 3 : 1;
+        if (sparse_precision(lat->prec)) {
+            if (sparse_prepare(*lat, lat->tile_shape == 1 ? 8 : 12) == MCLBM_OK && lat->nfp > 0) which = 4;
+        }
+    }
     if (which == 3 && !tma_supported(*lat))
         return fail(MCLBM_ERR_ARG, "the TMA tile kernel is not available for this precision");
     if (which == 2 && !sweep_supported(*lat))
