@@ -214,33 +214,35 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
         const uint32_t *T = tabs + tb * s.tab_words;
         const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
         const uint32_t *E = T + HDR;
-        // staged slot of every frame position (0 where nothing is staged)
+        // staged element offset (slot x planes) of every frame position (0
+        // where nothing is staged)
         const uint16_t *slot_of = reinterpret_cast<const uint16_t *>(E + n_own + n_ring + n_sol);
         const bool have = tid < n_own;
         const uint32_t me = have ? E[tid] : 0u;
         const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u), bidx = (int)(me >> 22);
 
-        auto val = [&](int plane, int comp, int slot, R wt) -> R {
-            R v = to_real(stg[slot * NPL + comp * 9 + plane]);
-            if constexpr (P::ref) v += wt * to_real(stg[slot * NPL + 18 + comp]);
+        // population (plane, comp) of the staged node at element offset off
+        auto val = [&](int plane, int comp, int off, R wt) -> R {
+            R v = to_real(stg[off + comp * 9 + plane]);
+            if constexpr (P::ref) v += wt * to_real(stg[off + 18 + comp]);
             return v;
         };
         // f_i = f*_i(x - e_i), or the node's own f*_opp(i) where x - e_i is not
         // fluid (half-way bounce-back), then Set-3 at the open ends
-        auto pull = [&](int fpos, int oslot, uint32_t e, int x, int y, R f[2][9]) {
+        auto pull = [&](int fpos, int ooff, uint32_t e, int x, int y, R f[2][9]) {
             const uint32_t m = (e >> 12) & 0xffu;
-            f[0][0] = val(0, 0, oslot, wgt<R>(0));
-            f[1][0] = val(0, 1, oslot, wgt<R>(0));
+            f[0][0] = val(0, 0, ooff, wgt<R>(0));
+            f[1][0] = val(0, 1, ooff, wgt<R>(0));
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const bool sb = (m >> (opp(i) - 1)) & 1u;
-                const int slot = sb ? oslot : (int)slot_of[fpos - ey(i) * SFW - ex(i)];
+                const int off = sb ? ooff : (int)slot_of[fpos - ey(i) * SFW - ex(i)];
                 const int pl = sb ? opp(i) : i;
-                f[0][i] = val(pl, 0, slot, wgt<R>(i));
-                f[1][i] = val(pl, 1, slot, wgt<R>(i));
+                f[0][i] = val(pl, 0, off, wgt<R>(i));
+                f[1][i] = val(pl, 1, off, wgt<R>(i));
             }
             if (e & SET3)
-                apply_set3<R>(a, x, y, [&](int comp, int i) { return val(i, comp, oslot, wgt<R>(i)); }, f);
+                apply_set3<R>(a, x, y, [&](int comp, int i) { return val(i, comp, ooff, wgt<R>(i)); }, f);
         };
 
         // ---- A: densities of the ring's fluid nodes and of the tile's own ------
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
         R f[2][9];
         R rho1 = 0, rho2 = 0;
         if (have) {
-            pull((ty + 3) * SFW + tx + 3, bidx, me, x0 + tx, y0 + ty, f);
+            pull((ty + 3) * SFW + tx + 3, bidx * NPL, me, x0 + tx, y0 + ty, f);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 rho1 += f[0][i];
@@ -536,7 +538,7 @@ int sparse_prepare(Lattice &L, int STY) {
             const int x = n % nx, y = n / nx;
             own.push_back((uint32_t)(x - x0) | (uint32_t)(y - y0) << 6 | (~fluid_mask(x, y) & 0xffu) << 12 |
                           set3(x) | (uint32_t)i << 22);
-            smap[(size_t)(y - y0 + 3) * SFW + (x - x0 + 3)] = (uint16_t)i;
+            smap[(size_t)(y - y0 + 3) * SFW + (x - x0 + 3)] = (uint16_t)(i * planes);
         }
         for (int k = 0; k < SN1; ++k) {
             const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
@@ -589,13 +591,13 @@ int sparse_prepare(Lattice &L, int STY) {
                 break;
             }
             for (size_t k = i; k <= j; ++k)
-                smap[(size_t)need[k].second] = (uint16_t)(cursor + need[k].first - a);
+                smap[(size_t)need[k].second] = (uint16_t)((cursor + need[k].first - a) * planes);
             ok = add_range(a, b - a, cursor);
             cursor += b - a;
             i = j + 1;
         }
         const long long words = HDR + (long long)own.size() + ring.size() + sol.size() + (smap.size() + 1) / 2;
-        if (!ok || words > tabcap || own.size() > (size_t)STX * STY)
+        if (!ok || words > tabcap || own.size() > (size_t)STX * STY || cursor * planes > 65535)
             return fail(MCLBM_ERR_STATE, "fluid-only layout: tile " + std::to_string(t) +
                                              " exceeds the staging capacity");
         max_own = std::max(max_own, own_len);
