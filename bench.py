@@ -341,7 +341,8 @@ def batched_section(args, stream) -> dict:
             "mlups_batched": round(nodes * k_steps / t_batch / 1e6, 1),
             "mlups_one_at_a_time": round(nodes * k_steps / t_seq / 1e6, 1),
             "mlups_one_at_a_time_fluid_only": round(nodes * k_steps / t_fluid / 1e6, 1),
-            "launches": int(launches), "tile_shape": info["shape"],
+            "launches": int(launches),
+            "step": ["tile 32x16", "tile 32x8", "fluid-only 32x12", "fluid-only 32x8"][info["shape"]],
             "grid": "persistent" if info["grid"] == 0 else "one CTA per tile",
             "tuner_ms_per_step": [round(x, 4) for x in tuning]}
 

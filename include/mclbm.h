@@ -273,23 +273,25 @@ int mclbm_batch_destroy(mclbm_batch *b);
  * its graph. */
 int mclbm_batch_lattice(mclbm_batch *b, int k, mclbm_lattice **view);
 
-/* Advance every case nsteps steps.  The first call times the candidate tile
- * shapes and grid sizes on its first steps (ordinary steps: all candidates
- * compute identical results) and keeps the fastest; steps then run in
- * graph replays of 16 launches.  Asynchronous. */
+/* Advance every case nsteps steps.  The first call times the candidate
+ * kernels, tile shapes and grid sizes on its first steps (ordinary steps:
+ * all candidates compute the same update, to rounding) and keeps the
+ * fastest; steps then run in graph replays of 16 launches.  Asynchronous. */
 int mclbm_batch_step(mclbm_batch *b, int64_t nsteps);
 
-/* out[0] cases, out[1] total nodes, out[2] chosen tile shape (0: 32 x 16
- * or 32 x 12, 1: 32 x 8; -1 not yet chosen), out[3] grid (0: one CTA per
- * resident slot, persistent; -1: one CTA per tile), out[4] steps per graph
- * replay, out[5] steps taken, out[6] resident CTA slots, out[7] 1 if a graph
- * is captured. */
+/* out[0] cases, out[1] total nodes, out[2] chosen step (0: tile kernel
+ * 32 x 16 or 32 x 12, 1: tile kernel 32 x 8, 2: fluid-only kernel 32 x 12,
+ * 3: fluid-only kernel 32 x 8; -1 not yet chosen), out[3] grid (0: one CTA
+ * per resident slot, persistent; -1: one CTA per tile), out[4] steps per
+ * graph replay, out[5] steps taken, out[6] resident CTA slots of the tile
+ * kernel (0 for the fluid-only kernel), out[7] 1 if a graph is captured. */
 int mclbm_batch_info(mclbm_batch *b, int64_t out[8]);
 
-/* Milliseconds per step the tuner measured for its 4 candidates (shape 0
- * persistent, shape 0 one CTA per tile, shape 1 persistent, shape 1 one CTA
- * per tile). */
-int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[4]);
+/* Milliseconds per step the tuner measured for its 6 candidates: the tile
+ * kernel at shape 0 persistent, shape 0 one CTA per tile, shape 1
+ * persistent, shape 1 one CTA per tile; the fluid-only kernel at 32 x 12
+ * and 32 x 8 (persistent).  -1 for a candidate not available. */
+int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[6]);
 
 /* Checkpoint: write the current state (populations as stored, the outlet
  * record of Eq. 26, the parameters and the step count) to a file, and read

@@ -11,15 +11,19 @@
 
 using namespace mclbm;
 
+constexpr int NCAND = 6;
+
 struct mclbm_batch {
     std::vector<mclbm_lattice *> cases;
     mclbm_precision prec = MCLBM_FP32;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::vector<unsigned char> maps[2];  // tensor descriptors per tile shape
-    int shape = -1;                      // chosen tile shape (-1: not tuned yet)
-    int grid = 0;                        // 0: resident CTA slots; otherwise the CTA count
-    double tune_ms[4] = {0, 0, 0, 0};
+    // chosen step (-1: not tuned yet): 0-3 the dense tile kernel (tile shape
+    // 0 or 1, persistent or one CTA per tile), 4-5 the fluid-only kernel
+    // (tile 32x12 or 32x8, persistent)
+    int cand = -1;
+    double tune_ms[NCAND] = {0, 0, 0, 0, 0, 0};
     cudaGraphExec_t graph = nullptr;
     int graph_parity = 0;
     uint64_t graph_version = ~0ull;
@@ -37,10 +41,43 @@ uint64_t version_of(const mclbm_batch &b) {
     return v;
 }
 
-int direct_step(mclbm_batch &b, int shape, int grid) {
+bool fluid_cand(int cand) { return cand >= 4; }
+int shape_of_cand(int cand) { return fluid_cand(cand) ? cand - 4 : cand / 2; }
+int grid_of_cand(int cand) { return !fluid_cand(cand) && cand % 2 ? 1 << 30 : 0; }
+
+// bring every case to the layout the step of candidate cand works on
+int ensure_layout(mclbm_batch &b, int cand) {
+    for (auto *L : b.cases) {
+        if (fluid_cand(cand)) {
+            if (int rc = sparse_prepare(*L, shape_of_cand(cand) == 1 ? 8 : 12)) return rc;
+            if (L->nfp <= 0) return fail(MCLBM_ERR_STATE, "fluid-only layout unavailable for a case");
+            if (int rc = dense_to_sparse(*L)) return rc;
+        } else {
+            if (int rc = dense_current(*L)) return rc;
+        }
+    }
+    return MCLBM_OK;
+}
+
+int parity_of(const mclbm_batch &b, int cand) {
+    return fluid_cand(cand) ? b.cases[0]->scur : b.cases[0]->cur;
+}
+
+// the launch of one step (layout already current)
+cudaError_t launch_cand(mclbm_batch &b, int cand) {
     std::vector<Lattice *> ls(b.cases.begin(), b.cases.end());
-    cudaError_t e = launch_step_batch(ls.data(), (int)ls.size(), b.maps[shape].data(), shape, grid,
-                                      b.stream);
+    if (fluid_cand(cand)) return launch_step_sparse_batch(ls.data(), (int)ls.size(), 0, b.stream);
+    const int shape = shape_of_cand(cand);
+    cudaError_t e = launch_step_batch(ls.data(), (int)ls.size(), b.maps[shape].data(), shape,
+                                      grid_of_cand(cand), b.stream);
+    if (e == cudaSuccess)
+        for (auto *L : b.cases) L->sparse_state = 0;
+    return e;
+}
+
+int direct_step(mclbm_batch &b, int cand) {
+    if (int rc = ensure_layout(b, cand)) return rc;
+    cudaError_t e = launch_cand(b, cand);
     if (e != cudaSuccess) return cuda_fail(e, "batched step kernel");
     for (auto *L : b.cases) ++L->steps;
     ++b.steps;
@@ -52,16 +89,14 @@ void drop_graph(mclbm_batch &b) {
     b.graph = nullptr;
 }
 
-// Time every candidate (tile shape x grid) on a few real steps of the batch
-// and keep the fastest.  The candidates compute identical results, so the
+// Time every candidate on a few real steps of the batch and keep the
+// fastest.  The candidates compute the same update (to rounding), so the
 // trial steps are ordinary steps of the simulation.  Returns steps used.
 int autotune(mclbm_batch &b, int64_t budget, int *rc) {
     *rc = MCLBM_OK;
     const int reps = 2;
-    const int n_cand = 4;
-    if (budget < (int64_t)n_cand * (reps + 1)) {
-        b.shape = 0;
-        b.grid = 0;
+    if (budget < (int64_t)NCAND * (reps + 1)) {
+        b.cand = 0;
         return 0;
     }
     cudaEvent_t t0, t1;
@@ -69,14 +104,23 @@ int autotune(mclbm_batch &b, int64_t budget, int *rc) {
     cudaEventCreate(&t1);
     int used = 0;
     double best = 1e300;
-    for (int c = 0; c < n_cand && *rc == MCLBM_OK; ++c) {
-        const int shape = c / 2;
-        const int grid = (c % 2 == 0) ? 0 : 1 << 30;  // resident slots, or one CTA per tile
-        if ((*rc = direct_step(b, shape, grid))) break;  // warm-up
+    for (int c = 0; c < NCAND && *rc == MCLBM_OK; ++c) {
+        if (fluid_cand(c) && !sparse_precision(b.prec)) {
+            b.tune_ms[c] = -1;
+            continue;
+        }
+        if ((*rc = direct_step(b, c))) {  // warm-up (and layout conversion)
+            if (fluid_cand(c)) {          // a geometry the fluid-only kernel cannot stage
+                *rc = MCLBM_OK;
+                b.tune_ms[c] = -1;
+                continue;
+            }
+            break;
+        }
         ++used;
         cudaEventRecord(t0, b.stream);
         for (int r = 0; r < reps && *rc == MCLBM_OK; ++r) {
-            *rc = direct_step(b, shape, grid);
+            *rc = direct_step(b, c);
             ++used;
         }
         cudaEventRecord(t1, b.stream);
@@ -86,33 +130,34 @@ int autotune(mclbm_batch &b, int64_t budget, int *rc) {
         b.tune_ms[c] = ms / reps;
         if (ms < best) {
             best = ms;
-            b.shape = shape;
-            b.grid = grid;
+            b.cand = c;
         }
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
+    if (b.cand < 0) b.cand = 0;
     return used;
 }
 
 int capture_graph(mclbm_batch &b) {
     drop_graph(b);
+    if (int rc = ensure_layout(b, b.cand)) return rc;  // conversions are not captured
     const int64_t launches0 = mclbm_launch_count();
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    const int parity = b.cases[0]->cur;
-    std::vector<Lattice *> ls(b.cases.begin(), b.cases.end());
+    const int parity = parity_of(b, b.cand);
     cudaError_t le = cudaSuccess;
-    for (int s = 0; s < GRAPH_STEPS && le == cudaSuccess; ++s)
-        le = launch_step_batch(ls.data(), (int)ls.size(), b.maps[b.shape].data(), b.shape, b.grid,
-                               b.stream);
+    for (int s = 0; s < GRAPH_STEPS && le == cudaSuccess; ++s) le = launch_cand(b, b.cand);
     e = cudaStreamEndCapture(b.stream, &g);
     // the captured launches ran nothing yet: undo their bookkeeping
     count_launch((int)(launches0 - mclbm_launch_count()));
     if (le != cudaSuccess || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        for (auto *L : b.cases) L->cur = parity;
+        for (auto *L : b.cases) {
+            if (fluid_cand(b.cand)) L->scur = parity;
+            else L->cur = parity;
+        }
         return cuda_fail(le != cudaSuccess ? le : e, "graph capture of the batched step");
     }
     e = cudaGraphInstantiate(&b.graph, g, 0);
@@ -209,24 +254,27 @@ int mclbm_batch_step(mclbm_batch *b, int64_t nsteps) {
     if (!b) return fail(MCLBM_ERR_ARG, "batch is NULL");
     if (nsteps < 0) return fail(MCLBM_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return MCLBM_OK;
-    const int parity = b->cases[0]->cur;
     for (auto *L : b->cases) {
-        if (int rc = lattice_prepare_step(*L)) return rc;
-        if (L->cur != parity)
-            return fail(MCLBM_ERR_STATE, "the cases of a batch were stepped separately "
-                                         "and are at different buffer parities");
+        if (int rc = check_ready(*L)) return rc;
+        if (int rc = refresh_ghosts(*L)) return rc;
     }
     int64_t left = nsteps;
-    if (b->shape < 0) {
+    if (b->cand < 0) {
         int rc = MCLBM_OK;
         left -= autotune(*b, left, &rc);
         if (rc) return rc;
     }
+    if (int rc = ensure_layout(*b, b->cand)) return rc;
+    const int parity = parity_of(*b, b->cand);
+    for (auto *L : b->cases)
+        if ((fluid_cand(b->cand) ? L->scur : L->cur) != parity)
+            return fail(MCLBM_ERR_STATE, "the cases of a batch were stepped separately "
+                                         "and are at different buffer parities");
     if (left >= 2 * GRAPH_STEPS) {
-        if (!b->graph || b->graph_version != version_of(*b) || b->graph_parity != b->cases[0]->cur) {
-            if (b->cases[0]->cur != b->graph_parity && b->graph && b->graph_version == version_of(*b)) {
+        if (!b->graph || b->graph_version != version_of(*b) || b->graph_parity != parity) {
+            if (parity != b->graph_parity && b->graph && b->graph_version == version_of(*b)) {
                 // one direct step brings the parity back to the captured one
-                if (int rc = direct_step(*b, b->shape, b->grid)) return rc;
+                if (int rc = direct_step(*b, b->cand)) return rc;
                 --left;
             } else if (int rc = capture_graph(*b)) {
                 return rc;
@@ -242,7 +290,7 @@ int mclbm_batch_step(mclbm_batch *b, int64_t nsteps) {
         }
     }
     while (left-- > 0)
-        if (int rc = direct_step(*b, b->shape, b->grid)) return rc;
+        if (int rc = direct_step(*b, b->cand)) return rc;
     return MCLBM_OK;
 }
 
@@ -250,18 +298,19 @@ int mclbm_batch_info(mclbm_batch *b, int64_t out[8]) {
     if (!b || !out) return fail(MCLBM_ERR_ARG, "NULL argument");
     out[0] = (int64_t)b->cases.size();
     out[1] = b->total_nodes;
-    out[2] = b->shape;
-    out[3] = b->grid == 0 ? 0 : -1;
+    const int cand = b->cand < 0 ? 0 : b->cand;
+    out[2] = b->cand < 0 ? -1 : (fluid_cand(cand) ? 2 + shape_of_cand(cand) : shape_of_cand(cand));
+    out[3] = grid_of_cand(cand) == 0 ? 0 : -1;
     out[4] = GRAPH_STEPS;
     out[5] = b->steps;
-    out[6] = batch_slots(b->prec, b->shape < 0 ? 0 : b->shape);
+    out[6] = fluid_cand(cand) ? 0 : batch_slots(b->prec, shape_of_cand(cand));
     out[7] = b->graph ? 1 : 0;
     return MCLBM_OK;
 }
 
-int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[4]) {
+int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[6]) {
     if (!b || !ms_per_step) return fail(MCLBM_ERR_ARG, "NULL argument");
-    for (int k = 0; k < 4; ++k) ms_per_step[k] = b->tune_ms[k];
+    for (int k = 0; k < NCAND; ++k) ms_per_step[k] = b->tune_ms[k];
     return MCLBM_OK;
 }
 

@@ -139,8 +139,22 @@ int run_diagnostics(Lattice &L, double out[8]) {
     return MCLBM_OK;
 }
 
-// Rebuild the ghost columns if the x boundary mode changed since they were
-// last built.
+}  // namespace
+
+int fail(int code, const std::string &msg) {
+    g_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return MCLBM_ERR_CUDA;
+}
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Rebuild the ghost columns and tables if the boundary mode changed since
+// they were last built.
 int refresh_ghosts(Lattice &L) {
     if (L.ghost_mode == L.ghost_key()) return MCLBM_OK;
     cudaError_t e = launch_geo_ghosts(L);
@@ -158,20 +172,6 @@ int check_ready(Lattice &L) {
                     "rows 0 and ny-1 must be solid unless the lattice is periodic in y");
     return MCLBM_OK;
 }
-
-}  // namespace
-
-int fail(int code, const std::string &msg) {
-    g_error = msg;
-    return code;
-}
-
-int cuda_fail(cudaError_t e, const char *what) {
-    g_error = std::string(what) + ": " + cudaGetErrorString(e);
-    return MCLBM_ERR_CUDA;
-}
-
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // the dense buffers current, with their ghost copies
 int dense_current(Lattice &L) {

@@ -224,6 +224,9 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void count_launch(int n = 1);
 int lattice_prepare_step(Lattice &L);  // checks and ghost refresh before stepping (capi.cu)
+int check_ready(Lattice &L);           // initialised, walls where y is not periodic
+int refresh_ghosts(Lattice &L);        // ghosts and tables for the current boundary mode
+int dense_current(Lattice &L);         // the dense buffers current, with their ghost copies
 
 // launchers (step.cu, sweep.cu, fields.cu); return cudaError_t of the launch
 cudaError_t launch_step_tile(Lattice &L, int tile_cfg);
@@ -237,6 +240,8 @@ int tma_build_tables(Lattice &L); // work tables for the current boundary mode (
 bool sparse_precision(mclbm_precision p);
 int sparse_prepare(Lattice &L, int tile_height);  // layout and tables (tile 32 x 12 or 32 x 8)
 cudaError_t launch_step_sparse(Lattice &L);
+// one launch over several lattices (fluid-only state current, same tile height)
+cudaError_t launch_step_sparse_batch(Lattice *const *cases, int n, int grid, cudaStream_t stream);
 int sparse_to_dense(Lattice &L);      // make the dense buffers current (no-op if they are)
 int dense_to_sparse(Lattice &L);      // make the fluid-only buffers current
 void sparse_release(Lattice &L);

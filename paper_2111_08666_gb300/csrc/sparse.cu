@@ -99,22 +99,25 @@ int staged_capacity(mclbm_precision p, int sty) {
     return p == MCLBM_FP32 ? SLayout<P32, 12>::SCAP : SLayout<P16D, 12>::SCAP;
 }
 
+// The lattices of a launch (1, or up to MAX_BATCH for a batch).
+template <int N>
 struct SArgs {
-    StepArgs a;
-    const void *fin;  // [nfp][planes]
-    void *fout;
-    long long nfp;
-    const uint32_t *tab;   // [ntiles][tab_words]
-    const uint32_t *rec;   // [ntiles][REC_WORDS]
-    int tab_words, tiles_x, ntiles;
-    // shared-memory layout, sized by the lattice's largest tile
+    StepArgs a[N];
+    const void *fin[N];  // [nfp][planes]
+    void *fout[N];
+    const uint32_t *tab[N];   // [tiles][tab_words]
+    const uint32_t *rec[N];   // [tiles][REC_WORDS]
+    int tab_words[N], tiles_x[N];
+    int first[N + 1];         // first work item of each lattice
+    int ncases, total, tab_stride;
+    // shared-memory layout, sized by the largest tile of the launch
     uint32_t out_off, rho_off, tab_off, rec_off, bar_off;
 };
 
 // offsets of the shared-memory regions for staged slots scap, own slots
 // ocap and table words tabw; returns the total bytes
-template <class P, int STY>
-size_t smem_layout(int scap, int ocap, int tabw, SArgs &s) {
+template <class P, int STY, int N>
+size_t smem_layout(int scap, int ocap, int tabw, SArgs<N> &s) {
     constexpr int SFH = STY + 6, SN1 = SDXW * (STY + 4);
     using S = typename P::store_t;
     using R = typename P::real_t;
@@ -134,8 +137,8 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-template <class P, int STY>
-__global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs s) {
+template <class P, int STY, int N>
+__global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs<N> s) {
     using L = SLayout<P, STY>;
     constexpr int SFH = L::SFH, SN1 = L::SN1;
     using S = typename P::store_t;
@@ -152,15 +155,21 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
     uint32_t *rec = reinterpret_cast<uint32_t *>(smem + s.rec_off);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + s.bar_off);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const StepArgs &a = s.a;
-    const Geometry &g = a.g;
-    const S *fin = static_cast<const S *>(s.fin);
-    S *fout = static_cast<S *>(s.fout);
+    auto case_of = [&](int w) -> int {
+        if constexpr (N == 1) {
+            return 0;
+        } else {
+            int c = 0;
+            while (c + 1 < s.ncases && w >= s.first[c + 1]) ++c;
+            return c;
+        }
+    };
 
     // copy warp: start the copy of tile w's record into shared memory
     auto fetch_record = [&](int w) {
+        const int c = case_of(w);
         if (lane < REC_WORDS / 4) {
-            const uint32_t *src = s.rec + (size_t)w * REC_WORDS + 4 * lane;
+            const uint32_t *src = s.rec[c] + (size_t)(w - s.first[c]) * REC_WORDS + 4 * lane;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + 4 * lane)), "l"(src)
                          : "memory");
         }
@@ -168,14 +177,17 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
     };
     // copy warp: stage tile w (record already in shared memory) into table buffer tb
     auto issue = [&](int w, int tb) {
+        const int c = case_of(w);
+        const S *fin = static_cast<const S *>(s.fin[c]);
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
         const int nr = (int)rec[0];
-        const uint32_t tbytes = 4u * (uint32_t)s.tab_words;
+        const uint32_t tbytes = 4u * (uint32_t)s.tab_words[c];
         fence_proxy_async();
         if (lane == 0) {
             mbar_expect_tx(bar, rec[1] + tbytes);
-            bulk_g2s(tabs + tb * s.tab_words, s.tab + (size_t)w * s.tab_words, tbytes, bar);
+            bulk_g2s(tabs + tb * s.tab_stride, s.tab[c] + (size_t)(w - s.first[c]) * s.tab_words[c], tbytes,
+                     bar);
         }
         __syncwarp();
         for (int r = lane; r < nr; r += 32) {
@@ -191,17 +203,22 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
         fence_mbar_init();
     }
     __syncthreads();
-    if ((int)blockIdx.x >= s.ntiles) return;
+    if ((int)blockIdx.x >= s.total) return;
     if (warp == DW) {
         fetch_record(blockIdx.x);
         issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + (int)gridDim.x < s.ntiles) fetch_record(blockIdx.x + gridDim.x);
+        if ((int)blockIdx.x + (int)gridDim.x < s.total) fetch_record(blockIdx.x + gridDim.x);
     }
 
     uint32_t parity = 0;
     int tb = 0;
-    for (int w = blockIdx.x; w < s.ntiles; w += gridDim.x) {
-        const int x0 = (w % s.tiles_x) * STX, y0 = (w / s.tiles_x) * STY;
+    for (int w = blockIdx.x; w < s.total; w += gridDim.x) {
+        const int c = case_of(w);
+        const int t = w - s.first[c];
+        const StepArgs &a = s.a[c];
+        const Geometry &g = a.g;
+        S *fout = static_cast<S *>(s.fout[c]);
+        const int x0 = (t % s.tiles_x[c]) * STX, y0 = (t / s.tiles_x[c]) * STY;
         const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
         if (__syncthreads_or(bad)) {
             if (tid == 0) {
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             if (warp == DW) bulk_wait_read();
             return;
         }
-        const uint32_t *T = tabs + tb * s.tab_words;
+        const uint32_t *T = tabs + tb * s.tab_stride;
         const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
         const uint32_t *E = T + HDR;
         // staged element offset (slot x planes) of every frame position (0
@@ -285,9 +302,9 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
         if (warp == DW) {
             bulk_wait_read();
             if (!dw_busy) asm volatile("bar.arrive 1, %0;" ::"n"(NT) : "memory");
-            if (wn < s.ntiles) {
+            if (wn < s.total) {
                 issue(wn, tb ^ 1);
-                if (wn + (int)gridDim.x < s.ntiles) fetch_record(wn + gridDim.x);
+                if (wn + (int)gridDim.x < s.total) fetch_record(wn + gridDim.x);
             }
         }
 
@@ -711,61 +728,88 @@ int sparse_to_dense(Lattice &L) {
 }
 
 namespace {
-template <class P, int STY>
-cudaError_t launch_sparse(Lattice &L) {
-    {
-        using Lay = SLayout<P, STY>;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(sparse_kernel<P, STY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)Lay::total);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        SArgs s{};
-        const size_t bytes = smem_layout<P, STY>(L.sscap, L.socap, L.stab_words, s);
-        if (bytes > Lay::total) return cudaErrorInvalidValue;
-        // resident CTAs per SM for this size (cached per size)
-        static size_t last_bytes = 0;
-        static int slots = 0;
-        if (bytes != last_bytes) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY>, STX * STY, bytes);
-            slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
-            last_bytes = bytes;
-        }
-        s.a.g = L.geometry();
-        s.a.p = L.p;
-        s.a.p.round_fp32();
-        s.a.d5 = L.d5;
-        s.a.err = L.err;
-        s.fin = L.fs[L.scur];
-        s.fout = L.fs[1 - L.scur];
-        s.nfp = L.nfp;
-        s.tab = L.stab;
-        s.rec = L.scopy;
-        s.tab_words = L.stab_words;
-        s.tiles_x = (L.nx + STX - 1) / STX;
-        s.ntiles = s.tiles_x * ((L.ny + STY - 1) / STY);
-        const int grid = slots < s.ntiles ? slots : s.ntiles;
-        sparse_kernel<P, STY><<<grid, STX * STY, bytes, L.stream>>>(s);
-        count_launch();
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) {
-            L.scur = 1 - L.scur;
-            L.sparse_state = 1;
-        }
-        return e;
+// one launch advancing lattices cases[0..n) by one step (all share the
+// precision, the tile height and have their fluid-only state current)
+template <class P, int STY, int N>
+cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t stream, int *slots_out) {
+    using Lay = SLayout<P, STY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(sparse_kernel<P, STY, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Lay::total);
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
+    static SArgs<N> s;  // host staging of the parameter block
+    std::memset(&s, 0, sizeof(s));
+    int scap = 16, ocap = 2, tabw = 4, total = 0;
+    for (int c = 0; c < n; ++c) {
+        Lattice &L = *cases[c];
+        if (L.nfp <= 0 || L.sparse_ty != STY || L.sparse_state == 0) return cudaErrorInvalidValue;
+        scap = std::max(scap, L.sscap);
+        ocap = std::max(ocap, L.socap);
+        tabw = std::max(tabw, L.stab_words);
+        s.a[c].g = L.geometry();
+        s.a[c].p = L.p;
+        s.a[c].p.round_fp32();
+        s.a[c].d5 = L.d5;
+        s.a[c].err = L.err;
+        s.fin[c] = L.fs[L.scur];
+        s.fout[c] = L.fs[1 - L.scur];
+        s.tab[c] = L.stab;
+        s.rec[c] = L.scopy;
+        s.tab_words[c] = L.stab_words;
+        s.tiles_x[c] = (L.nx + STX - 1) / STX;
+        s.first[c] = total;
+        total += s.tiles_x[c] * ((L.ny + STY - 1) / STY);
+    }
+    s.first[n] = total;
+    s.ncases = n;
+    s.total = total;
+    s.tab_stride = tabw;
+    const size_t bytes = smem_layout<P, STY, N>(scap, ocap, tabw, s);
+    if (bytes > Lay::total) return cudaErrorInvalidValue;
+    // resident CTAs per SM for this size (cached per size)
+    static size_t last_bytes = 0;
+    static int slots = 0;
+    if (bytes != last_bytes) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY, N>, STX * STY, bytes);
+        slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
+        last_bytes = bytes;
+    }
+    if (slots_out) *slots_out = slots;
+    const int g = grid > 0 ? std::min(grid, total) : std::min(slots, total);
+    sparse_kernel<P, STY, N><<<g, STX * STY, bytes, stream>>>(s);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        for (int c = 0; c < n; ++c) {
+            cases[c]->scur = 1 - cases[c]->scur;
+            cases[c]->sparse_state = 1;
+        }
+    return e;
 }
 }  // namespace
 
 cudaError_t launch_step_sparse(Lattice &L) {
+    Lattice *one = &L;
     return dispatch_prec(L.prec, [&](auto tag) {
         using P = decltype(tag);
-        return L.sparse_ty == 8 ? launch_sparse<P, 8>(L) : launch_sparse<P, 12>(L);
+        return L.sparse_ty == 8 ? launch_sparse<P, 8, 1>(&one, 1, 0, L.stream, nullptr)
+                                : launch_sparse<P, 12, 1>(&one, 1, 0, L.stream, nullptr);
+    });
+}
+
+cudaError_t launch_step_sparse_batch(Lattice *const *cases, int n, int grid, cudaStream_t stream) {
+    if (n < 1 || n > MAX_BATCH) return cudaErrorInvalidValue;
+    const int ty = cases[0]->sparse_ty;
+    return dispatch_prec(cases[0]->prec, [&](auto tag) {
+        using P = decltype(tag);
+        return ty == 8 ? launch_sparse<P, 8, MAX_BATCH>(cases, n, grid, stream, nullptr)
+                       : launch_sparse<P, 12, MAX_BATCH>(cases, n, grid, stream, nullptr);
     });
 }
 

@@ -351,7 +351,7 @@ def mclbm_batch_info(b) -> dict:
 
 
 def mclbm_batch_tuning(b) -> list[float]:
-    out = np.zeros(4)
+    out = np.zeros(6)
     _check(load().mclbm_batch_tuning(b, out.ctypes.data))
     return out.tolist()
 

@@ -1,6 +1,9 @@
-"""Batched persistent stepping: every case of a batch computes exactly what
-the same lattice computes alone, whatever tile shape and grid the tuner
-picks and across graph replays."""
+"""Batched persistent stepping: every case of a batch computes what the same
+lattice computes alone, whatever kernel, tile shape and grid the tuner
+picks and across graph replays.  The tuner's candidates include the tile
+kernel and the fluid-only kernel, which differ in how the compiler fuses
+FP32 multiply-adds, so the comparison is to rounding (the bounds of the
+kernel-agreement test)."""
 import numpy as np
 import pytest
 
@@ -37,7 +40,7 @@ def test_batch_matches_single_lattices(prec):
         mclbm.mclbm_batch_step(b, steps)
         info = mclbm.mclbm_batch_info(b)
         assert info["steps"] == steps and info["cases"] == 4 and info["graph"] == 1
-        assert info["shape"] in (0, 1)
+        assert info["shape"] in (0, 1, 2, 3)
         for k, c in enumerate(cases):
             ny, nx = c["solid"].shape
             view = mclbm.LatticeView(b, k, ny, nx, p)
@@ -46,9 +49,10 @@ def test_batch_matches_single_lattices(prec):
             alone.init(c["rho1"], c["rho2"])
             alone.step(steps)
             fa, fb = alone.populations(), view.populations()
-            assert np.array_equal(fa, fb), (k, np.max(np.abs(fa - fb)))
+            tol = {"fp32": 4e-6, "fp16dev": 1e-3}[prec]
+            assert np.max(np.abs(fa - fb)) <= tol * np.max(np.abs(fa)), (k, np.max(np.abs(fa - fb)))
             da, db = alone.diagnostics(), view.diagnostics()
-            assert da["mass1"] == db["mass1"]
+            assert da["mass1"] == pytest.approx(db["mass1"], rel=tol)
         # a parameter change through a view is picked up (graph re-captured)
         view0 = mclbm.LatticeView(b, 0, *cases[0]["solid"].shape, p)
         view0.set_pressure_bc(1.02, 1.0)
