@@ -12,14 +12,16 @@
 // Loss: mean over the masked (fluid) pixels of (phi_hat - phi)^2; Adam.
 //
 // The three passes of every 3x3 convolution are implicit GEMMs on the
-// tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32):
+// tensor cores, BF16 x BF16 -> FP32:
 //   forward  C[pixel][co] = sum_(tap,ci) X[pixel + d_tap][ci] W[co][tap][ci]
 //   dgrad    C[pixel][ci] = sum_(tap,co) dZ[pixel - d_tap][co] W[co][tap][ci]
 //   wgrad    C[co][ci]    = sum_pixel dZ[pixel][co] X[pixel + d_tap][ci]  (per tap)
 // with operands gathered into shared memory by cp.async (zero fill at the
 // image border; the decoder's concat and upsampling are folded into the
-// gather) and fragments read with ldmatrix.  Pooling, the head, the loss and
-// Adam are elementwise kernels.
+// gather).  Forward and dgrad run on tcgen05 (accumulator in tensor
+// memory); wgrad, a reduction over all pixels split across CTAs, on
+// mma.sync m16n8k16 with ldmatrix.trans fragments.  Pooling, the head, the
+// loss and Adam are elementwise kernels.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -52,11 +54,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
-__device__ __forceinline__ void ldsm4(uint32_t r[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
-}
 __device__ __forceinline__ void ldsm4t(uint32_t r[4], const void *p) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -71,11 +68,6 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// 64-byte shared rows (32 BF16) of 4 16-byte chunks, XOR-swizzled so that
-// the 8 rows an ldmatrix reads fall in distinct banks
-__device__ __forceinline__ int sw64(int row, int chunk) {
-    return row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4);
-}
 // 128-byte shared rows (64 BF16) of 8 chunks
 __device__ __forceinline__ int sw128(int row, int chunk) { return row * 128 + ((chunk ^ (row & 7)) << 4); }
 
@@ -93,131 +85,206 @@ struct ConvArgs {
     const float *bias;    // [N] or null
     bf16 *ybf;            // ReLU(C + bias) as BF16 [M][N], or null
     float *yf;            // C as FP32 [M][N], or null
+    int *err;             // set when a bounded wait gives up
 };
 
-constexpr int CBM = 128, CBK = 32;
+// ---------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores: a CTA of four
+// warps owns 128 pixels x BN channels.  Per k-chunk of 32 (one tap, 32
+// channels) every thread gathers one pixel row of A and (part of) the B rows
+// with cp.async into shared memory in the K-major core-matrix layout (8 rows
+// x 16 bytes per core matrix, no swizzle); one thread issues two
+// tcgen05.mma (M = 128, N = BN, K = 16, BF16 x BF16 -> FP32) into a tensor-
+// memory accumulator and commits them to the stage's mbarrier, so the next
+// chunk's gather overlaps the MMAs (two stages).  The four warps then read
+// their 32 accumulator lanes (pixels) with tcgen05.ld for the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int TBM = 128, TBK = 32;
+
+// shared-memory matrix descriptor: K-major, no swizzle; lbo = byte offset
+// between core matrices adjacent in K, sbo = between 8-row groups
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | (uint64_t)((lbo >> 4) & 0x3fffu) << 16 |
+           (uint64_t)((sbo >> 4) & 0x3fffu) << 32 | (uint64_t)1 << 46;
+}
+
+// instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
+__host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
 
 template <int BN>
-__global__ void __launch_bounds__(256) conv_kernel(const ConvArgs a) {
-    constexpr int WN = BN / 32;       // warps along n (warp tile n = 32)
-    constexpr int WMW = 8 / WN;       // warps along m
-    constexpr int WTM = CBM / WMW;    // warp tile m
-    constexpr int MT = WTM / 16;
-    __shared__ __align__(128) unsigned char sA[2][CBM * 64];
-    __shared__ __align__(128) unsigned char sB[2][BN * 64];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp % WMW, wn = warp / WMW;
-    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+__global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
+    constexpr int A_BYTES = TBM * TBK * 2, B_BYTES = BN * TBK * 2;
+    constexpr int STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;  // TMEM columns
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * BN;
     const int K0 = a.c0 + a.c1;
-    const int kchunks = K0 / CBK;
+    const int kchunks = K0 / TBK;
     const int ksteps = 9 * kchunks;
 
-    // rows of A this thread copies: tid/4 and tid/4 + 64, chunk tid % 4
-    int ab[2], ay[2], ax[2];
-    bool am[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int m = m0 + (tid >> 2) + j * 64;
-        am[j] = m < a.M;
-        const int mm = am[j] ? m : 0;
-        ax[j] = mm % a.W;
-        const int t = mm / a.W;
-        ay[j] = t % a.H;
-        ab[j] = t / a.H;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    const int ach = tid & 3;
-    const int brow = tid >> 2, bch = tid & 3;
-    const bool bload = brow < BN;
-    const bool bvalid = bload && n0 + brow < a.N;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
 
-    auto load = [&](int ks, int buf) {
+    // this thread's pixel (A row tid)
+    const int m = m0 + tid;
+    const bool am = m < a.M;
+    const int mm = am ? m : 0;
+    const int ax = mm % a.W, ay = (mm / a.W) % a.H, ab = mm / (a.W * a.H);
+    auto off = [](int row, int q) { return ((row >> 3) * (TBK / 8) + q) * 128 + (row & 7) * 16; };
+
+    auto load = [&](int ks, int st) {
+        unsigned char *As = smem + st * STAGE, *Bs = As + A_BYTES;
         const int tap = ks / kchunks, kc = ks - tap * kchunks;
         const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-        const int ci = kc * CBK + ach * 8;
+        const int yy = ay + dy, xx = ax + dx;
+        const bool v = am && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int yy = ay[j] + dy, xx = ax[j] + dx;
-            const bool v = am[j] && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        for (int q = 0; q < TBK / 8; ++q) {
+            const int ci = kc * TBK + q * 8;
             const bf16 *src = a.x0;
             if (v) {
                 if (ci < a.c0)
-                    src = a.x0 + ((size_t)(ab[j] * a.H + yy) * a.W + xx) * a.c0 + ci;
+                    src = a.x0 + ((size_t)(ab * a.H + yy) * a.W + xx) * a.c0 + ci;
                 else
-                    src = a.x1 + ((size_t)(ab[j] * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
-                          (ci - a.c0);
+                    src = a.x1 + ((size_t)(ab * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 + (ci - a.c0);
             }
-            cp_async16(sA[buf] + sw64((tid >> 2) + j * 64, ach), src, v);
+            cp_async16(As + off(tid, q), src, v);
         }
-        if (bload) {
-            const bf16 *src = bvalid ? a.w + ((size_t)(n0 + brow) * 9 + tap) * K0 + kc * CBK + bch * 8 : a.w;
-            cp_async16(sB[buf] + sw64(brow, bch), src, bvalid);
+#pragma unroll
+        for (int rr = 0; rr < (BN + 127) / 128; ++rr) {
+            const int n = tid + rr * 128;
+            if (n < BN) {
+                const bool vb = n0 + n < a.N;
+#pragma unroll
+                for (int q = 0; q < TBK / 8; ++q) {
+                    const bf16 *src = vb ? a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + kc * TBK + q * 8 : a.w;
+                    cp_async16(Bs + off(n, q), src, vb);
+                }
+            }
         }
         cp_async_commit();
     };
 
-    float acc[MT][4][4];
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
-
-    load(0, 0);
-    for (int ks = 0; ks < ksteps; ++ks) {
-        const int buf = ks & 1;
-        if (ks + 1 < ksteps) {
-            load(ks + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-            uint32_t af[MT][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-                ldsm4(af[mt], sA[buf] + sw64(wm * WTM + mt * 16 + (lane & 15), kk * 2 + (lane >> 4)));
-#pragma unroll
-            for (int np = 0; np < 2; ++np) {
-                uint32_t r[4];
-                ldsm4(r, sB[buf] + sw64(wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3),
-                                        kk * 2 + ((lane >> 3) & 1)));
-                bfr[2 * np][0] = r[0];
-                bfr[2 * np][1] = r[1];
-                bfr[2 * np + 1][0] = r[2];
-                bfr[2 * np + 1][1] = r[3];
+    bool bad = false;
+    for (int ks = 0; ks < ksteps && !bad; ++ks) {
+        const int st = ks & 1;
+        if (ks >= 2) {
+            // the MMAs of chunk ks - 2 have read stage st
+            const bool ok = mbar_wait(&bar[st], ((ks - 2) >> 1) & 1, WAIT_LIMIT_NS);
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
             }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt][0], bfr[nt][1]);
+            tc_fence_after();
         }
+        load(ks, st);
+        cp_async_wait<0>();
+        fence_proxy_async();  // the gathered tiles, for the tensor cores' (async) reads
+        tc_fence_before();
         __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t As = smem_u32(smem + st * STAGE), Bs = As + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < TBK / 16; ++j) {
+                const uint64_t ad = umma_desc(As + j * 256, 128, (TBK / 8) * 128);
+                const uint64_t bd = umma_desc(Bs + j * 256, 128, (TBK / 8) * 128);
+                const uint32_t acc = (ks > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(umma_idesc(TBM, BN)), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[st]))
+                         : "memory");
+        }
     }
-
-    const int g = lane >> 2, t4 = lane & 3;
+    if (!bad && ksteps > 0) {
+        const int last = ksteps - 1;
+        const bool ok = mbar_wait(&bar[last & 1], (last >> 1) & 1, WAIT_LIMIT_NS);
+        bad = __syncthreads_or(!ok);
+    }
+    tc_fence_after();
+    if (bad) {
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+        // give in-flight MMAs a last, short chance before the memory is freed
+        mbar_wait(&bar[0], 0, DRAIN_LIMIT_NS);
+    } else {
+        // epilogue: warp w reads accumulator lanes 32w..32w+31 (its pixels)
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int n = n0 + c;
+            if (row < a.M && n < a.N) {
+            float v[16];
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
+            for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+            if (a.yf) {
+                float4 *d = reinterpret_cast<float4 *>(a.yf + (size_t)row * a.N + n);
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm * WTM + mt * 16 + g + h * 8;
-                const int n = n0 + wn * 32 + nt * 8 + 2 * t4;
-                if (m >= a.M || n >= a.N) continue;
-                float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-                if (a.yf) *reinterpret_cast<float2 *>(a.yf + (size_t)m * a.N + n) = make_float2(v0, v1);
-                if (a.ybf) {
-                    if (a.bias) {
-                        v0 += a.bias[n];
-                        v1 += a.bias[n + 1];
-                    }
-                    *reinterpret_cast<__nv_bfloat162 *>(a.ybf + (size_t)m * a.N + n) =
-                        __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
-                }
+                for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
             }
+            if (a.ybf) {
+                __nv_bfloat162 h[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float v0 = v[2 * k], v1 = v[2 * k + 1];
+                    if (a.bias) {
+                        v0 += a.bias[n + 2 * k];
+                        v1 += a.bias[n + 2 * k + 1];
+                    }
+                    h[k] = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                }
+                uint4 *d = reinterpret_cast<uint4 *>(a.ybf + (size_t)row * a.N + n);
+                d[0] = *reinterpret_cast<const uint4 *>(&h[0]);
+                d[1] = *reinterpret_cast<const uint4 *>(&h[4]);
+            }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -565,6 +632,7 @@ struct mclbm_unet {
     bf16 *z = nullptr;
     float *xin_f = nullptr, *t_f = nullptr, *mask_f = nullptr;  // staging of host inputs
     double *loss_part = nullptr, *loss_stat = nullptr;
+    int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
     std::vector<void *> allocs;
     int cur_b = 0, cur_h = 0, cur_w = 0;
 };
@@ -590,14 +658,35 @@ void unet_release(mclbm_unet *u) {
     delete u;
 }
 
-cudaError_t launch_conv(const mclbm_unet &u, const ConvArgs &a) {
-    const dim3 grid((a.M + CBM - 1) / CBM, a.N % 64 == 0 ? a.N / 64 : (a.N + 31) / 32);
-    if (a.N % 64 == 0)
-        conv_kernel<64><<<grid, 256, 0, u.stream>>>(a);
-    else
-        conv_kernel<32><<<grid, 256, 0, u.stream>>>(a);
+template <int BN>
+cudaError_t launch_tc(const mclbm_unet &u, ConvArgs a) {
+    constexpr int bytes = 2 * (TBM * TBK * 2 + BN * TBK * 2) + 32;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid((a.M + TBM - 1) / TBM, (a.N + BN - 1) / BN);
+    conv_tc_kernel<BN><<<grid, 128, bytes, u.stream>>>(a);
     count_launch();
     return cudaGetLastError();
+}
+
+// forward and data-gradient convolutions on the tensor cores (N tile = N
+// up to 256, else 128)
+cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
+    a.err = u.err;
+    if (a.c0 % TBK || (a.c0 + a.c1) % TBK || a.N % 16) return cudaErrorInvalidValue;
+    switch (a.N) {
+        case 32: return launch_tc<32>(u, a);
+        case 64: return launch_tc<64>(u, a);
+        case 96: return launch_tc<96>(u, a);
+        case 128: return launch_tc<128>(u, a);
+        case 192: return launch_tc<192>(u, a);
+        case 256: return launch_tc<256>(u, a);
+        default: return a.N % 128 == 0 ? launch_tc<128>(u, a) : cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_wgrad(const mclbm_unet &u, WgradArgs a) {
@@ -846,11 +935,24 @@ int run_forward(mclbm_unet *u, int B, int H, int W, const float *x, const float 
     return MCLBM_OK;
 }
 
+// after a synchronisation: report (and clear) a wait that gave up
+int check_err(mclbm_unet *u) {
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, u->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "unet error word");
+    if (err) {
+        cudaMemset(u->err, 0, sizeof(int));
+        return fail(MCLBM_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    }
+    return MCLBM_OK;
+}
+
 int read_loss(mclbm_unet *u, double *loss) {
     double st[2] = {0, 0};
     cudaError_t e = cudaMemcpyAsync(st, u->loss_stat, sizeof(st), cudaMemcpyDeviceToHost, u->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
     if (e != cudaSuccess) return cuda_fail(e, "unet loss read-back");
+    if (int rc = check_err(u)) return rc;
     if (loss) *loss = st[1];
     return MCLBM_OK;
 }
@@ -952,10 +1054,12 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     A((void **)&u->mask_f, (size_t)P * 4);
     A((void **)&u->loss_part, LOSS_BLOCKS * 2 * sizeof(double));
     A((void **)&u->loss_stat, 2 * sizeof(double));
+    A((void **)&u->err, sizeof(int));
     if (rc == MCLBM_OK) {
         cudaError_t e = cudaMemsetAsync(u->theta, 0, u->nparam * 4, u->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(u->v, 0, u->nparam * 4, u->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(u->err, 0, sizeof(int), u->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "unet initialisation");
     }
@@ -1005,7 +1109,7 @@ int mclbm_unet_infer(mclbm_unet *u, int batch, int h, int w, const float *x, flo
     cudaError_t e = stage_out(*u, phi, u->phi, (size_t)batch * h * w);
     if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
     if (e != cudaSuccess) return cuda_fail(e, "unet output");
-    return MCLBM_OK;
+    return check_err(u);
 }
 
 int mclbm_unet_gradient(mclbm_unet *u, int batch, int h, int w, const float *x, const float *target,
