@@ -120,12 +120,41 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// epilogue of one pixel row and 16 accumulator columns n..n+15: FP32 C, or
+// BF16 ReLU(C + bias)
+__device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n, const uint32_t r[16]) {
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+    if (a.yf) {
+        float4 *d = reinterpret_cast<float4 *>(a.yf + row * a.N + n);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    if (a.ybf) {
+        __nv_bfloat162 h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v0 = v[2 * k], v1 = v[2 * k + 1];
+            if (a.bias) {
+                v0 += a.bias[n + 2 * k];
+                v1 += a.bias[n + 2 * k + 1];
+            }
+            h[k] = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(a.ybf + row * a.N + n);
+        d[0] = *reinterpret_cast<const uint4 *>(&h[0]);
+        d[1] = *reinterpret_cast<const uint4 *>(&h[4]);
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
     constexpr int A_BYTES = TBM * TBK * 2, B_BYTES = BN * TBK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;  // TMEM columns
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+    static_assert(TBK == 32, "four 16-byte pieces per row and chunk");
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);  // [2]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
@@ -151,42 +180,47 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    // this thread's pixel (A row tid)
-    const int m = m0 + tid;
-    const bool am = m < a.M;
-    const int mm = am ? m : 0;
-    const int ax = mm % a.W, ay = (mm / a.W) % a.H, ab = mm / (a.W * a.H);
-    auto off = [](int row, int q) { return ((row >> 3) * (TBK / 8) + q) * 128 + (row & 7) * 16; };
+    // A rows (pixels) this thread gathers: rows (tid >> 2) + 32 i, 16-byte
+    // piece q = tid & 3 of each chunk, so that four neighbouring threads read
+    // one pixel's 64 contiguous bytes
+    const int q = tid & 3;
+    int ax[4], ay[4], ab[4];
+    bool am[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + (tid >> 2) + 32 * i;
+        am[i] = m < a.M;
+        const int mm = am[i] ? m : 0;
+        ax[i] = mm % a.W;
+        ay[i] = (mm / a.W) % a.H;
+        ab[i] = mm / (a.W * a.H);
+    }
+    auto off = [](int row, int qq) { return ((row >> 3) * (TBK / 8) + qq) * 128 + (row & 7) * 16; };
 
     auto load = [&](int ks, int st) {
         unsigned char *As = smem + st * STAGE, *Bs = As + A_BYTES;
         const int tap = ks / kchunks, kc = ks - tap * kchunks;
         const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-        const int yy = ay + dy, xx = ax + dx;
-        const bool v = am && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const int ci = kc * TBK + q * 8;
 #pragma unroll
-        for (int q = 0; q < TBK / 8; ++q) {
-            const int ci = kc * TBK + q * 8;
+        for (int i = 0; i < 4; ++i) {
+            const int yy = ay[i] + dy, xx = ax[i] + dx;
+            const bool v = am[i] && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
             const bf16 *src = a.x0;
             if (v) {
                 if (ci < a.c0)
-                    src = a.x0 + ((size_t)(ab * a.H + yy) * a.W + xx) * a.c0 + ci;
+                    src = a.x0 + ((size_t)(ab[i] * a.H + yy) * a.W + xx) * a.c0 + ci;
                 else
-                    src = a.x1 + ((size_t)(ab * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 + (ci - a.c0);
+                    src = a.x1 + ((size_t)(ab[i] * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
+                          (ci - a.c0);
             }
-            cp_async16(As + off(tid, q), src, v);
+            cp_async16(As + off((tid >> 2) + 32 * i, q), src, v);
         }
 #pragma unroll
-        for (int rr = 0; rr < (BN + 127) / 128; ++rr) {
-            const int n = tid + rr * 128;
-            if (n < BN) {
-                const bool vb = n0 + n < a.N;
-#pragma unroll
-                for (int q = 0; q < TBK / 8; ++q) {
-                    const bf16 *src = vb ? a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + kc * TBK + q * 8 : a.w;
-                    cp_async16(Bs + off(n, q), src, vb);
-                }
-            }
+        for (int n = tid >> 2; n < BN; n += 32) {
+            const bool vb = n0 + n < a.N;
+            const bf16 *src = vb ? a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + ci : a.w;
+            cp_async16(Bs + off(n, q), src, vb);
         }
         cp_async_commit();
     };
@@ -252,31 +286,173 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
                 : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int n = n0 + c;
-            if (row < a.M && n < a.N) {
-            float v[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-            if (a.yf) {
-                float4 *d = reinterpret_cast<float4 *>(a.yf + (size_t)row * a.N + n);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            if (row < a.M && n < a.N) store_row16(a, (size_t)row, n, r);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row-tile variant for images whose width is a multiple of 128: a CTA owns
+// 128 consecutive pixels of one image row.  Per chunk of 32 input channels it
+// stages the 3 x 130 halo of that row segment once (channel piece q of pixel
+// p of halo row r at plane q, offset (130 r + p) x 16 bytes) with the nine
+// taps' weights; the A operand of tap (dy, dx) is then the same halo read
+// through a descriptor whose start moves by dy rows and dx pixels (K-major,
+// no swizzle: K-adjacent core matrices one plane apart, 8-pixel groups 128
+// bytes apart).  Each input pixel crosses L2 -> shared memory about
+// 3 x 130 / 128 times instead of nine.  Two-stage ring over channel chunks.
+// ---------------------------------------------------------------------------
+constexpr int RW = 128, RHALO = RW + 2;
+constexpr int RPLANE = 3 * RHALO * 16;  // one 16-byte channel piece of the halo
+constexpr int RA_BYTES = 4 * RPLANE;
+
+template <int BN>
+__host__ __device__ constexpr int row_stage_bytes() {
+    return RA_BYTES + 9 * BN * 64;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
+    constexpr int STAGE = row_stage_bytes<BN>();
+    constexpr uint32_t COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128");
+    static_assert(STAGE % 16 == 0 && RPLANE % 16 == 0, "16-byte operand alignment");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int K0 = a.c0 + a.c1;
+    const int kchunks = K0 / 32;
+    const int ring = kchunks > 1 ? 2 : 1;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + ring * STAGE);  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = a.W / RW;
+    const int x0 = (blockIdx.x % segs) * RW;
+    const int y = (blockIdx.x / segs) % a.H;
+    const int b = blockIdx.x / (segs * a.H);
+    const int n0 = blockIdx.y * BN;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int q = tid & 3;  // 16-byte piece of a pixel's 32 channels
+    auto load = [&](int kc, int st) {
+        unsigned char *As = smem + st * STAGE, *Bs = As + RA_BYTES;
+        const int ci = kc * 32 + q * 8;
+        // halo: 3 rows x 130 pixels, pixel index (tid >> 2) + 32 i
+        for (int pix = tid >> 2; pix < 3 * RHALO; pix += 32) {
+            const int r = pix / RHALO, p = pix - r * RHALO;
+            const int yy = y + r - 1, xx = x0 + p - 1;
+            const bool v = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+            const bf16 *src = a.x0;
+            if (v) {
+                if (ci < a.c0)
+                    src = a.x0 + ((size_t)(b * a.H + yy) * a.W + xx) * a.c0 + ci;
+                else
+                    src = a.x1 + ((size_t)(b * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
+                          (ci - a.c0);
             }
-            if (a.ybf) {
-                __nv_bfloat162 h[8];
+            cp_async16(As + q * RPLANE + pix * 16, src, v);
+        }
+        // weights of the nine taps: row (n, tap) at tap * BN * 64 + core-matrix offset of n
+        for (int nt = tid >> 2; nt < 9 * BN; nt += 32) {
+            const int n = nt / 9, tap = nt - n * 9;
+            const bool vb = n0 + n < a.N;
+            const bf16 *src = vb ? a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + ci : a.w;
+            cp_async16(Bs + tap * BN * 64 + ((n >> 3) * 4 + q) * 128 + (n & 7) * 16, src, vb);
+        }
+    };
+
+    load(0, 0);
+    cp_async_commit();
+    if (kchunks > 1) load(1, 1);
+    cp_async_commit();
+    bool bad = false;
+    for (int kc = 0; kc < kchunks; ++kc) {
+        const int st = kc & 1;
+        cp_async_wait<1>();   // this thread's pieces of chunk kc have landed
+        fence_proxy_async();  // ... and are visible to the tensor cores' reads
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t As = smem_u32(smem + st * STAGE), Bs = As + RA_BYTES;
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
+                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 16;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    float v0 = v[2 * k], v1 = v[2 * k + 1];
-                    if (a.bias) {
-                        v0 += a.bias[n + 2 * k];
-                        v1 += a.bias[n + 2 * k + 1];
-                    }
-                    h[k] = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+                for (int j = 0; j < 2; ++j) {
+                    const uint64_t ad = umma_desc(a0 + 2 * j * RPLANE, RPLANE, 128);
+                    const uint64_t bd = umma_desc(Bs + tap * BN * 64 + j * 256, 128, 512);
+                    const uint32_t acc = (kc > 0 || tap > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(umma_idesc(RW, BN)), "r"(acc)
+                        : "memory");
                 }
-                uint4 *d = reinterpret_cast<uint4 *>(a.ybf + (size_t)row * a.N + n);
-                d[0] = *reinterpret_cast<const uint4 *>(&h[0]);
-                d[1] = *reinterpret_cast<const uint4 *>(&h[4]);
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[st]))
+                         : "memory");
+        }
+        if (kc + 2 < kchunks) {
+            // the MMAs of chunk kc have read stage st
+            const bool ok = mbar_wait(&bar[st], (kc >> 1) & 1, WAIT_LIMIT_NS);
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
             }
+            tc_fence_after();
+            load(kc + 2, st);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (!bad) {
+        const int last = kchunks - 1;
+        const bool ok = mbar_wait(&bar[last & 1], (last >> 1) & 1, WAIT_LIMIT_NS);
+        bad = __syncthreads_or(!ok);
+    }
+    tc_fence_after();
+    if (bad) {
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+        mbar_wait(&bar[0], 0, DRAIN_LIMIT_NS);
+    } else {
+        // epilogue: warp w reads accumulator lanes 32w..32w+31 (its pixels)
+        const size_t row = ((size_t)(b * a.H + y) * a.W + x0) + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int n = n0 + c;
+            if (n >= a.N) continue;
+            store_row16(a, row, n, r);
         }
     }
     tc_fence_before();
@@ -673,11 +849,37 @@ cudaError_t launch_tc(const mclbm_unet &u, ConvArgs a) {
     return cudaGetLastError();
 }
 
-// forward and data-gradient convolutions on the tensor cores (N tile = N
-// up to 256, else 128)
+template <int BN>
+cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
+    constexpr int max_bytes = 2 * row_stage_bytes<BN>() + 32;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_row_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ring = (a.c0 + a.c1) / 32 > 1 ? 2 : 1;
+    const dim3 grid(a.M / RW, a.N / BN);
+    conv_row_kernel<BN><<<grid, 128, ring * row_stage_bytes<BN>() + 32, u.stream>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// forward and data-gradient convolutions on the tensor cores: the row-tile
+// kernel where the width is a multiple of 128 and the N tile divides N,
+// else the pixel-gather kernel (N tile = N up to 256, else 128)
 cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
     a.err = u.err;
     if (a.c0 % TBK || (a.c0 + a.c1) % TBK || a.N % 16) return cudaErrorInvalidValue;
+    if (a.W % RW == 0) {
+        if (a.N == 32) return launch_row<32>(u, a);
+        if (a.N == 64) return launch_row<64>(u, a);
+        if (a.N % 128 == 0) return launch_row<128>(u, a);
+        if (a.N % 96 == 0) return launch_row<96>(u, a);
+        if (a.N % 64 == 0) return launch_row<64>(u, a);
+        if (a.N % 32 == 0) return launch_row<32>(u, a);
+    }
     switch (a.N) {
         case 32: return launch_tc<32>(u, a);
         case 64: return launch_tc<64>(u, a);

@@ -33,7 +33,9 @@ def _x8(x4):
     return x
 
 
-@pytest.mark.parametrize("levels,b,h,w", [(3, 2, 32, 48), (4, 1, 64, 32)])
+# widths below 128 take the pixel-gather kernel, multiples of 128 the
+# row-tile kernel (the last case: 512, 256 and 128 over its three levels)
+@pytest.mark.parametrize("levels,b,h,w", [(3, 2, 32, 48), (4, 1, 64, 32), (3, 1, 8, 512)])
 def test_forward_matches_reference(levels, b, h, w):
     base = 32
     theta, x4, _, _ = _problem(levels, base, b, h, w, seed=levels)
@@ -50,8 +52,9 @@ def test_forward_matches_reference(levels, b, h, w):
     net.close()
 
 
-def test_gradient_matches_reference():
-    levels, base, b, h, w = 3, 32, 2, 32, 32
+@pytest.mark.parametrize("b,h,w", [(2, 32, 32), (1, 8, 512)])
+def test_gradient_matches_reference(b, h, w):
+    levels, base = 3, 32
     theta, x4, target, mask = _problem(levels, base, b, h, w, seed=7)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
     net.set_params(theta)
