@@ -42,10 +42,13 @@ using bf16 = __nv_bfloat16;
 // ---------------------------------------------------------------------------
 // PTX helpers
 // ---------------------------------------------------------------------------
+// 16-byte copy global -> shared, or zeros when !valid (a plain shared store:
+// the zero-fill form of cp.async was seen to move twice the bytes from L2)
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
+    if (valid)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -298,43 +301,61 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Row-tile variant for images whose width is a multiple of 128: a CTA owns
-// 128 consecutive pixels of one image row.  Per chunk of 32 input channels it
-// stages the 3 x 130 halo of that row segment once (channel piece q of pixel
-// p of halo row r at plane q, offset (130 r + p) x 16 bytes) with the nine
-// taps' weights; the A operand of tap (dy, dx) is then the same halo read
-// through a descriptor whose start moves by dy rows and dx pixels (K-major,
-// no swizzle: K-adjacent core matrices one plane apart, 8-pixel groups 128
-// bytes apart).  Each input pixel crosses L2 -> shared memory about
-// 3 x 130 / 128 times instead of nine.  Two-stage ring over channel chunks.
+// Row-tile variant for images whose width is a multiple of 128, persistent
+// and pipelined.  A tile is 128 consecutive pixels of one image row.  Per
+// chunk of 32 input channels the tile needs the 3 x 130 halo of its row
+// segment (channel piece q of pixel p of halo row r at plane q, offset
+// (130 r + p) x 16 bytes) and the nine taps' weights; the A operand of tap
+// (dy, dx) is the same halo read through a descriptor whose start moves by dy
+// rows and dx pixels (K-major, no swizzle: K-adjacent core matrices one plane
+// apart, 8-pixel groups 128 bytes apart), so each input pixel crosses
+// L2 -> shared memory about 3 x 130 / 128 times instead of nine.
+//
+// A CTA owns one N tile and walks its tiles as a sequence of jobs (tile,
+// chunk) through a ring of S stages filled by cp.async S - 1 jobs ahead.
+// When all chunks' weights fit they are loaded once per CTA and the stages
+// carry halos only.  The accumulator is double-buffered in tensor memory:
+// the epilogue of tile i - 1 runs while the MMAs of tile i execute.
 // ---------------------------------------------------------------------------
 constexpr int RW = 128, RHALO = RW + 2;
 constexpr int RPLANE = 3 * RHALO * 16;  // one 16-byte channel piece of the halo
 constexpr int RA_BYTES = 4 * RPLANE;
 
-template <int BN>
-__host__ __device__ constexpr int row_stage_bytes() {
-    return RA_BYTES + 9 * BN * 64;
+struct RowPlan {
+    int wres;    // all chunks' weights resident (1) or streamed per job (0)
+    int stages;  // 2..4
+    int smem;    // dynamic shared memory bytes
+};
+
+__host__ __device__ inline int row_weight_bytes(int BN, int kchunks) { return 9 * BN * 64 * kchunks; }
+__host__ __device__ inline int row_stage_bytes(int BN, int wres) { return RA_BYTES + (wres ? 0 : 9 * BN * 64); }
+__host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int stages) {
+    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres) + 8 * 8;
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
-    constexpr int STAGE = row_stage_bytes<BN>();
-    constexpr uint32_t COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+__global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, const RowPlan plan) {
+    constexpr uint32_t COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;  // two accumulators
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128");
-    static_assert(STAGE % 16 == 0 && RPLANE % 16 == 0, "16-byte operand alignment");
     extern __shared__ __align__(1024) unsigned char smem[];
     const int K0 = a.c0 + a.c1;
     const int kchunks = K0 / 32;
-    const int ring = kchunks > 1 ? 2 : 1;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + ring * STAGE);  // [2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int S = plan.stages, wres = plan.wres;
+    const int WB = wres ? row_weight_bytes(BN, kchunks) : 0;
+    const int STG = row_stage_bytes(BN, wres);
+    unsigned char *wsm = smem;                 // resident weights [kc][tap][core-matrix layout]
+    unsigned char *stg = smem + WB;            // S stages: halo (+ weights when streamed)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + S * STG);  // [4] stage, [2] accumulator, [1] drain
+    uint64_t *accbar = bar + 4, *drain = bar + 6;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntn = a.N / BN;
+    const int nt = blockIdx.x % ntn, n0 = nt * BN;
+    const int tile0 = blockIdx.x / ntn, tstride = gridDim.x / ntn;
     const int segs = a.W / RW;
-    const int x0 = (blockIdx.x % segs) * RW;
-    const int y = (blockIdx.x / segs) % a.H;
-    const int b = blockIdx.x / (segs * a.H);
-    const int n0 = blockIdx.y * BN;
+    const int ntiles = a.M / RW;
+    const int my_tiles = tile0 < ntiles ? (ntiles - tile0 + tstride - 1) / tstride : 0;
+    const int njobs = my_tiles * kchunks;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -343,8 +364,7 @@ __global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < 7; ++k) mbar_init(&bar[k], 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -353,10 +373,22 @@ __global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
     const uint32_t tmem = *tslot;
 
     const int q = tid & 3;  // 16-byte piece of a pixel's 32 channels
-    auto load = [&](int kc, int st) {
-        unsigned char *As = smem + st * STAGE, *Bs = As + RA_BYTES;
+    // weights of chunk kc, nine taps: row (n, tap) at tap * BN * 64 + core-matrix offset of n
+    auto load_w = [&](int kc, unsigned char *Bs) {
         const int ci = kc * 32 + q * 8;
-        // halo: 3 rows x 130 pixels, pixel index (tid >> 2) + 32 i
+        for (int ntp = tid >> 2; ntp < 9 * BN; ntp += 32) {
+            const int n = ntp / 9, tap = ntp - n * 9;
+            const bf16 *src = a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + ci;
+            cp_async16(Bs + tap * BN * 64 + ((n >> 3) * 4 + q) * 128 + (n & 7) * 16, src, true);
+        }
+    };
+    auto tile_of = [&](int i) { return tile0 + i * tstride; };
+    auto load_job = [&](int j, int st) {
+        const int i = j / kchunks, kc = j - i * kchunks;
+        const int t = tile_of(i);
+        const int x0 = (t % segs) * RW, y = (t / segs) % a.H, b = t / (segs * a.H);
+        unsigned char *As = stg + st * STG;
+        const int ci = kc * 32 + q * 8;
         for (int pix = tid >> 2; pix < 3 * RHALO; pix += 32) {
             const int r = pix / RHALO, p = pix - r * RHALO;
             const int yy = y + r - 1, xx = x0 + p - 1;
@@ -371,74 +403,20 @@ __global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
             }
             cp_async16(As + q * RPLANE + pix * 16, src, v);
         }
-        // weights of the nine taps: row (n, tap) at tap * BN * 64 + core-matrix offset of n
-        for (int nt = tid >> 2; nt < 9 * BN; nt += 32) {
-            const int n = nt / 9, tap = nt - n * 9;
-            const bool vb = n0 + n < a.N;
-            const bf16 *src = vb ? a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + ci : a.w;
-            cp_async16(Bs + tap * BN * 64 + ((n >> 3) * 4 + q) * 128 + (n & 7) * 16, src, vb);
-        }
+        if (!wres) load_w(kc, As + RA_BYTES);
     };
-
-    load(0, 0);
-    cp_async_commit();
-    if (kchunks > 1) load(1, 1);
-    cp_async_commit();
-    bool bad = false;
-    for (int kc = 0; kc < kchunks; ++kc) {
-        const int st = kc & 1;
-        cp_async_wait<1>();   // this thread's pieces of chunk kc have landed
-        fence_proxy_async();  // ... and are visible to the tensor cores' reads
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t As = smem_u32(smem + st * STAGE), Bs = As + RA_BYTES;
-#pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 16;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const uint64_t ad = umma_desc(a0 + 2 * j * RPLANE, RPLANE, 128);
-                    const uint64_t bd = umma_desc(Bs + tap * BN * 64 + j * 256, 128, 512);
-                    const uint32_t acc = (kc > 0 || tap > 0 || j > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(umma_idesc(RW, BN)), "r"(acc)
-                        : "memory");
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar[st]))
-                         : "memory");
-        }
-        if (kc + 2 < kchunks) {
-            // the MMAs of chunk kc have read stage st
-            const bool ok = mbar_wait(&bar[st], (kc >> 1) & 1, WAIT_LIMIT_NS);
-            if (__syncthreads_or(!ok)) {
-                bad = true;
-                break;
-            }
-            tc_fence_after();
-            load(kc + 2, st);
-        }
-        cp_async_commit();
-    }
-    cp_async_wait<0>();
-    if (!bad) {
-        const int last = kchunks - 1;
-        const bool ok = mbar_wait(&bar[last & 1], (last >> 1) & 1, WAIT_LIMIT_NS);
-        bad = __syncthreads_or(!ok);
-    }
-    tc_fence_after();
-    if (bad) {
-        if (tid == 0 && a.err) atomicExch(a.err, 1);
-        mbar_wait(&bar[0], 0, DRAIN_LIMIT_NS);
-    } else {
-        // epilogue: warp w reads accumulator lanes 32w..32w+31 (its pixels)
-        const size_t row = ((size_t)(b * a.H + y) * a.W + x0) + warp * 32 + lane;
+    auto wait_jobs = [&]() {  // all but the newest S - 2 groups have landed
+        if (S >= 4)
+            cp_async_wait<2>();
+        else if (S == 3)
+            cp_async_wait<1>();
+        else
+            cp_async_wait<0>();
+    };
+    auto epilogue = [&](int i) {
+        const int t = tile_of(i);
+        const uint32_t acc = tmem + (uint32_t)((i & 1) * BN);
+        const size_t row = (size_t)t * RW + warp * 32 + lane;
 #pragma unroll 1
         for (int c = 0; c < BN; c += 16) {
             uint32_t r[16];
@@ -448,12 +426,102 @@ __global__ void __launch_bounds__(128) conv_row_kernel(const ConvArgs a) {
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                   "=r"(r[15])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+                : "r"(acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const int n = n0 + c;
-            if (n >= a.N) continue;
-            store_row16(a, row, n, r);
+            store_row16(a, row, n0 + c, r);
         }
+        tc_fence_before();  // the reads are ordered before the next barrier (buffer reuse)
+    };
+
+    if (wres) {
+        for (int kc = 0; kc < kchunks; ++kc) load_w(kc, wsm + kc * 9 * BN * 64);
+        cp_async_commit();
+    }
+    for (int p = 0; p < S - 1; ++p) {
+        if (p < njobs) load_job(p, p);
+        cp_async_commit();
+    }
+    bool bad = false;
+    for (int j = 0; j < njobs; ++j) {
+        const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
+        wait_jobs();
+        fence_proxy_async();  // the staged operands, for the tensor cores' reads
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t As = smem_u32(stg + st * STG);
+            const uint32_t Bs = wres ? smem_u32(wsm + kc * 9 * BN * 64) : As + RA_BYTES;
+            const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
+                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 16;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ad = umma_desc(a0 + 2 * h * RPLANE, RPLANE, 128);
+                    const uint64_t bd = umma_desc(Bs + tap * BN * 64 + h * 256, 128, 512);
+                    const uint32_t accum = (kc > 0 || tap > 0 || h > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(umma_idesc(RW, BN)), "r"(accum)
+                        : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar[st]))
+                         : "memory");
+            if (kc == kchunks - 1)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&accbar[i & 1]))
+                             : "memory");
+        }
+        if (kc == 0 && i >= 1) {
+            // tile i - 1 is complete once its last MMAs have committed
+            const bool ok = mbar_wait(&accbar[(i - 1) & 1], ((i - 1) >> 1) & 1, WAIT_LIMIT_NS);
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+            tc_fence_after();
+            epilogue(i - 1);
+        }
+        const int nj = j + S - 1;
+        if (nj < njobs) {
+            if (j >= 1) {
+                // the stage of job nj was last read by the MMAs of job j - 1
+                const int pj = j - 1;
+                const bool ok = mbar_wait(&bar[pj % S], (pj / S) & 1, WAIT_LIMIT_NS);
+                if (__syncthreads_or(!ok)) {
+                    bad = true;
+                    break;
+                }
+                tc_fence_after();
+            }
+            load_job(nj, nj % S);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (!bad && my_tiles > 0) {
+        const int i = my_tiles - 1;
+        const bool ok = mbar_wait(&accbar[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS);
+        bad = __syncthreads_or(!ok);
+        if (!bad) {
+            tc_fence_after();
+            epilogue(i);
+        }
+    }
+    if (bad) {
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+        // one last commit tracks every MMA this CTA issued: a short wait for it
+        // before the tensor memory is released
+        if (tid == 0)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(drain))
+                         : "memory");
+        mbar_wait(drain, 0, DRAIN_LIMIT_NS);
     }
     tc_fence_before();
     __syncthreads();
@@ -574,38 +642,70 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const WgradArgs a) {
 #define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
                                 i += (long long)gridDim.x * blockDim.x)
 
-// network input: 4 FP32 channels per pixel -> BF16 padded to cpad channels
+// network input: 4 FP32 channels per pixel -> BF16 padded to cpad channels;
+// one thread per pixel and 8-channel piece
 __global__ void pack_input_kernel(const float *x, bf16 *out, long long P, int cpad) {
-    GRID_STRIDE(i, P * cpad) {
-        const long long p = i / cpad;
-        const int c = (int)(i % cpad);
-        out[i] = __float2bfloat16_rn(c < 4 ? x[p * 4 + c] : 0.f);
+    const int g = cpad / 8;
+    GRID_STRIDE(i, P * g) {
+        const long long p = i / g;
+        uint4 o = make_uint4(0u, 0u, 0u, 0u);
+        if (i - p * g == 0) {
+            const float4 v = reinterpret_cast<const float4 *>(x)[p];
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+            o.x = *reinterpret_cast<uint32_t *>(&lo);
+            o.y = *reinterpret_cast<uint32_t *>(&hi);
+        }
+        reinterpret_cast<uint4 *>(out)[i] = o;
     }
 }
 
-// 2x2 average pooling, NHWC
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t u) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
+
+// 2x2 average pooling, NHWC BF16; one thread per output pixel and 8 channels
 __global__ void pool_kernel(const bf16 *in, bf16 *out, int B, int H, int W, int C) {
-    const int h2 = H / 2, w2 = W / 2;
-    GRID_STRIDE(i, (long long)B * h2 * w2 * C) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+    const int h2 = H / 2, w2 = W / 2, g = C / 8;
+    GRID_STRIDE(i, (long long)B * h2 * w2 * g) {
+        const int c8 = (int)(i % g);
+        long long t = i / g;
         const int x = (int)(t % w2);
         t /= w2;
         const int y = (int)(t % h2);
         const int b = (int)(t / h2);
-        auto at = [&](int yy, int xx) {
-            return __bfloat162float(in[(((long long)b * H + yy) * W + xx) * C + c]);
-        };
-        const float s = at(2 * y, 2 * x) + at(2 * y, 2 * x + 1) + at(2 * y + 1, 2 * x) + at(2 * y + 1, 2 * x + 1);
-        out[i] = __float2bfloat16_rn(0.25f * s);
+        const uint4 *src = reinterpret_cast<const uint4 *>(in);
+        auto at = [&](int yy, int xx) { return src[(((long long)b * H + yy) * W + xx) * g + c8]; };
+        const uint4 v00 = at(2 * y, 2 * x), v01 = at(2 * y, 2 * x + 1), v10 = at(2 * y + 1, 2 * x),
+                    v11 = at(2 * y + 1, 2 * x + 1);
+        const uint32_t *a = &v00.x, *b1 = &v01.x, *c = &v10.x, *d = &v11.x;
+        uint4 o;
+        uint32_t *op = &o.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 fa = bf2_to_f2(a[k]), fb = bf2_to_f2(b1[k]), fc = bf2_to_f2(c[k]), fd = bf2_to_f2(d[k]);
+            __nv_bfloat162 r = __floats2bfloat162_rn(0.25f * (fa.x + fb.x + fc.x + fd.x),
+                                                     0.25f * (fa.y + fb.y + fc.y + fd.y));
+            op[k] = *reinterpret_cast<uint32_t *>(&r);
+        }
+        reinterpret_cast<uint4 *>(out)[i] = o;
     }
 }
 
-// head: phi = tanh(d . w + b)
+// head: phi = tanh(w . d + b) per pixel (C a multiple of 8)
 __global__ void head_forward_kernel(const bf16 *d, const float *wb, int C, long long P, float *phi) {
     GRID_STRIDE(p, P) {
         float z = wb[C];
-        for (int c = 0; c < C; ++c) z += __bfloat162float(d[p * C + c]) * wb[c];
+        const uint4 *row = reinterpret_cast<const uint4 *>(d + p * C);
+        for (int c8 = 0; c8 < C / 8; ++c8) {
+            const uint4 v = row[c8];
+            const uint32_t *u = &v.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = bf2_to_f2(u[k]);
+                z += f.x * wb[8 * c8 + 2 * k];
+                z += f.y * wb[8 * c8 + 2 * k + 1];
+            }
+        }
         phi[p] = tanhf(z);
     }
 }
@@ -809,6 +909,7 @@ struct mclbm_unet {
     float *xin_f = nullptr, *t_f = nullptr, *mask_f = nullptr;  // staging of host inputs
     double *loss_part = nullptr, *loss_stat = nullptr;
     int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
+    int max_ctas = 0;    // bound on the row-tile convolution's CTAs (0: one wave)
     std::vector<void *> allocs;
     int cur_b = 0, cur_h = 0, cur_w = 0;
 };
@@ -849,19 +950,66 @@ cudaError_t launch_tc(const mclbm_unet &u, ConvArgs a) {
     return cudaGetLastError();
 }
 
+constexpr int ROW_SMEM_MAX = 227 * 1024;   // opt-in dynamic shared memory per CTA
+constexpr int ROW_SMEM_PAIR = 113 * 1024;  // per CTA when two share an SM
+
+// stages and weight residency of the row kernel: two CTAs per SM where that
+// leaves at least two stages, else one; weights resident where they fit
+RowPlan row_plan(int BN, int kchunks) {
+    for (int wres = 1; wres >= 0; --wres) {
+        const int fixed = row_smem(BN, kchunks, wres, 0);
+        const int stg = row_stage_bytes(BN, wres);
+        for (int cap : {ROW_SMEM_PAIR, ROW_SMEM_MAX}) {
+            int S = (cap - fixed) / stg;
+            if (S > 4) S = 4;
+            if (S >= 2) return RowPlan{wres, S, row_smem(BN, kchunks, wres, S)};
+        }
+    }
+    return RowPlan{0, 0, 0};
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    }
+    return n;
+}
+
 template <int BN>
 cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
-    constexpr int max_bytes = 2 * row_stage_bytes<BN>() + 32;
     static bool attr = false;
     if (!attr) {
         cudaError_t e =
-            cudaFuncSetAttribute(conv_row_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+            cudaFuncSetAttribute(conv_row_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, ROW_SMEM_MAX);
+        // all of the unified L1/shared memory as shared memory, so that two
+        // CTAs fit where the plan allows
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv_row_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int ring = (a.c0 + a.c1) / 32 > 1 ? 2 : 1;
-    const dim3 grid(a.M / RW, a.N / BN);
-    conv_row_kernel<BN><<<grid, 128, ring * row_stage_bytes<BN>() + 32, u.stream>>>(a);
+    const RowPlan plan = row_plan(BN, (a.c0 + a.c1) / 32);
+    if (plan.stages < 2) return cudaErrorInvalidValue;
+    // resident CTAs per SM: 228 KB of shared memory (1 KB reserved per CTA)
+    // and 512 tensor-memory columns (the occupancy query was seen to answer
+    // one where two fit; a CTA that does not fit merely starts later)
+    constexpr int cols = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;
+    int per_sm = (228 * 1024) / (plan.smem + 1024);
+    if (per_sm > 512 / cols) per_sm = 512 / cols;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int ntn = a.N / BN;
+    const long long items = (long long)(a.M / RW) * ntn;
+    long long grid = (long long)per_sm * sm_count();
+    if (u.max_ctas > 0 && grid > u.max_ctas) grid = u.max_ctas;
+    if (grid > items) grid = items;
+    grid -= grid % ntn;
+    if (grid < ntn) grid = ntn;
+    conv_row_kernel<BN><<<(int)grid, 128, plan.smem, u.stream>>>(a, plan);
     count_launch();
     return cudaGetLastError();
 }
@@ -991,7 +1139,7 @@ cudaError_t forward(mclbm_unet &u, int B, int H, int W) {
     for (int l = 0; l < Lv && e == cudaSuccess; ++l) {
         const int h = H >> l, w = W >> l;
         if (l > 0) {
-            pool_kernel<<<blocks_for((long long)B * h * w * ch(u, l - 1)), 256, 0, u.stream>>>(
+            pool_kernel<<<blocks_for((long long)B * h * w * (ch(u, l - 1) / 8)), 256, 0, u.stream>>>(
                 u.e_out[l - 1], u.a_in[l], B, 2 * h, 2 * w, ch(u, l - 1));
             count_launch();
         }
@@ -1125,7 +1273,7 @@ int run_forward(mclbm_unet *u, int B, int H, int W, const float *x, const float 
     if (e == cudaSuccess && target) e = stage_in(*u, u->t_f, target, (size_t)P);
     if (e == cudaSuccess && target) e = stage_in(*u, u->mask_f, mask, (size_t)P);
     if (e != cudaSuccess) return cuda_fail(e, "unet input copy");
-    pack_input_kernel<<<blocks_for(P * UNET_PAD0), 256, 0, u->stream>>>(u->xin_f, u->a_in[0], P, UNET_PAD0);
+    pack_input_kernel<<<blocks_for(P * (UNET_PAD0 / 8)), 256, 0, u->stream>>>(u->xin_f, u->a_in[0], P, UNET_PAD0);
     count_launch();
     if ((e = forward(*u, B, H, W)) != cudaSuccess) return cuda_fail(e, "unet forward");
     if (target) {
@@ -1281,6 +1429,12 @@ int mclbm_unet_destroy(mclbm_unet *u) {
 int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n) {
     if (!u || !n) return fail(MCLBM_ERR_ARG, "NULL argument");
     *n = u->nparam;
+    return MCLBM_OK;
+}
+
+int mclbm_unet_set_max_ctas(mclbm_unet *u, int n) {
+    if (!u || n < 0) return fail(MCLBM_ERR_ARG, "NULL network or negative bound");
+    u->max_ctas = n;
     return MCLBM_OK;
 }
 

@@ -92,6 +92,7 @@ _SIGS = {
     "mclbm_unet_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _P(_vp)]),
     "mclbm_unet_destroy": (C.c_int, [_vp]),
     "mclbm_unet_param_count": (C.c_int, [_vp, _P(_i64)]),
+    "mclbm_unet_set_max_ctas": (C.c_int, [_vp, C.c_int]),
     "mclbm_unet_set_params": (C.c_int, [_vp, _vp]),
     "mclbm_unet_get_params": (C.c_int, [_vp, _vp]),
     "mclbm_unet_infer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
@@ -487,6 +488,10 @@ def mclbm_unet_param_count(h) -> int:
     n = _i64()
     _check(load().mclbm_unet_param_count(h, C.byref(n)))
     return n.value
+
+
+def mclbm_unet_set_max_ctas(h, n: int) -> None:
+    _check(load().mclbm_unet_set_max_ctas(h, int(n)))
 
 
 def mclbm_unet_set_params(h, theta) -> None:

@@ -34,13 +34,17 @@ def _x8(x4):
 
 
 # widths below 128 take the pixel-gather kernel, multiples of 128 the
-# row-tile kernel (the last case: 512, 256 and 128 over its three levels)
-@pytest.mark.parametrize("levels,b,h,w", [(3, 2, 32, 48), (4, 1, 64, 32), (3, 1, 8, 512)])
-def test_forward_matches_reference(levels, b, h, w):
+# persistent row-tile kernel (the last cases: 512, 256 and 128 over three
+# levels); max_ctas = 3 makes each of its CTAs walk up to 11 tiles, through
+# both accumulator buffers and every stage of its ring
+@pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 32, 48, 0), (4, 1, 64, 32, 0), (3, 1, 8, 512, 0),
+                                                   (3, 1, 8, 512, 3)])
+def test_forward_matches_reference(levels, b, h, w, max_ctas):
     base = 32
     theta, x4, _, _ = _problem(levels, base, b, h, w, seed=levels)
     assert warmstart.param_count(levels, base) == ref.param_count(levels, base)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
+    mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
     net.set_params(theta)
     assert np.array_equal(net.params(), theta)
     phi = net.infer(x4)
@@ -52,11 +56,12 @@ def test_forward_matches_reference(levels, b, h, w):
     net.close()
 
 
-@pytest.mark.parametrize("b,h,w", [(2, 32, 32), (1, 8, 512)])
-def test_gradient_matches_reference(b, h, w):
+@pytest.mark.parametrize("b,h,w,max_ctas", [(2, 32, 32, 0), (1, 8, 512, 0), (1, 8, 512, 3)])
+def test_gradient_matches_reference(b, h, w, max_ctas):
     levels, base = 3, 32
     theta, x4, target, mask = _problem(levels, base, b, h, w, seed=7)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
+    mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
     net.set_params(theta)
     loss, g = net.gradient(x4, target, mask)
     want_loss, want_g, _ = ref.loss_and_gradient(theta.astype(np.float64), _x8(x4),
