@@ -22,6 +22,7 @@
 // memory); wgrad, a reduction over all pixels split across CTAs, on
 // mma.sync m16n8k16 with ldmatrix.trans fragments.  Pooling, the head, the
 // loss and Adam are elementwise kernels.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -84,6 +85,7 @@ struct ConvArgs {
     int B, H, W, M;       // M = B H W
     int sign;             // +1: taps read pixel + d; -1: pixel - d
     const bf16 *w;        // [N][9][c0 + c1]
+    const bf16 *wp;       // w packed for the row kernel with N tile row_bn(N), or null
     int N;
     const float *bias;    // [N] or null
     bf16 *ybf;            // ReLU(C + bias) as BF16 [M][N], or null
@@ -311,15 +313,24 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
 // apart, 8-pixel groups 128 bytes apart), so each input pixel crosses
 // L2 -> shared memory about 3 x 130 / 128 times instead of nine.
 //
+// Copies: the halo planes of the directly read input come by four tiled
+// tensor loads (box 8 channels x 130 pixels x 3 rows, zero fill outside the
+// image); the weights, pre-packed in global memory in exactly the shared
+// layout (per N tile and chunk), by one bulk copy; the upsampled input of a
+// decoder concat by cp.async from all threads (nearest upsampling is a
+// gather the tensor copy cannot express).
+//
 // A CTA owns one N tile and walks its tiles as a sequence of jobs (tile,
-// chunk) through a ring of S stages filled by cp.async S - 1 jobs ahead.
-// When all chunks' weights fit they are loaded once per CTA and the stages
-// carry halos only.  The accumulator is double-buffered in tensor memory:
-// the epilogue of tile i - 1 runs while the MMAs of tile i execute.
+// chunk) through a ring of S stages filled S - 1 jobs ahead.  When all
+// chunks' weights fit they are loaded once per CTA and the stages carry
+// halos only.  The accumulator is double-buffered in tensor memory: the
+// epilogue of tile i - 1 runs while the MMAs of tile i execute.
 // ---------------------------------------------------------------------------
 constexpr int RW = 128, RHALO = RW + 2;
-constexpr int RPLANE = 3 * RHALO * 16;  // one 16-byte channel piece of the halo
+constexpr int RPLANE = 6272;            // 3 x 130 x 16 bytes, rounded up to 128 (tensor-copy destination)
 constexpr int RA_BYTES = 4 * RPLANE;
+constexpr int RHALO_TX = 4 * 3 * RHALO * 16;  // bytes the four halo loads deliver
+static_assert(RPLANE >= 3 * RHALO * 16 && RPLANE % 128 == 0, "halo plane");
 
 struct RowPlan {
     int wres;    // all chunks' weights resident (1) or streamed per job (0)
@@ -330,24 +341,50 @@ struct RowPlan {
 __host__ __device__ inline int row_weight_bytes(int BN, int kchunks) { return 9 * BN * 64 * kchunks; }
 __host__ __device__ inline int row_stage_bytes(int BN, int wres) { return RA_BYTES + (wres ? 0 : 9 * BN * 64); }
 __host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int stages) {
-    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres) + 8 * 8;
+    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres) + 128;
 }
 
+// N tile of the row kernel for N output channels (0: none)
+__host__ __device__ inline int row_bn(int N) {
+    if (N == 32 || N == 64) return N;
+    if (N % 128 == 0) return 128;
+    if (N % 96 == 0) return 96;
+    if (N % 64 == 0) return 64;
+    if (N % 32 == 0) return 32;
+    return 0;
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr int ROW_THREADS = 256;  // 8 warps: loads by all, epilogue in two column halves
+
 template <int BN>
-__global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, const RowPlan plan) {
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    conv_row_kernel(const ConvArgs a, const RowPlan plan, const bf16 *__restrict__ wp,
+                    const __grid_constant__ CUtensorMap tmx) {
     constexpr uint32_t COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;  // two accumulators
-    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128");
+    constexpr int WTILE = 9 * BN * 64;                                        // weights of one chunk
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128; column halves of 16s");
     extern __shared__ __align__(1024) unsigned char smem[];
     const int K0 = a.c0 + a.c1;
     const int kchunks = K0 / 32;
     const int S = plan.stages, wres = plan.wres;
     const int WB = wres ? row_weight_bytes(BN, kchunks) : 0;
     const int STG = row_stage_bytes(BN, wres);
-    unsigned char *wsm = smem;                 // resident weights [kc][tap][core-matrix layout]
-    unsigned char *stg = smem + WB;            // S stages: halo (+ weights when streamed)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(stg + S * STG);  // [4] stage, [2] accumulator, [1] drain
-    uint64_t *accbar = bar + 4, *drain = bar + 6;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
+    unsigned char *wsm = smem;       // resident weights [kc][tap][core-matrix layout]
+    unsigned char *stg = smem + WB;  // S stages: halo planes (+ weights when streamed)
+    // barriers: full[4] (copies landed), done[4] (MMAs read the stage),
+    // acc[2] (accumulator complete), wfull (resident weights), drain
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg + S * STG);
+    uint64_t *done = full + 4, *accbar = full + 8, *wfull = full + 10, *drain = full + 11;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
     const int nt = blockIdx.x % ntn, n0 = nt * BN;
@@ -356,6 +393,7 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
     const int ntiles = a.M / RW;
     const int my_tiles = tile0 < ntiles ? (ntiles - tile0 + tstride - 1) / tstride : 0;
     const int njobs = my_tiles * kchunks;
+    const bf16 *wnt = wp + (size_t)nt * kchunks * (WTILE / 2);  // this N tile's packed weights
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -364,7 +402,7 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < 7; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < 12; ++k) mbar_init(&full[k], 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -372,40 +410,41 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    const int q = tid & 3;  // 16-byte piece of a pixel's 32 channels
-    // weights of chunk kc, nine taps: row (n, tap) at tap * BN * 64 + core-matrix offset of n
-    auto load_w = [&](int kc, unsigned char *Bs) {
-        const int ci = kc * 32 + q * 8;
-        for (int ntp = tid >> 2; ntp < 9 * BN; ntp += 32) {
-            const int n = ntp / 9, tap = ntp - n * 9;
-            const bf16 *src = a.w + ((size_t)(n0 + n) * 9 + tap) * K0 + ci;
-            cp_async16(Bs + tap * BN * 64 + ((n >> 3) * 4 + q) * 128 + (n & 7) * 16, src, true);
-        }
-    };
+    const int q = tid & 3;  // 16-byte piece of a pixel's 32 channels (cp.async path)
     auto tile_of = [&](int i) { return tile0 + i * tstride; };
+    // job j = (tile i, chunk kc) into stage st: thread 0 issues the bulk and
+    // tensor copies and the arrival on full[st]; upsampled chunks are
+    // gathered by all threads with cp.async
     auto load_job = [&](int j, int st) {
         const int i = j / kchunks, kc = j - i * kchunks;
         const int t = tile_of(i);
         const int x0 = (t % segs) * RW, y = (t / segs) % a.H, b = t / (segs * a.H);
         unsigned char *As = stg + st * STG;
-        const int ci = kc * 32 + q * 8;
-        for (int pix = tid >> 2; pix < 3 * RHALO; pix += 32) {
-            const int r = pix / RHALO, p = pix - r * RHALO;
-            const int yy = y + r - 1, xx = x0 + p - 1;
-            const bool v = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-            const bf16 *src = a.x0;
-            if (v) {
-                if (ci < a.c0)
-                    src = a.x0 + ((size_t)(b * a.H + yy) * a.W + xx) * a.c0 + ci;
-                else
-                    src = a.x1 + ((size_t)(b * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
-                          (ci - a.c0);
+        const bool direct = kc * 32 < a.c0;
+        if (tid == 0) {
+            const uint32_t tx = (direct ? RHALO_TX : 0) + (wres ? 0 : WTILE);
+            if (tx) {
+                mbar_expect_tx(&full[st], tx);
+                if (direct)
+                    for (int qq = 0; qq < 4; ++qq) tma_load_4d(As + qq * RPLANE, &tmx, kc * 32 + qq * 8, x0 - 1, y - 1, b, &full[st]);
+                if (!wres) bulk_g2s(As + RA_BYTES, wnt + (size_t)kc * (WTILE / 2), WTILE, &full[st]);
+            } else {
+                mbar_arrive(&full[st]);
             }
-            cp_async16(As + q * RPLANE + pix * 16, src, v);
         }
-        if (!wres) load_w(kc, As + RA_BYTES);
+        if (!direct) {
+            const int ci = kc * 32 + q * 8 - a.c0;
+            for (int pix = tid >> 2; pix < 3 * RHALO; pix += ROW_THREADS / 4) {
+                const int r = pix / RHALO, p = pix - r * RHALO;
+                const int yy = y + r - 1, xx = x0 + p - 1;
+                const bool v = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                const bf16 *src =
+                    v ? a.x1 + ((size_t)(b * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 + ci : a.x1;
+                cp_async16(As + q * RPLANE + pix * 16, src, v);
+            }
+        }
     };
-    auto wait_jobs = [&]() {  // all but the newest S - 2 groups have landed
+    auto wait_jobs = [&]() {  // all but the newest S - 2 cp.async groups have landed
         if (S >= 4)
             cp_async_wait<2>();
         else if (S == 3)
@@ -416,9 +455,11 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
     auto epilogue = [&](int i) {
         const int t = tile_of(i);
         const uint32_t acc = tmem + (uint32_t)((i & 1) * BN);
-        const size_t row = (size_t)t * RW + warp * 32 + lane;
+        // warp w reads accumulator lanes 32 (w % 4) .. + 31 (its pixels), column half w / 4
+        const size_t row = (size_t)t * RW + (warp & 3) * 32 + lane;
+        const int c_begin = (warp >> 2) * (BN / 2);
 #pragma unroll 1
-        for (int c = 0; c < BN; c += 16) {
+        for (int c = c_begin; c < c_begin + BN / 2; c += 16) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -426,32 +467,46 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                   "=r"(r[15])
-                : "r"(acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+                : "r"(acc + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             store_row16(a, row, n0 + c, r);
         }
         tc_fence_before();  // the reads are ordered before the next barrier (buffer reuse)
     };
 
-    if (wres) {
-        for (int kc = 0; kc < kchunks; ++kc) load_w(kc, wsm + kc * 9 * BN * 64);
-        cp_async_commit();
+    bool bad = false, wdone = !wres || njobs == 0;
+    int issued = 0, consumed = 0;  // jobs whose copies were issued / have landed
+    if (!wdone && tid == 0) {
+        mbar_expect_tx(wfull, WB);
+        bulk_g2s(wsm, wnt, WB, wfull);
     }
     for (int p = 0; p < S - 1; ++p) {
-        if (p < njobs) load_job(p, p);
+        if (p < njobs) {
+            load_job(p, p);
+            ++issued;
+        }
         cp_async_commit();
     }
-    bool bad = false;
-    for (int j = 0; j < njobs; ++j) {
+    if (!wdone) {
+        const bool ok = mbar_wait(wfull, 0, WAIT_LIMIT_NS);
+        bad = __syncthreads_or(!ok);
+        wdone = !bad;
+    }
+    for (int j = 0; j < njobs && !bad; ++j) {
         const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
         wait_jobs();
-        fence_proxy_async();  // the staged operands, for the tensor cores' reads
+        const bool okf = mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
+        fence_proxy_async();  // the cp.async-gathered operands, for the tensor cores' reads
         tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(!okf)) {
+            bad = true;
+            break;
+        }
+        ++consumed;
         if (tid == 0) {
             tc_fence_after();
             const uint32_t As = smem_u32(stg + st * STG);
-            const uint32_t Bs = wres ? smem_u32(wsm + kc * 9 * BN * 64) : As + RA_BYTES;
+            const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES;
             const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
 #pragma unroll 1
             for (int tap = 0; tap < 9; ++tap) {
@@ -470,7 +525,7 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&bar[st]))
+                             smem_u32(&done[st]))
                          : "memory");
             if (kc == kchunks - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -492,7 +547,7 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
             if (j >= 1) {
                 // the stage of job nj was last read by the MMAs of job j - 1
                 const int pj = j - 1;
-                const bool ok = mbar_wait(&bar[pj % S], (pj / S) & 1, WAIT_LIMIT_NS);
+                const bool ok = mbar_wait(&done[pj % S], (pj / S) & 1, WAIT_LIMIT_NS);
                 if (__syncthreads_or(!ok)) {
                     bad = true;
                     break;
@@ -500,6 +555,7 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
                 tc_fence_after();
             }
             load_job(nj, nj % S);
+            ++issued;
         }
         cp_async_commit();
     }
@@ -515,8 +571,11 @@ __global__ void __launch_bounds__(128, 1) conv_row_kernel(const ConvArgs a, cons
     }
     if (bad) {
         if (tid == 0 && a.err) atomicExch(a.err, 1);
-        // one last commit tracks every MMA this CTA issued: a short wait for it
-        // before the tensor memory is released
+        // short waits for the copies still in flight into shared memory, and
+        // for every MMA this CTA issued (one last commit tracks them all),
+        // before the memory is released
+        if (!wdone) mbar_wait(wfull, 0, DRAIN_LIMIT_NS);
+        for (int jb = consumed; jb < issued; ++jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
         if (tid == 0)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(drain))
@@ -838,6 +897,24 @@ __global__ void weights_bf16_kernel(const float *w, int co, int ci, int cpad, bf
     }
 }
 
+// BF16 weights w [N][9][K0] -> the row kernel's shared-memory image: per N
+// tile of BN and chunk of 32 input channels, [tap][n / 8][k / 8][n % 8][k % 8]
+// (the K-major core-matrix layout of the B operand), tiles and chunks in
+// (N tile, chunk) order
+__global__ void pack_row_kernel(const bf16 *w, int N, int K0, int BN, bf16 *out) {
+    const int kchunks = K0 / 32;
+    GRID_STRIDE(i, (long long)N * 9 * K0) {
+        const int k_all = (int)(i % K0);
+        const long long t = i / K0;
+        const int tap = (int)(t % 9);
+        const int n_all = (int)(t / 9);
+        const int nt = n_all / BN, n = n_all - nt * BN, kc = k_all / 32, k = k_all - kc * 32;
+        const long long dst = ((long long)(nt * kchunks + kc) * 9 + tap) * BN * 32 +
+                              ((n >> 3) * 4 + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+        out[dst] = w[i];
+    }
+}
+
 // padded weight gradient [co][9][cpad] -> flat [co][3][3][ci]
 __global__ void grad_pack_kernel(const float *dw, int co, int ci, int cpad, float *g) {
     GRID_STRIDE(i, (long long)co * 9 * ci) {
@@ -891,6 +968,7 @@ struct UnetLayer {
     int co, ci, cpad, k;     // k = 3 (conv3x3) or 1 (head)
     long long off;           // offset of the weights in the flat parameter vector; bias follows
     bf16 *wf = nullptr, *wt = nullptr;
+    bf16 *wpf = nullptr, *wpt = nullptr;  // wf, wt packed for the row kernel (N tile row_bn(N))
     float *dw = nullptr;     // [co][9][cpad]
 };
 
@@ -979,6 +1057,42 @@ int sm_count() {
     return n;
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// tensor map of the directly read input x0 [B][H][W][c0] (BF16): box of 8
+// channels x 130 pixels x 3 rows x 1 image, zero fill outside
+cudaError_t halo_map(const ConvArgs &a, CUtensorMap *m) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)a.c0, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+    const cuuint64_t strides[3] = {(cuuint64_t)a.c0 * 2, (cuuint64_t)a.W * a.c0 * 2,
+                                   (cuuint64_t)a.H * a.W * a.c0 * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)RHALO, 3, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(a.x0), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int BN>
 cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     static bool attr = false;
@@ -1009,7 +1123,10 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     if (grid > items) grid = items;
     grid -= grid % ntn;
     if (grid < ntn) grid = ntn;
-    conv_row_kernel<BN><<<(int)grid, 128, plan.smem, u.stream>>>(a, plan);
+    CUtensorMap tmx;
+    cudaError_t e = halo_map(a, &tmx);
+    if (e != cudaSuccess) return e;
+    conv_row_kernel<BN><<<(int)grid, ROW_THREADS, plan.smem, u.stream>>>(a, plan, a.wp, tmx);
     count_launch();
     return cudaGetLastError();
 }
@@ -1020,13 +1137,14 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
 cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
     a.err = u.err;
     if (a.c0 % TBK || (a.c0 + a.c1) % TBK || a.N % 16) return cudaErrorInvalidValue;
-    if (a.W % RW == 0) {
-        if (a.N == 32) return launch_row<32>(u, a);
-        if (a.N == 64) return launch_row<64>(u, a);
-        if (a.N % 128 == 0) return launch_row<128>(u, a);
-        if (a.N % 96 == 0) return launch_row<96>(u, a);
-        if (a.N % 64 == 0) return launch_row<64>(u, a);
-        if (a.N % 32 == 0) return launch_row<32>(u, a);
+    if (a.W % RW == 0 && a.wp) {
+        switch (row_bn(a.N)) {
+            case 32: return launch_row<32>(u, a);
+            case 64: return launch_row<64>(u, a);
+            case 96: return launch_row<96>(u, a);
+            case 128: return launch_row<128>(u, a);
+            default: break;
+        }
     }
     switch (a.N) {
         case 32: return launch_tc<32>(u, a);
@@ -1068,6 +1186,7 @@ cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W
     a.M = B * H * W;
     a.sign = 1;
     a.w = L.wf;
+    a.wp = L.wpf;
     a.N = L.co;
     a.bias = u.theta + L.off + (long long)L.co * 9 * L.ci;
     a.ybf = y;
@@ -1115,6 +1234,7 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
     a.M = M;
     a.sign = -1;
     a.w = L.wt;
+    a.wp = L.wpt;
     a.N = L.cpad;
     a.bias = nullptr;
     a.ybf = nullptr;
@@ -1128,6 +1248,16 @@ cudaError_t refresh_weights(mclbm_unet &u) {
         weights_bf16_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
             u.theta + L.off, L.co, L.ci, L.cpad, L.wf, L.wt);
         count_launch();
+        if (row_bn(L.co)) {
+            pack_row_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
+                L.wf, L.co, L.cpad, row_bn(L.co), L.wpf);
+            count_launch();
+        }
+        if (row_bn(L.cpad)) {
+            pack_row_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
+                L.wt, L.cpad, L.co, row_bn(L.cpad), L.wpt);
+            count_launch();
+        }
     }
     return cudaGetLastError();
 }
@@ -1374,6 +1504,8 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
         if (L.k != 3) continue;
         A((void **)&L.wf, (size_t)L.co * 9 * L.cpad * 2);
         A((void **)&L.wt, (size_t)L.co * 9 * L.cpad * 2);
+        A((void **)&L.wpf, (size_t)L.co * 9 * L.cpad * 2);
+        A((void **)&L.wpt, (size_t)L.co * 9 * L.cpad * 2);
         A((void **)&L.dw, (size_t)L.co * 9 * L.cpad * 4);
     }
     u->a_in.assign(levels, nullptr);
