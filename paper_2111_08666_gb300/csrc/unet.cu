@@ -113,6 +113,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
            (uint64_t)((sbo >> 4) & 0x3fffu) << 32 | (uint64_t)1 << 46;
 }
 
+// the same for the 64-byte-swizzled K-major layout (rows of 64 bytes, the
+// 16-byte chunk c of a row stored at c ^ (address bits 7-8), as the tensor
+// copy writes it): sbo between 8-row groups.  The swizzle follows the
+// absolute shared-memory address, so a start moved by whole rows needs no
+// base offset (measured: base offset 0 is exact for every row shift, the
+// start's phase in that field is not)
+__device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | (uint64_t)1 << 16 | (uint64_t)((sbo >> 4) & 0x3fffu) << 32 |
+           (uint64_t)1 << 46 | (uint64_t)4 << 61;
+}
+
 // instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
 __host__ __device__ constexpr uint32_t umma_idesc(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -306,19 +317,22 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
 // Row-tile variant for images whose width is a multiple of 128, persistent
 // and pipelined.  A tile is 128 consecutive pixels of one image row.  Per
 // chunk of 32 input channels the tile needs the 3 x 130 halo of its row
-// segment (channel piece q of pixel p of halo row r at plane q, offset
-// (130 r + p) x 16 bytes) and the nine taps' weights; the A operand of tap
-// (dy, dx) is the same halo read through a descriptor whose start moves by dy
-// rows and dx pixels (K-major, no swizzle: K-adjacent core matrices one plane
-// apart, 8-pixel groups 128 bytes apart), so each input pixel crosses
-// L2 -> shared memory about 3 x 130 / 128 times instead of nine.
+// segment and the nine taps' weights.  The halo is stored pixel-major, 64
+// bytes (32 channels) per pixel in the 64-byte-swizzled K-major layout of
+// the tensor cores; the A operand of tap (dy, dx) is the same halo read
+// through a descriptor whose start moves by dy rows and dx pixels (the
+// descriptor's base offset carries the start's phase in the swizzle), so each
+// input pixel crosses L2 -> shared memory about 3 x 130 / 128 times instead
+// of nine.
 //
-// Copies: the halo planes of the directly read input come by four tiled
-// tensor loads (box 8 channels x 130 pixels x 3 rows, zero fill outside the
+// Copies: the halo of the directly read input comes by one tiled tensor load
+// (box 32 channels x 130 pixels x 3 rows, swizzled, zero fill outside the
 // image); the weights, pre-packed in global memory in exactly the shared
-// layout (per N tile and chunk), by one bulk copy; the upsampled input of a
-// decoder concat by cp.async from all threads (nearest upsampling is a
-// gather the tensor copy cannot express).
+// layout (per N tile and chunk; K-major core matrices, no swizzle), by one
+// bulk copy.  The upsampled input of a decoder concat comes as the coarse
+// 2 x 66 pixels it needs (one tensor load) and is expanded into the halo by
+// all threads (nearest upsampling is a gather the tensor copy cannot
+// express).
 //
 // A CTA owns one N tile and walks its tiles as a sequence of jobs (tile,
 // chunk) through a ring of S stages filled S - 1 jobs ahead.  When all
@@ -327,21 +341,29 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
 // epilogue of tile i - 1 runs while the MMAs of tile i execute.
 // ---------------------------------------------------------------------------
 constexpr int RW = 128, RHALO = RW + 2;
-constexpr int RPLANE = 6272;            // 3 x 130 x 16 bytes, rounded up to 128 (tensor-copy destination)
-constexpr int RA_BYTES = 4 * RPLANE;
-constexpr int RHALO_TX = 4 * 3 * RHALO * 16;  // bytes the four halo loads deliver
-static_assert(RPLANE >= 3 * RHALO * 16 && RPLANE % 128 == 0, "halo plane");
+constexpr int RHALO_TX = 3 * RHALO * 64;  // halo of one chunk: 3 rows x 130 pixels x 64 bytes
+constexpr int RA_BYTES = 25600;           // ... rounded up to 1024 (swizzled tensor-copy destination)
+static_assert(RA_BYTES >= RHALO_TX && RA_BYTES % 1024 == 0, "halo area");
 
 struct RowPlan {
     int wres;    // all chunks' weights resident (1) or streamed per job (0)
+    int ux;      // the input has an upsampled part (stages carry its coarse staging)
     int stages;  // 2..4
     int smem;    // dynamic shared memory bytes
 };
 
+// coarse staging of an upsampled chunk: 2 rows x 66 pixels x 64 bytes,
+// rounded up to 1024 (keeps the stages aligned)
+constexpr int RU_TX = 2 * 66 * 64;
+constexpr int RU_BYTES = 9216;
+static_assert(RU_BYTES >= RU_TX && RU_BYTES % 1024 == 0, "staging area");
+
 __host__ __device__ inline int row_weight_bytes(int BN, int kchunks) { return 9 * BN * 64 * kchunks; }
-__host__ __device__ inline int row_stage_bytes(int BN, int wres) { return RA_BYTES + (wres ? 0 : 9 * BN * 64); }
-__host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int stages) {
-    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres) + 128;
+__host__ __device__ inline int row_stage_bytes(int BN, int wres, int ux) {
+    return RA_BYTES + (ux ? RU_BYTES : 0) + (wres ? 0 : 9 * BN * 64);
+}
+__host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int ux, int stages) {
+    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres, ux) + 128;
 }
 
 // N tile of the row kernel for N output channels (0: none)
@@ -368,16 +390,20 @@ constexpr int ROW_THREADS = 256;  // 8 warps: loads by all, epilogue in two colu
 template <int BN>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
     conv_row_kernel(const ConvArgs a, const RowPlan plan, const bf16 *__restrict__ wp,
-                    const __grid_constant__ CUtensorMap tmx) {
+                    const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmu) {
     constexpr uint32_t COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;  // two accumulators
     constexpr int WTILE = 9 * BN * 64;                                        // weights of one chunk
     static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128; column halves of 16s");
     extern __shared__ __align__(1024) unsigned char smem[];
+    if (smem_u32(smem) & 1023u) {  // the swizzled copies need 1024-byte-aligned stages
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+        return;
+    }
     const int K0 = a.c0 + a.c1;
     const int kchunks = K0 / 32;
     const int S = plan.stages, wres = plan.wres;
     const int WB = wres ? row_weight_bytes(BN, kchunks) : 0;
-    const int STG = row_stage_bytes(BN, wres);
+    const int STG = row_stage_bytes(BN, wres, plan.ux);
     unsigned char *wsm = smem;       // resident weights [kc][tap][core-matrix layout]
     unsigned char *stg = smem + WB;  // S stages: halo planes (+ weights when streamed)
     // barriers: full[4] (copies landed), done[4] (MMAs read the stage),
@@ -385,6 +411,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(stg + S * STG);
     uint64_t *done = full + 4, *accbar = full + 8, *wfull = full + 10, *drain = full + 11;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 12);
+    int *flag = reinterpret_cast<int *>(full + 13);  // a wait of thread 0 gave up
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
     const int nt = blockIdx.x % ntn, n0 = nt * BN;
@@ -403,6 +430,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     }
     if (tid == 0) {
         for (int k = 0; k < 12; ++k) mbar_init(&full[k], 1);
+        *flag = 0;
         fence_mbar_init();
     }
     tc_fence_before();
@@ -410,47 +438,46 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    const int q = tid & 3;  // 16-byte piece of a pixel's 32 channels (cp.async path)
     auto tile_of = [&](int i) { return tile0 + i * tstride; };
-    // job j = (tile i, chunk kc) into stage st: thread 0 issues the bulk and
-    // tensor copies and the arrival on full[st]; upsampled chunks are
-    // gathered by all threads with cp.async
+    struct Where {
+        int x0, y, b;
+    };
+    auto where = [&](int i) {
+        const int t = tile_of(i);
+        return Where{(t % segs) * RW, (t / segs) % a.H, t / (segs * a.H)};
+    };
+    // job j = (tile i, chunk kc) into stage st, by thread 0: the four halo
+    // planes of a direct chunk, or the coarse rows of an upsampled chunk into
+    // the stage's staging area; the chunk's weights when they are streamed
     auto load_job = [&](int j, int st) {
         const int i = j / kchunks, kc = j - i * kchunks;
-        const int t = tile_of(i);
-        const int x0 = (t % segs) * RW, y = (t / segs) % a.H, b = t / (segs * a.H);
+        const Where w = where(i);
         unsigned char *As = stg + st * STG;
         const bool direct = kc * 32 < a.c0;
-        if (tid == 0) {
-            const uint32_t tx = (direct ? RHALO_TX : 0) + (wres ? 0 : WTILE);
-            if (tx) {
-                mbar_expect_tx(&full[st], tx);
-                if (direct)
-                    for (int qq = 0; qq < 4; ++qq) tma_load_4d(As + qq * RPLANE, &tmx, kc * 32 + qq * 8, x0 - 1, y - 1, b, &full[st]);
-                if (!wres) bulk_g2s(As + RA_BYTES, wnt + (size_t)kc * (WTILE / 2), WTILE, &full[st]);
-            } else {
-                mbar_arrive(&full[st]);
-            }
-        }
-        if (!direct) {
-            const int ci = kc * 32 + q * 8 - a.c0;
-            for (int pix = tid >> 2; pix < 3 * RHALO; pix += ROW_THREADS / 4) {
-                const int r = pix / RHALO, p = pix - r * RHALO;
-                const int yy = y + r - 1, xx = x0 + p - 1;
-                const bool v = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                const bf16 *src =
-                    v ? a.x1 + ((size_t)(b * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 + ci : a.x1;
-                cp_async16(As + q * RPLANE + pix * 16, src, v);
-            }
-        }
-    };
-    auto wait_jobs = [&]() {  // all but the newest S - 2 cp.async groups have landed
-        if (S >= 4)
-            cp_async_wait<2>();
-        else if (S == 3)
-            cp_async_wait<1>();
+        mbar_expect_tx(&full[st], (direct ? RHALO_TX : RU_TX) + (wres ? 0 : WTILE));
+        if (direct)
+            tma_load_4d(As, &tmx, kc * 32, w.x0 - 1, w.y - 1, w.b, &full[st]);
         else
-            cp_async_wait<0>();
+            tma_load_4d(As + RA_BYTES, &tmu, kc * 32 - a.c0, (w.x0 >> 1) - 1, (w.y - 1) >> 1, w.b, &full[st]);
+        if (!wres)
+            bulk_g2s(As + RA_BYTES + (plan.ux ? RU_BYTES : 0), wnt + (size_t)kc * (WTILE / 2), WTILE, &full[st]);
+    };
+    // nearest upsampling: halo pixel (r, p) of the fine grid takes coarse
+    // pixel ((y + r - 1) >> 1, (x0 + p - 1) >> 1), relative to the staged rows
+    auto expand = [&](int i, int st) {
+        const Where w = where(i);
+        unsigned char *As = stg + st * STG;
+        const unsigned char *U = As + RA_BYTES;
+        const int cy0 = (w.y - 1) >> 1, cx0 = (w.x0 >> 1) - 1;
+        const uint32_t hbase = smem_u32(As);
+        for (int idx = tid; idx < 4 * 3 * RHALO; idx += ROW_THREADS) {
+            const int qq = idx & 3, pix = idx >> 2;
+            const int r = pix / RHALO, p = pix - r * RHALO;
+            const int cr = ((w.y + r - 1) >> 1) - cy0, cp = ((w.x0 + p - 1) >> 1) - cx0;
+            const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // the 64-byte swizzle of this row
+            *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
+                *reinterpret_cast<const uint4 *>(U + (cr * 66 + cp) * 64 + qq * 16);
+        }
     };
     auto epilogue = [&](int i) {
         const int t = tile_of(i);
@@ -475,17 +502,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     };
 
     bool bad = false, wdone = !wres || njobs == 0;
-    int issued = 0, consumed = 0;  // jobs whose copies were issued / have landed
-    if (!wdone && tid == 0) {
-        mbar_expect_tx(wfull, WB);
-        bulk_g2s(wsm, wnt, WB, wfull);
-    }
-    for (int p = 0; p < S - 1; ++p) {
-        if (p < njobs) {
-            load_job(p, p);
-            ++issued;
+    int issued = 0, consumed = 0;  // jobs whose copies thread 0 issued / that have landed
+    if (tid == 0) {
+        if (!wdone) {
+            mbar_expect_tx(wfull, WB);
+            bulk_g2s(wsm, wnt, WB, wfull);
         }
-        cp_async_commit();
+        for (int p = 0; p < S - 1 && p < njobs; ++p) load_job(p, p);
+        issued = S - 1 < njobs ? S - 1 : njobs;
     }
     if (!wdone) {
         const bool ok = mbar_wait(wfull, 0, WAIT_LIMIT_NS);
@@ -494,11 +518,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     }
     for (int j = 0; j < njobs && !bad; ++j) {
         const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
-        wait_jobs();
         const bool okf = mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
-        fence_proxy_async();  // the cp.async-gathered operands, for the tensor cores' reads
+        if (okf && kc * 32 >= a.c0) expand(i, st);
+        fence_proxy_async();  // expanded halo (generic writes), for the tensor cores' reads
         tc_fence_before();
-        if (__syncthreads_or(!okf)) {
+        if (__syncthreads_or(!okf || *flag)) {
             bad = true;
             break;
         }
@@ -506,15 +530,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         if (tid == 0) {
             tc_fence_after();
             const uint32_t As = smem_u32(stg + st * STG);
-            const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES;
+            const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES + (plan.ux ? RU_BYTES : 0);
             const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
 #pragma unroll 1
             for (int tap = 0; tap < 9; ++tap) {
                 const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 16;
+                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 64;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint64_t ad = umma_desc(a0 + 2 * h * RPLANE, RPLANE, 128);
+                    const uint64_t ad = umma_desc_sw64(a0 + h * 32, 512);
                     const uint64_t bd = umma_desc(Bs + tap * BN * 64 + h * 256, 128, 512);
                     const uint32_t accum = (kc > 0 || tap > 0 || h > 0) ? 1u : 0u;
                     asm volatile(
@@ -531,6 +555,19 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&accbar[i & 1]))
                              : "memory");
+            // refill: job j + S - 1 goes into the stage of job j - 1 once its
+            // MMAs have read it
+            const int nj = j + S - 1;
+            if (nj < njobs) {
+                bool ok = true;
+                if (j >= 1) ok = mbar_wait(&done[(j - 1) % S], ((j - 1) / S) & 1, WAIT_LIMIT_NS);
+                if (ok) {
+                    load_job(nj, nj % S);
+                    ++issued;
+                } else {
+                    *flag = 1;
+                }
+            }
         }
         if (kc == 0 && i >= 1) {
             // tile i - 1 is complete once its last MMAs have committed
@@ -542,24 +579,9 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             tc_fence_after();
             epilogue(i - 1);
         }
-        const int nj = j + S - 1;
-        if (nj < njobs) {
-            if (j >= 1) {
-                // the stage of job nj was last read by the MMAs of job j - 1
-                const int pj = j - 1;
-                const bool ok = mbar_wait(&done[pj % S], (pj / S) & 1, WAIT_LIMIT_NS);
-                if (__syncthreads_or(!ok)) {
-                    bad = true;
-                    break;
-                }
-                tc_fence_after();
-            }
-            load_job(nj, nj % S);
-            ++issued;
-        }
-        cp_async_commit();
     }
-    cp_async_wait<0>();
+    __syncthreads();
+    if (*flag) bad = true;
     if (!bad && my_tiles > 0) {
         const int i = my_tiles - 1;
         const bool ok = mbar_wait(&accbar[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS);
@@ -575,7 +597,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         // for every MMA this CTA issued (one last commit tracks them all),
         // before the memory is released
         if (!wdone) mbar_wait(wfull, 0, DRAIN_LIMIT_NS);
-        for (int jb = consumed; jb < issued; ++jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
+        if (tid == 0)
+            for (int jb = consumed; jb < issued; ++jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
         if (tid == 0)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(drain))
@@ -1033,17 +1056,17 @@ constexpr int ROW_SMEM_PAIR = 113 * 1024;  // per CTA when two share an SM
 
 // stages and weight residency of the row kernel: two CTAs per SM where that
 // leaves at least two stages, else one; weights resident where they fit
-RowPlan row_plan(int BN, int kchunks) {
+RowPlan row_plan(int BN, int kchunks, int ux) {
     for (int wres = 1; wres >= 0; --wres) {
-        const int fixed = row_smem(BN, kchunks, wres, 0);
-        const int stg = row_stage_bytes(BN, wres);
+        const int fixed = row_smem(BN, kchunks, wres, ux, 0);
+        const int stg = row_stage_bytes(BN, wres, ux);
         for (int cap : {ROW_SMEM_PAIR, ROW_SMEM_MAX}) {
             int S = (cap - fixed) / stg;
             if (S > 4) S = 4;
-            if (S >= 2) return RowPlan{wres, S, row_smem(BN, kchunks, wres, S)};
+            if (S >= 2) return RowPlan{wres, ux, S, row_smem(BN, kchunks, wres, ux, S)};
         }
     }
-    return RowPlan{0, 0, 0};
+    return RowPlan{0, ux, 0, 0};
 }
 
 int sm_count() {
@@ -1077,18 +1100,19 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// tensor map of the directly read input x0 [B][H][W][c0] (BF16): box of 8
-// channels x 130 pixels x 3 rows x 1 image, zero fill outside
-cudaError_t halo_map(const ConvArgs &a, CUtensorMap *m) {
+// tensor map of an NHWC BF16 tensor [B][H][W][C] read in boxes of 32
+// channels x bw pixels x bh rows x 1 image (64-byte rows, swizzled or not),
+// zero fill outside
+cudaError_t nhwc_map(const bf16 *base, int B, int H, int W, int C, int bw, int bh, bool sw64, CUtensorMap *m) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[4] = {(cuuint64_t)a.c0, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
-    const cuuint64_t strides[3] = {(cuuint64_t)a.c0 * 2, (cuuint64_t)a.W * a.c0 * 2,
-                                   (cuuint64_t)a.H * a.W * a.c0 * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)RHALO, 3, 1};
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {32, (cuuint32_t)bw, (cuuint32_t)bh, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(a.x0), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -1107,7 +1131,7 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const RowPlan plan = row_plan(BN, (a.c0 + a.c1) / 32);
+    const RowPlan plan = row_plan(BN, (a.c0 + a.c1) / 32, a.c1 > 0 ? 1 : 0);
     if (plan.stages < 2) return cudaErrorInvalidValue;
     // resident CTAs per SM: 228 KB of shared memory (1 KB reserved per CTA)
     // and 512 tensor-memory columns (the occupancy query was seen to answer
@@ -1123,10 +1147,14 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     if (grid > items) grid = items;
     grid -= grid % ntn;
     if (grid < ntn) grid = ntn;
-    CUtensorMap tmx;
-    cudaError_t e = halo_map(a, &tmx);
+    // the direct input in swizzled halo boxes (130 pixels x 3 rows); the
+    // coarse input of an upsampled concat in plain boxes of 66 pixels x 2 rows
+    CUtensorMap tmx, tmu;
+    cudaError_t e = nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmx);
+    if (e == cudaSuccess)
+        e = a.c1 > 0 ? nhwc_map(a.x1, a.B, a.H >> 1, a.W >> 1, a.c1, 66, 2, false, &tmu) : nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmu);
     if (e != cudaSuccess) return e;
-    conv_row_kernel<BN><<<(int)grid, ROW_THREADS, plan.smem, u.stream>>>(a, plan, a.wp, tmx);
+    conv_row_kernel<BN><<<(int)grid, ROW_THREADS, plan.smem, u.stream>>>(a, plan, a.wp, tmx, tmu);
     count_launch();
     return cudaGetLastError();
 }
@@ -1422,7 +1450,8 @@ int check_err(mclbm_unet *u) {
     if (e != cudaSuccess) return cuda_fail(e, "unet error word");
     if (err) {
         cudaMemset(u->err, 0, sizeof(int));
-        return fail(MCLBM_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+        if (err == 2) return fail(MCLBM_ERR_CUDA, "row-tile convolution: shared memory not 1024-byte aligned");
+        return fail(MCLBM_ERR_TIMEOUT, "a tensor-core convolution timed out waiting for its copies or MMAs");
     }
     return MCLBM_OK;
 }
