@@ -363,7 +363,7 @@ __host__ __device__ inline int row_stage_bytes(int BN, int wres, int ux) {
     return RA_BYTES + (ux ? RU_BYTES : 0) + (wres ? 0 : 9 * BN * 64);
 }
 __host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int ux, int stages) {
-    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres, ux) + 128;
+    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres, ux) + 256;
 }
 
 // N tile of the row kernel for N output channels (0: none)
@@ -385,7 +385,18 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0,
         : "memory");
 }
 
-constexpr int ROW_THREADS = 256;  // 8 warps: loads by all, epilogue in two column halves
+// Roles (warp-specialized, mbarriers only in the steady state):
+//   warp 0        producer: tensor/bulk copies of job j into stage j % S once
+//                 the MMAs of job j - S have read that stage
+//   warp 1        MMA issue: waits for job j's data (and expansion), for the
+//                 accumulator buffer of tile i (its epilogue two tiles back),
+//                 issues the 18 MMAs of the chunk and commits
+//   warps 2-5     expansion of upsampled chunks into the halo (an arrival on
+//                 expanded[st] for every job keeps the phases in step)
+//   warps 6-9     epilogue: accumulator -> registers (tcgen05.ld), frees the
+//                 buffer, bias + ReLU + stores (warp w reads lanes 32 (w % 4)..)
+constexpr int ROW_THREADS = 320;
+constexpr int ROW_EXP = 128;  // expansion threads
 
 template <int BN>
 __global__ void __launch_bounds__(ROW_THREADS, 1)
@@ -393,7 +404,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmu) {
     constexpr uint32_t COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;  // two accumulators
     constexpr int WTILE = 9 * BN * 64;                                        // weights of one chunk
-    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128; column halves of 16s");
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 128, "UMMA N for M = 128");
     extern __shared__ __align__(1024) unsigned char smem[];
     if (smem_u32(smem) & 1023u) {  // the swizzled copies need 1024-byte-aligned stages
         if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
@@ -405,13 +416,15 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     const int WB = wres ? row_weight_bytes(BN, kchunks) : 0;
     const int STG = row_stage_bytes(BN, wres, plan.ux);
     unsigned char *wsm = smem;       // resident weights [kc][tap][core-matrix layout]
-    unsigned char *stg = smem + WB;  // S stages: halo planes (+ weights when streamed)
-    // barriers: full[4] (copies landed), done[4] (MMAs read the stage),
-    // acc[2] (accumulator complete), wfull (resident weights), drain
-    uint64_t *full = reinterpret_cast<uint64_t *>(stg + S * STG);
-    uint64_t *done = full + 4, *accbar = full + 8, *wfull = full + 10, *drain = full + 11;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 12);
-    int *flag = reinterpret_cast<int *>(full + 13);  // a wait of thread 0 gave up
+    unsigned char *stg = smem + WB;  // S stages: halo (+ coarse staging) (+ weights when streamed)
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg + S * STG);  // [4] copies landed
+    uint64_t *done = full + 4;                                     // [4] MMAs have read the stage
+    uint64_t *expd = full + 8;                                     // [4] halo complete (expansion)
+    uint64_t *accf = full + 12;                                    // [2] accumulator complete
+    uint64_t *acce = full + 14;                                    // [2] accumulator read out
+    uint64_t *wfull = full + 16, *drain = full + 17;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 18);
+    int *flag = reinterpret_cast<int *>(full + 19);  // some role gave up waiting
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
     const int nt = blockIdx.x % ntn, n0 = nt * BN;
@@ -429,7 +442,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < 12; ++k) mbar_init(&full[k], 1);
+        for (int k = 0; k < 4; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&done[k], 1);
+            mbar_init(&expd[k], ROW_EXP);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&accf[k], 1);
+            mbar_init(&acce[k], 4);
+        }
+        mbar_init(wfull, 1);
+        mbar_init(drain, 1);
         *flag = 0;
         fence_mbar_init();
     }
@@ -438,172 +461,170 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    auto tile_of = [&](int i) { return tile0 + i * tstride; };
     struct Where {
         int x0, y, b;
     };
     auto where = [&](int i) {
-        const int t = tile_of(i);
+        const int t = tile0 + i * tstride;
         return Where{(t % segs) * RW, (t / segs) % a.H, t / (segs * a.H)};
     };
-    // job j = (tile i, chunk kc) into stage st, by thread 0: the four halo
-    // planes of a direct chunk, or the coarse rows of an upsampled chunk into
-    // the stage's staging area; the chunk's weights when they are streamed
-    auto load_job = [&](int j, int st) {
-        const int i = j / kchunks, kc = j - i * kchunks;
-        const Where w = where(i);
-        unsigned char *As = stg + st * STG;
-        const bool direct = kc * 32 < a.c0;
-        mbar_expect_tx(&full[st], (direct ? RHALO_TX : RU_TX) + (wres ? 0 : WTILE));
-        if (direct)
-            tma_load_4d(As, &tmx, kc * 32, w.x0 - 1, w.y - 1, w.b, &full[st]);
-        else
-            tma_load_4d(As + RA_BYTES, &tmu, kc * 32 - a.c0, (w.x0 >> 1) - 1, (w.y - 1) >> 1, w.b, &full[st]);
-        if (!wres)
-            bulk_g2s(As + RA_BYTES + (plan.ux ? RU_BYTES : 0), wnt + (size_t)kc * (WTILE / 2), WTILE, &full[st]);
+    auto give_up = [&]() {
+        *(volatile int *)flag = 1;
+        if (a.err) atomicExch(a.err, 1);
     };
-    // nearest upsampling: halo pixel (r, p) of the fine grid takes coarse
-    // pixel ((y + r - 1) >> 1, (x0 + p - 1) >> 1), relative to the staged rows
-    auto expand = [&](int i, int st) {
-        const Where w = where(i);
-        unsigned char *As = stg + st * STG;
-        const unsigned char *U = As + RA_BYTES;
-        const int cy0 = (w.y - 1) >> 1, cx0 = (w.x0 >> 1) - 1;
-        const uint32_t hbase = smem_u32(As);
-        for (int idx = tid; idx < 4 * 3 * RHALO; idx += ROW_THREADS) {
-            const int qq = idx & 3, pix = idx >> 2;
-            const int r = pix / RHALO, p = pix - r * RHALO;
-            const int cr = ((w.y + r - 1) >> 1) - cy0, cp = ((w.x0 + p - 1) >> 1) - cx0;
-            const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // the 64-byte swizzle of this row
-            *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
-                *reinterpret_cast<const uint4 *>(U + (cr * 66 + cp) * 64 + qq * 16);
-        }
-    };
-    auto epilogue = [&](int i) {
-        const int t = tile_of(i);
-        const uint32_t acc = tmem + (uint32_t)((i & 1) * BN);
-        // warp w reads accumulator lanes 32 (w % 4) .. + 31 (its pixels), column half w / 4
-        const size_t row = (size_t)t * RW + (warp & 3) * 32 + lane;
-        const int c_begin = (warp >> 2) * (BN / 2);
-#pragma unroll 1
-        for (int c = c_begin; c < c_begin + BN / 2; c += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(acc + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            store_row16(a, row, n0 + c, r);
-        }
-        tc_fence_before();  // the reads are ordered before the next barrier (buffer reuse)
-    };
+    auto stopped = [&]() { return *(volatile int *)flag != 0; };
 
-    bool bad = false, wdone = !wres || njobs == 0;
-    int issued = 0, consumed = 0;  // jobs whose copies thread 0 issued / that have landed
-    if (tid == 0) {
-        if (!wdone) {
-            mbar_expect_tx(wfull, WB);
-            bulk_g2s(wsm, wnt, WB, wfull);
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            if (wres && njobs > 0) {
+                mbar_expect_tx(wfull, WB);
+                bulk_g2s(wsm, wnt, WB, wfull);
+            }
+            int j = 0;
+            for (; j < njobs && !stopped(); ++j) {
+                const int st = j % S;
+                if (j >= S && !mbar_wait(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+                    give_up();
+                    break;
+                }
+                const int i = j / kchunks, kc = j - i * kchunks;
+                const Where w = where(i);
+                unsigned char *As = stg + st * STG;
+                const bool direct = kc * 32 < a.c0;
+                mbar_expect_tx(&full[st], (direct ? RHALO_TX : RU_TX) + (wres ? 0 : WTILE));
+                if (direct)
+                    tma_load_4d(As, &tmx, kc * 32, w.x0 - 1, w.y - 1, w.b, &full[st]);
+                else
+                    tma_load_4d(As + RA_BYTES, &tmu, kc * 32 - a.c0, (w.x0 >> 1) - 1, (w.y - 1) >> 1, w.b,
+                                &full[st]);
+                if (!wres)
+                    bulk_g2s(As + RA_BYTES + (plan.ux ? RU_BYTES : 0), wnt + (size_t)kc * (WTILE / 2), WTILE,
+                             &full[st]);
+            }
+            // copies in flight land before the CTA may end: the last S issued
+            for (int jb = j - 1; jb >= 0 && jb >= j - S; --jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
+            if (wres && njobs > 0) mbar_wait(wfull, 0, DRAIN_LIMIT_NS);
         }
-        for (int p = 0; p < S - 1 && p < njobs; ++p) load_job(p, p);
-        issued = S - 1 < njobs ? S - 1 : njobs;
-    }
-    if (!wdone) {
-        const bool ok = mbar_wait(wfull, 0, WAIT_LIMIT_NS);
-        bad = __syncthreads_or(!ok);
-        wdone = !bad;
-    }
-    for (int j = 0; j < njobs && !bad; ++j) {
-        const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
-        const bool okf = mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
-        if (okf && kc * 32 >= a.c0) expand(i, st);
-        fence_proxy_async();  // expanded halo (generic writes), for the tensor cores' reads
-        tc_fence_before();
-        if (__syncthreads_or(!okf || *flag)) {
-            bad = true;
-            break;
-        }
-        ++consumed;
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t As = smem_u32(stg + st * STG);
-            const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES + (plan.ux ? RU_BYTES : 0);
-            const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            bool ok = !(wres && njobs > 0) || mbar_wait(wfull, 0, WAIT_LIMIT_NS);
+            if (!ok) give_up();
+            for (int j = 0; ok && j < njobs && !stopped(); ++j) {
+                const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
+                const uint32_t par = (j / S) & 1;
+                ok = mbar_wait(&full[st], par, WAIT_LIMIT_NS) && mbar_wait(&expd[st], par, WAIT_LIMIT_NS);
+                if (ok && kc == 0 && i >= 2) ok = mbar_wait(&acce[i & 1], ((i - 2) >> 1) & 1, WAIT_LIMIT_NS);
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t As = smem_u32(stg + st * STG);
+                const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES + (plan.ux ? RU_BYTES : 0);
+                const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
 #pragma unroll 1
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-                const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 64;
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
+                    const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 64;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint64_t ad = umma_desc_sw64(a0 + h * 32, 512);
-                    const uint64_t bd = umma_desc(Bs + tap * BN * 64 + h * 256, 128, 512);
-                    const uint32_t accum = (kc > 0 || tap > 0 || h > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                        "l"(ad), "l"(bd), "r"(umma_idesc(RW, BN)), "r"(accum)
-                        : "memory");
+                    for (int h = 0; h < 2; ++h) {
+                        const uint64_t ad = umma_desc_sw64(a0 + h * 32, 512);
+                        const uint64_t bd = umma_desc(Bs + tap * BN * 64 + h * 256, 128, 512);
+                        const uint32_t accum = (kc > 0 || tap > 0 || h > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(umma_idesc(RW, BN)), "r"(accum)
+                            : "memory");
+                    }
                 }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&done[st]))
-                         : "memory");
-            if (kc == kchunks - 1)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_u32(&accbar[i & 1]))
+                                 smem_u32(&done[st]))
                              : "memory");
-            // refill: job j + S - 1 goes into the stage of job j - 1 once its
-            // MMAs have read it
-            const int nj = j + S - 1;
-            if (nj < njobs) {
-                bool ok = true;
-                if (j >= 1) ok = mbar_wait(&done[(j - 1) % S], ((j - 1) / S) & 1, WAIT_LIMIT_NS);
-                if (ok) {
-                    load_job(nj, nj % S);
-                    ++issued;
-                } else {
-                    *flag = 1;
-                }
+                if (kc == kchunks - 1)
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            smem_u32(&accf[i & 1]))
+                        : "memory");
             }
-        }
-        if (kc == 0 && i >= 1) {
-            // tile i - 1 is complete once its last MMAs have committed
-            const bool ok = mbar_wait(&accbar[(i - 1) & 1], ((i - 1) >> 1) & 1, WAIT_LIMIT_NS);
-            if (__syncthreads_or(!ok)) {
-                bad = true;
-                break;
-            }
-            tc_fence_after();
-            epilogue(i - 1);
-        }
-    }
-    __syncthreads();
-    if (*flag) bad = true;
-    if (!bad && my_tiles > 0) {
-        const int i = my_tiles - 1;
-        const bool ok = mbar_wait(&accbar[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS);
-        bad = __syncthreads_or(!ok);
-        if (!bad) {
-            tc_fence_after();
-            epilogue(i);
-        }
-    }
-    if (bad) {
-        if (tid == 0 && a.err) atomicExch(a.err, 1);
-        // short waits for the copies still in flight into shared memory, and
-        // for every MMA this CTA issued (one last commit tracks them all),
-        // before the memory is released
-        if (!wdone) mbar_wait(wfull, 0, DRAIN_LIMIT_NS);
-        if (tid == 0)
-            for (int jb = consumed; jb < issued; ++jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
-        if (tid == 0)
+            // every MMA issued has completed before the tensor memory is freed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(drain))
                          : "memory");
-        mbar_wait(drain, 0, DRAIN_LIMIT_NS);
+            if (!mbar_wait(drain, 0, WAIT_LIMIT_NS)) give_up();
+        }
+    } else if (warp < 6) {
+        // ---------------- expansion (128 threads) ----------------
+        const int et = tid - 64, qq = et & 3;
+        for (int j = 0; j < njobs && !stopped(); ++j) {
+            const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
+            // the stage's previous job has been read by its MMAs (keeps the
+            // phases of expd[st] in step with the MMA warp)
+            if (j >= S && !mbar_wait(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+                give_up();
+                break;
+            }
+            if (kc * 32 >= a.c0) {
+                if (!mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
+                    give_up();
+                    break;
+                }
+                // nearest upsampling: halo pixel (r, p) takes coarse pixel
+                // ((y + r - 1) >> 1, (x0 + p - 1) >> 1); relative to the staged
+                // rows that is (cr(r), (p + 1) >> 1) since x0 is even
+                const Where w = where(i);
+                unsigned char *As = stg + st * STG;
+                const unsigned char *U = As + RA_BYTES;
+                const uint32_t hbase = smem_u32(As);
+                for (int r = 0; r < 3; ++r) {
+                    const int cr = ((w.y + r - 1) >> 1) - ((w.y - 1) >> 1);
+                    for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
+                        const int pix = r * RHALO + p;
+                        const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // 64-byte swizzle of the row
+                        *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
+                            *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
+                    }
+                }
+                fence_proxy_async();  // generic writes, for the tensor cores' reads
+            }
+            mbar_arrive(&expd[st]);
+        }
+    } else {
+        // ---------------- epilogue (128 threads) ----------------
+        const int ew = warp & 3;  // accumulator lanes 32 ew .. 32 ew + 31
+        for (int i = 0; i < my_tiles && !stopped(); ++i) {
+            if (!mbar_wait(&accf[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS)) {
+                give_up();
+                break;
+            }
+            tc_fence_after();
+            const uint32_t acc = tmem + (uint32_t)((i & 1) * BN) + ((uint32_t)(ew * 32) << 16);
+            const size_t row = (size_t)(tile0 + i * tstride) * RW + ew * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(r[c]), "=r"(r[c + 1]), "=r"(r[c + 2]), "=r"(r[c + 3]), "=r"(r[c + 4]), "=r"(r[c + 5]),
+                          "=r"(r[c + 6]), "=r"(r[c + 7]), "=r"(r[c + 8]), "=r"(r[c + 9]), "=r"(r[c + 10]),
+                          "=r"(r[c + 11]), "=r"(r[c + 12]), "=r"(r[c + 13]), "=r"(r[c + 14]), "=r"(r[c + 15])
+                        : "r"(acc + (uint32_t)(c0 + c)));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c0 + 32 >= BN) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce[i & 1]);  // the buffer may take tile i + 2
+                }
+                store_row16(a, row, n0 + c0, r);
+                store_row16(a, row, n0 + c0 + 16, r + 16);
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
