@@ -80,8 +80,9 @@ __device__ __forceinline__ int sw128(int row, int chunk) { return row * 128 + ((
 // m = pixel (b, y, x), k = (tap, channel), n = output channel.
 // ---------------------------------------------------------------------------
 struct ConvArgs {
-    const bf16 *x0, *x1;  // gathered input: x0 [B][H][W][c0]; x1 [B][H/2][W/2][c1] upsampled
-    int c0, c1;
+    const bf16 *x0, *x1;  // gathered input: x0 [B][H][W][c0]; x1 [B][H/2][W/2][c1] upsampled,
+    int c0, c1;           // or x1 [B][H][W][c1] when x1_full
+    int x1_full;
     int B, H, W, M;       // M = B H W
     int sign;             // +1: taps read pixel + d; -1: pixel - d
     const bf16 *w;        // [N][9][c0 + c1]
@@ -89,6 +90,7 @@ struct ConvArgs {
     int N;
     const float *bias;    // [N] or null
     bf16 *ybf;            // ReLU(C + bias) as BF16 [M][N], or null
+    bf16 *yup;            // the same, nearest-upsampled to [B][2H][2W][N] (the next decoder's input), or null
     float *yf;            // C as FP32 [M][N], or null
     int *err;             // set when a bounded wait gives up
 };
@@ -161,6 +163,19 @@ __device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n
         uint4 *d = reinterpret_cast<uint4 *>(a.ybf + row * a.N + n);
         d[0] = *reinterpret_cast<const uint4 *>(&h[0]);
         d[1] = *reinterpret_cast<const uint4 *>(&h[4]);
+        if (a.yup) {
+            const int x = (int)(row % a.W);
+            const size_t t = row / a.W;
+            const int y = (int)(t % a.H);
+            const size_t b = t / a.H;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint4 *u = reinterpret_cast<uint4 *>(
+                    a.yup + (((b * 2 * a.H + 2 * y + (k >> 1)) * 2 * a.W) + 2 * x + (k & 1)) * a.N + n);
+                u[0] = *reinterpret_cast<const uint4 *>(&h[0]);
+                u[1] = *reinterpret_cast<const uint4 *>(&h[4]);
+            }
+        }
     }
 }
 
@@ -226,6 +241,8 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
             if (v) {
                 if (ci < a.c0)
                     src = a.x0 + ((size_t)(ab[i] * a.H + yy) * a.W + xx) * a.c0 + ci;
+                else if (a.x1_full)
+                    src = a.x1 + ((size_t)(ab[i] * a.H + yy) * a.W + xx) * a.c1 + (ci - a.c0);
                 else
                     src = a.x1 + ((size_t)(ab[i] * (a.H >> 1) + (yy >> 1)) * (a.W >> 1) + (xx >> 1)) * a.c1 +
                           (ci - a.c0);
@@ -492,9 +509,11 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const Where w = where(i);
                 unsigned char *As = stg + st * STG;
                 const bool direct = kc * 32 < a.c0;
-                mbar_expect_tx(&full[st], (direct ? RHALO_TX : RU_TX) + (wres ? 0 : WTILE));
+                mbar_expect_tx(&full[st], (direct || a.x1_full ? RHALO_TX : RU_TX) + (wres ? 0 : WTILE));
                 if (direct)
                     tma_load_4d(As, &tmx, kc * 32, w.x0 - 1, w.y - 1, w.b, &full[st]);
+                else if (a.x1_full)
+                    tma_load_4d(As, &tmu, kc * 32 - a.c0, w.x0 - 1, w.y - 1, w.b, &full[st]);
                 else
                     tma_load_4d(As + RA_BYTES, &tmu, kc * 32 - a.c0, (w.x0 >> 1) - 1, (w.y - 1) >> 1, w.b,
                                 &full[st]);
@@ -566,7 +585,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 give_up();
                 break;
             }
-            if (kc * 32 >= a.c0) {
+            if (kc * 32 >= a.c0 && !a.x1_full) {
                 if (!mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
                     give_up();
                     break;
@@ -855,75 +874,130 @@ __global__ void loss_final_kernel(const double *part, int nblocks, double *out) 
 
 // head backward: dz = dL/dphi (1 - phi^2) with dL/dphi = 2 mask (phi - t) / n;
 // dd[p][c] = dz w[c]; gradients of the head weights and bias (block sums)
+// head backward: dz = d loss / d (w . d + b) per pixel, dd = dz w (input
+// gradient), and the head's weight and bias gradients.  One warp per pixel
+// (strided), lane c and c + 32 own channels c and c + 32 (C <= 64).
 __global__ void head_backward_kernel(const float *phi, const float *t, const float *mask, const double *stat,
                                      const bf16 *d, const float *wb, int C, long long P, float *dd,
                                      float *gwb) {
     const float inv_n = (float)(1.0 / stat[0]);
-    float acc[65];
-    for (int c = 0; c <= C; ++c) acc[c] = 0.f;
-    GRID_STRIDE(p, P) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const bool has0 = lane < C, has1 = lane + 32 < C;
+    const float w0 = has0 ? wb[lane] : 0.f, w1 = has1 ? wb[lane + 32] : 0.f;
+    float a0 = 0.f, a1 = 0.f, ab = 0.f;
+    for (long long p = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
         const float f = phi[p];
         const float dz = 2.f * mask[p] * (f - t[p]) * inv_n * (1.f - f * f);
-        for (int c = 0; c < C; ++c) {
-            dd[p * C + c] = dz * wb[c];
-            acc[c] += dz * __bfloat162float(d[p * C + c]);
+        if (has0) {
+            dd[p * C + lane] = dz * w0;
+            a0 += dz * __bfloat162float(d[p * C + lane]);
         }
-        acc[C] += dz;
+        if (has1) {
+            dd[p * C + lane + 32] = dz * w1;
+            a1 += dz * __bfloat162float(d[p * C + lane + 32]);
+        }
+        ab += dz;
     }
-    // warp sums, then one atomic per warp and value
-    for (int c = 0; c <= C; ++c) {
-        float v = acc[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(gwb + c, v);
-    }
+    if (has0) atomicAdd(gwb + lane, a0);
+    if (has1) atomicAdd(gwb + lane + 32, a1);
+    if (lane == 0) atomicAdd(gwb + C, ab);
 }
 
 // dz = g (h > 0), as BF16 (h: the ReLU output the gradient flows into)
+// dz = g where the forward activation h > 0, else 0 (BF16); 8 elements a thread
 __global__ void relu_mask_kernel(const float *g, const bf16 *h, bf16 *dz, long long n) {
-    GRID_STRIDE(i, n) dz[i] = __float2bfloat16_rn(__bfloat162float(h[i]) > 0.f ? g[i] : 0.f);
+    GRID_STRIDE(i, n / 8) {
+        const float4 g0 = reinterpret_cast<const float4 *>(g)[2 * i], g1 = reinterpret_cast<const float4 *>(g)[2 * i + 1];
+        const uint4 hv = reinterpret_cast<const uint4 *>(h)[i];
+        const uint32_t *hp = &hv.x;
+        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        uint4 o;
+        uint32_t *op = &o.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 hf = bf2_to_f2(hp[k]);
+            __nv_bfloat162 r = __floats2bfloat162_rn(hf.x > 0.f ? gv[2 * k] : 0.f, hf.y > 0.f ? gv[2 * k + 1] : 0.f);
+            op[k] = *reinterpret_cast<uint32_t *>(&r);
+        }
+        reinterpret_cast<uint4 *>(dz)[i] = o;
+    }
 }
 
 // decoder concat backward: de [P][cs] += dcat[:, :cs]; dd (coarse
 // [B][H/2][W/2][cu]) = sum over the 2x2 block of dcat[:, cs:]
+// gradient of concat(e, up(d)): de += first cs channels; dd = the last cu
+// channels summed over each 2x2 block (nearest-upsampling backward); 4
+// channels a thread
 __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, int H, int W, float *de,
                                     float *dd) {
     const int ct = cs + cu;
-    GRID_STRIDE(i, (long long)B * H * W * cs) {
-        const long long p = i / cs;
-        const int c = (int)(i % cs);
-        de[i] += dcat[p * ct + c];
+    GRID_STRIDE(i, (long long)B * H * W * (cs / 4)) {
+        const long long p = i / (cs / 4);
+        const int c = (int)(i - p * (cs / 4)) * 4;
+        float4 *o = reinterpret_cast<float4 *>(de + p * cs + c);
+        const float4 v = *reinterpret_cast<const float4 *>(dcat + p * ct + c);
+        float4 r = *o;
+        r.x += v.x;
+        r.y += v.y;
+        r.z += v.z;
+        r.w += v.w;
+        *o = r;
     }
     const int h2 = H / 2, w2 = W / 2;
-    GRID_STRIDE(i, (long long)B * h2 * w2 * cu) {
-        const int c = (int)(i % cu);
-        long long t = i / cu;
+    GRID_STRIDE(i, (long long)B * h2 * w2 * (cu / 4)) {
+        const int c = (int)(i % (cu / 4)) * 4;
+        long long t = i / (cu / 4);
         const int x = (int)(t % w2);
         t /= w2;
         const int y = (int)(t % h2);
         const int b = (int)(t / h2);
-        float s = 0.f;
+        float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int a = 0; a < 2; ++a)
-            for (int e = 0; e < 2; ++e)
-                s += dcat[(((long long)b * H + 2 * y + a) * W + 2 * x + e) * ct + cs + c];
-        dd[i] = s;
+            for (int e = 0; e < 2; ++e) {
+                const float4 v = *reinterpret_cast<const float4 *>(
+                    dcat + (((long long)b * H + 2 * y + a) * W + 2 * x + e) * ct + cs + c);
+                s4.x += v.x;
+                s4.y += v.y;
+                s4.z += v.z;
+                s4.w += v.w;
+            }
+        *reinterpret_cast<float4 *>(dd + (((long long)b * h2 + y) * w2 + x) * cu + c) = s4;
     }
 }
 
 // encoder pooling backward: de_fine [B][H][W][C] += dx_coarse / 4
+// de += 2x2 average-pooling backward of dx; 4 channels a thread
 __global__ void pool_backward_add_kernel(const float *dx, int B, int H, int W, int C, float *de) {
-    GRID_STRIDE(i, (long long)B * H * W * C) {
-        const int c = (int)(i % C);
-        long long t = i / C;
+    GRID_STRIDE(i, (long long)B * H * W * (C / 4)) {
+        const int c = (int)(i % (C / 4)) * 4;
+        long long t = i / (C / 4);
         const int x = (int)(t % W);
         t /= W;
         const int y = (int)(t % H);
         const int b = (int)(t / H);
-        de[i] += 0.25f * dx[(((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c];
+        const float4 v = *reinterpret_cast<const float4 *>(dx + (((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c);
+        float4 *o = reinterpret_cast<float4 *>(de + i * 4);
+        float4 r = *o;
+        r.x += 0.25f * v.x;
+        r.y += 0.25f * v.y;
+        r.z += 0.25f * v.z;
+        r.w += 0.25f * v.w;
+        *o = r;
     }
 }
 
 __global__ void add_kernel(float *a, const float *b, long long n) {
-    GRID_STRIDE(i, n) a[i] += b[i];
+    GRID_STRIDE(i, n / 4) {
+        float4 *o = reinterpret_cast<float4 *>(a) + i;
+        const float4 v = reinterpret_cast<const float4 *>(b)[i];
+        float4 r = *o;
+        r.x += v.x;
+        r.y += v.y;
+        r.z += v.z;
+        r.w += v.w;
+        *o = r;
+    }
 }
 
 // FP32 master weights [co][3][3][ci] -> BF16 [co][9][cpad] (forward) and
@@ -969,16 +1043,33 @@ __global__ void grad_pack_kernel(const float *dw, int co, int ci, int cpad, floa
 }
 
 // per-channel sums of a BF16 [P][C] gradient (bias gradient)
+// gb[c] += sum over pixels of dz[p][c]: a thread sums 8 channels of a
+// strided set of pixels, the block reduces by channel in shared memory
 __global__ void bias_grad_kernel(const bf16 *dz, long long P, int C, float *gb) {
-    // thread handles channel threadIdx.x % C over a strided set of pixels
-    const int c = threadIdx.x % C;
-    const int lanes = blockDim.x / C;
-    const int sub = threadIdx.x / C;
-    if (sub >= lanes) return;
-    float s = 0.f;
-    for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes)
-        s += __bfloat162float(dz[p * C + c]);
-    atomicAdd(gb + c, s);
+    __shared__ float part[256 * 8];
+    const int g8 = C / 8;
+    const int lanes = blockDim.x / g8;  // pixels in flight per block
+    const int grp = threadIdx.x % g8, sub = threadIdx.x / g8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (sub < lanes)
+        for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes) {
+            const uint4 v = reinterpret_cast<const uint4 *>(dz + p * C)[grp];
+            const uint32_t *vp = &v.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = bf2_to_f2(vp[k]);
+                acc[2 * k] += f.x;
+                acc[2 * k + 1] += f.y;
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[threadIdx.x * 8 + k] = acc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float sum = 0.f;
+        for (int l = 0; l < lanes; ++l) sum += part[(l * g8 + c / 8) * 8 + (c & 7)];
+        atomicAdd(gb + c, sum);
+    }
 }
 
 // Adam (bias-corrected), in place on the FP32 master parameters
@@ -1025,6 +1116,7 @@ struct mclbm_unet {
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     long long adam_t = 0;
     std::vector<bf16 *> a_in, e_ha, e_out, d_ha, d_out;  // per level
+    std::vector<bf16 *> up;  // up[0]: d_1 (or e_1) upsampled to level 0, the finest decoder's input
     std::vector<float *> de;                              // per level
     float *phi = nullptr, *s1 = nullptr, *s2 = nullptr, *dd = nullptr;
     bf16 *z = nullptr;
@@ -1152,7 +1244,7 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const RowPlan plan = row_plan(BN, (a.c0 + a.c1) / 32, a.c1 > 0 ? 1 : 0);
+    const RowPlan plan = row_plan(BN, (a.c0 + a.c1) / 32, a.c1 > 0 && !a.x1_full ? 1 : 0);
     if (plan.stages < 2) return cudaErrorInvalidValue;
     // resident CTAs per SM: 228 KB of shared memory (1 KB reserved per CTA)
     // and 512 tensor-memory columns (the occupancy query was seen to answer
@@ -1173,7 +1265,9 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     CUtensorMap tmx, tmu;
     cudaError_t e = nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmx);
     if (e == cudaSuccess)
-        e = a.c1 > 0 ? nhwc_map(a.x1, a.B, a.H >> 1, a.W >> 1, a.c1, 66, 2, false, &tmu) : nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmu);
+        e = a.c1 == 0   ? nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmu)
+            : a.x1_full ? nhwc_map(a.x1, a.B, a.H, a.W, a.c1, RHALO, 3, true, &tmu)
+                        : nhwc_map(a.x1, a.B, a.H >> 1, a.W >> 1, a.c1, 66, 2, false, &tmu);
     if (e != cudaSuccess) return e;
     conv_row_kernel<BN><<<(int)grid, ROW_THREADS, plan.smem, u.stream>>>(a, plan, a.wp, tmx, tmu);
     count_launch();
@@ -1219,16 +1313,19 @@ cudaError_t launch_wgrad(const mclbm_unet &u, WgradArgs a) {
 struct In {
     const bf16 *x0, *x1;
     int c0, c1;
+    int x1_full = 0;  // x1 at the resolution of x0 (an upsampled copy), else half
 };
 
 // forward of conv layer li on input `in` at (B, H, W): y = ReLU(conv + b)
-cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W, bf16 *y) {
+cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W, bf16 *y, bf16 *yup = nullptr) {
     const UnetLayer &L = u.layers[li];
     ConvArgs a{};
     a.x0 = in.x0;
     a.x1 = in.x1;
     a.c0 = in.c0;
     a.c1 = in.c1;
+    a.x1_full = in.x1_full;
+    a.yup = yup;
     a.B = B;
     a.H = H;
     a.W = W;
@@ -1325,17 +1422,25 @@ cudaError_t forward(mclbm_unet &u, int B, int H, int W) {
         const In ina{u.a_in[l], nullptr, l == 0 ? UNET_PAD0 : ch(u, l - 1), 0};
         if ((e = conv_forward(u, 2 * l, ina, B, h, w, u.e_ha[l])) != cudaSuccess) break;
         const In inb{u.e_ha[l], nullptr, ch(u, l), 0};
-        e = conv_forward(u, 2 * l + 1, inb, B, h, w, u.e_out[l]);
+        // the coarsest level writes its output upsampled too when the first
+        // decoder is the finest level
+        e = conv_forward(u, 2 * l + 1, inb, B, h, w, u.e_out[l], l == 1 && Lv == 2 ? u.up[0] : nullptr);
     }
     // decoder, coarse to fine
     int li = 2 * Lv;
     for (int l = Lv - 2; l >= 0 && e == cudaSuccess; --l, li += 2) {
         const int h = H >> l, w = W >> l;
+        // concat(e_l, nearest-upsampled d_{l+1}).  At the finest level the
+        // producer of d_1 also writes it upsampled (4x its output, but the
+        // convolution then stages it like a direct input); coarser levels
+        // expand the coarse rows in shared memory, where the extra writes
+        // would cost more than they save
         const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
-        const In ina{u.e_out[l], coarse, ch(u, l), ch(u, l + 1)};
+        const In ina = l == 0 ? In{u.e_out[0], u.up[0], ch(u, 0), ch(u, 1), 1}
+                              : In{u.e_out[l], coarse, ch(u, l), ch(u, l + 1)};
         if ((e = conv_forward(u, li, ina, B, h, w, u.d_ha[l])) != cudaSuccess) break;
         const In inb{u.d_ha[l], nullptr, ch(u, l), 0};
-        e = conv_forward(u, li + 1, inb, B, h, w, u.d_out[l]);
+        e = conv_forward(u, li + 1, inb, B, h, w, u.d_out[l], l == 1 ? u.up[0] : nullptr);
     }
     if (e != cudaSuccess) return e;
     const UnetLayer &hd = u.layers.back();
@@ -1353,7 +1458,7 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
     cudaError_t e = cudaMemsetAsync(u.grad + hd.off, 0, (u.base + 1) * sizeof(float), u.stream);
     if (e != cudaSuccess) return e;
     const bf16 *d0 = Lv > 1 ? u.d_out[0] : u.e_out[0];
-    head_backward_kernel<<<blocks_for(P), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
+    head_backward_kernel<<<blocks_for(P * 32 < 152LL * 8 * 256 ? P * 32 : 152LL * 8 * 256), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
                                                               u.theta + hd.off, u.base, P, u.dd,
                                                               u.grad + hd.off);
     count_launch();
@@ -1367,25 +1472,25 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         const long long Pl = (long long)B * h * w;
         const int cl = ch(u, l), cu = ch(u, l + 1);
         const int li = 2 * Lv + 2 * (Lv - 2 - l);
-        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.dd, u.d_out[l], u.z, Pl * cl);
+        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.dd, u.d_out[l], u.z, Pl * cl);
         count_launch();
         if ((e = conv_backward(u, li + 1, In{u.d_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
             return e;
-        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s2, u.d_ha[l], u.z, Pl * cl);
+        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.s2, u.d_ha[l], u.z, Pl * cl);
         count_launch();
         const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
         if ((e = conv_backward(u, li, In{u.e_out[l], coarse, cl, cu}, B, h, w, u.z, u.s1)) != cudaSuccess)
             return e;
-        split_concat_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l], u.dd);
+        split_concat_kernel<<<blocks_for(Pl * cl / 4), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l], u.dd);
         count_launch();
     }
     if (Lv > 1) {
         const long long n = (P >> (2 * (Lv - 1))) * ch(u, Lv - 1);
-        add_kernel<<<blocks_for(n), 256, 0, u.stream>>>(u.de[Lv - 1], u.dd, n);
+        add_kernel<<<blocks_for(n / 4), 256, 0, u.stream>>>(u.de[Lv - 1], u.dd, n);
         count_launch();
     } else {
         const long long n = P * ch(u, 0);
-        add_kernel<<<blocks_for(n), 256, 0, u.stream>>>(u.de[0], u.dd, n);
+        add_kernel<<<blocks_for(n / 4), 256, 0, u.stream>>>(u.de[0], u.dd, n);
         count_launch();
     }
     // encoder, coarse to fine
@@ -1393,11 +1498,11 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         const int h = H >> l, w = W >> l;
         const long long Pl = (long long)B * h * w;
         const int cl = ch(u, l);
-        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.de[l], u.e_out[l], u.z, Pl * cl);
+        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.de[l], u.e_out[l], u.z, Pl * cl);
         count_launch();
         if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
             return e;
-        relu_mask_kernel<<<blocks_for(Pl * cl), 256, 0, u.stream>>>(u.s2, u.e_ha[l], u.z, Pl * cl);
+        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.s2, u.e_ha[l], u.z, Pl * cl);
         count_launch();
         const int cin = l == 0 ? UNET_PAD0 : ch(u, l - 1);
         if ((e = conv_backward(u, 2 * l, In{u.a_in[l], nullptr, cin, 0}, B, h, w, u.z, l > 0 ? u.s1 : nullptr)) !=
@@ -1405,7 +1510,7 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
             return e;
         if (l > 0) {
             const int cp = ch(u, l - 1);
-            pool_backward_add_kernel<<<blocks_for(4 * Pl * cp), 256, 0, u.stream>>>(u.s1, B, 2 * h, 2 * w, cp,
+            pool_backward_add_kernel<<<blocks_for(Pl * cp), 256, 0, u.stream>>>(u.s1, B, 2 * h, 2 * w, cp,
                                                                                   u.de[l - 1]);
             count_launch();
         }
@@ -1563,6 +1668,7 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     u->e_out.assign(levels, nullptr);
     u->d_ha.assign(levels, nullptr);
     u->d_out.assign(levels, nullptr);
+    u->up.assign(levels, nullptr);
     u->de.assign(levels, nullptr);
     for (int l = 0; l < levels; ++l) {
         const long long Pl = P >> (2 * l);
@@ -1574,6 +1680,7 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
         if (l < levels - 1) {
             A((void **)&u->d_ha[l], (size_t)Pl * cl * 2);
             A((void **)&u->d_out[l], (size_t)Pl * cl * 2);
+            if (l == 0) A((void **)&u->up[l], (size_t)Pl * 2 * cl * 2);
         }
     }
     A((void **)&u->phi, P * 4);
