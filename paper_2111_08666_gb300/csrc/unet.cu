@@ -139,8 +139,9 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // epilogue of one pixel row and 16 accumulator columns n..n+15: FP32 C, or
-// BF16 ReLU(C + bias)
-__device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n, const uint32_t r[16]) {
+// BF16 ReLU(C + bias) with bias = the 16 values for these columns (or null)
+__device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n, const uint32_t r[16],
+                                            const float *bias) {
     float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
@@ -154,9 +155,9 @@ __device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             float v0 = v[2 * k], v1 = v[2 * k + 1];
-            if (a.bias) {
-                v0 += a.bias[n + 2 * k];
-                v1 += a.bias[n + 2 * k + 1];
+            if (bias) {
+                v0 += bias[2 * k];
+                v1 += bias[2 * k + 1];
             }
             h[k] = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
         }
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const ConvArgs a) {
                 : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int n = n0 + c;
-            if (row < a.M && n < a.N) store_row16(a, (size_t)row, n, r);
+            if (row < a.M && n < a.N) store_row16(a, (size_t)row, n, r, a.bias ? a.bias + n : nullptr);
         }
     }
     tc_fence_before();
@@ -380,7 +381,7 @@ __host__ __device__ inline int row_stage_bytes(int BN, int wres, int ux) {
     return RA_BYTES + (ux ? RU_BYTES : 0) + (wres ? 0 : 9 * BN * 64);
 }
 __host__ __device__ inline int row_smem(int BN, int kchunks, int wres, int ux, int stages) {
-    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres, ux) + 256;
+    return (wres ? row_weight_bytes(BN, kchunks) : 0) + stages * row_stage_bytes(BN, wres, ux) + 256 + 4 * BN;
 }
 
 // N tile of the row kernel for N output channels (0: none)
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     uint64_t *wfull = full + 16, *drain = full + 17;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 18);
     int *flag = reinterpret_cast<int *>(full + 19);  // some role gave up waiting
+    float *sbias = reinterpret_cast<float *>(full + 20);  // this N tile's biases [BN]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntn = a.N / BN;
     const int nt = blockIdx.x % ntn, n0 = nt * BN;
@@ -473,6 +475,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         *flag = 0;
         fence_mbar_init();
     }
+    if (a.bias)
+        for (int c = tid; c < BN; c += ROW_THREADS) sbias[c] = a.bias[n0 + c];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -640,8 +644,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acce[i & 1]);  // the buffer may take tile i + 2
                 }
-                store_row16(a, row, n0 + c0, r);
-                store_row16(a, row, n0 + c0 + 16, r + 16);
+                store_row16(a, row, n0 + c0, r, a.bias ? sbias + c0 : nullptr);
+                store_row16(a, row, n0 + c0 + 16, r + 16, a.bias ? sbias + c0 + 16 : nullptr);
             }
         }
     }
