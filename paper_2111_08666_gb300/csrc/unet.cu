@@ -413,6 +413,28 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const void *tmap, int c0,
 //                 expanded[st] for every job keeps the phases in step)
 //   warps 6-9     epilogue: accumulator -> registers (tcgen05.ld), frees the
 //                 buffer, bias + ReLU + stores (warp w reads lanes 32 (w % 4)..)
+// bounded wait whose polls let the hardware suspend the thread until the
+// phase completes (up to 0.1 ms a poll), so that waiting roles take no issue
+// slots from the working ones
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test_sleep(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test_sleep(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
 constexpr int ROW_THREADS = 320;
 constexpr int ROW_EXP = 128;  // expansion threads
 
@@ -505,7 +527,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             int j = 0;
             for (; j < njobs && !stopped(); ++j) {
                 const int st = j % S;
-                if (j >= S && !mbar_wait(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+                if (j >= S && !mbar_wait_sleep(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
                     give_up();
                     break;
                 }
@@ -526,19 +548,23 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                              &full[st]);
             }
             // copies in flight land before the CTA may end: the last S issued
-            for (int jb = j - 1; jb >= 0 && jb >= j - S; --jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
-            if (wres && njobs > 0) mbar_wait(wfull, 0, DRAIN_LIMIT_NS);
+            for (int jb = j - 1; jb >= 0 && jb >= j - S; --jb) mbar_wait_sleep(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
+            if (wres && njobs > 0) mbar_wait_sleep(wfull, 0, DRAIN_LIMIT_NS);
         }
     } else if (warp == 1) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
-            bool ok = !(wres && njobs > 0) || mbar_wait(wfull, 0, WAIT_LIMIT_NS);
+            bool ok = !(wres && njobs > 0) || mbar_wait_sleep(wfull, 0, WAIT_LIMIT_NS);
             if (!ok) give_up();
+            uint32_t xpar = 0;  // bit st: parity of the upsampled-coarse jobs seen on stage st (expd phases)
             for (int j = 0; ok && j < njobs && !stopped(); ++j) {
                 const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
-                const uint32_t par = (j / S) & 1;
-                ok = mbar_wait(&full[st], par, WAIT_LIMIT_NS) && mbar_wait(&expd[st], par, WAIT_LIMIT_NS);
-                if (ok && kc == 0 && i >= 2) ok = mbar_wait(&acce[i & 1], ((i - 2) >> 1) & 1, WAIT_LIMIT_NS);
+                ok = mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
+                if (ok && plan.ux && kc * 32 >= a.c0) {
+                    ok = mbar_wait_sleep(&expd[st], (xpar >> st) & 1u, WAIT_LIMIT_NS);
+                    xpar ^= 1u << st;
+                }
+                if (ok && kc == 0 && i >= 2) ok = mbar_wait_sleep(&acce[i & 1], ((i - 2) >> 1) & 1, WAIT_LIMIT_NS);
                 if (!ok) {
                     give_up();
                     break;
@@ -576,49 +602,52 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(drain))
                          : "memory");
-            if (!mbar_wait(drain, 0, WAIT_LIMIT_NS)) give_up();
+            if (!mbar_wait_sleep(drain, 0, WAIT_LIMIT_NS)) give_up();
         }
     } else if (warp < 6) {
         // ---------------- expansion (128 threads) ----------------
+        // expands the jobs of an upsampled-coarse chunk; expd[st] completes once
+        // per such job on stage st.  It follows done[st] for every job, so that
+        // no parity wait here is ever two phases ahead (a wait for parity P
+        // passes whenever the barrier is not in a phase of parity P)
         const int et = tid - 64, qq = et & 3;
-        for (int j = 0; j < njobs && !stopped(); ++j) {
+        for (int j = 0; plan.ux && j < njobs && !stopped(); ++j) {
             const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
-            // the stage's previous job has been read by its MMAs (keeps the
-            // phases of expd[st] in step with the MMA warp)
-            if (j >= S && !mbar_wait(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+            // the stage's previous job has been read by its MMAs
+            if (j >= S && !mbar_wait_sleep(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
                 give_up();
                 break;
             }
-            if (kc * 32 >= a.c0 && !a.x1_full) {
-                if (!mbar_wait(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
-                    give_up();
-                    break;
-                }
-                // nearest upsampling: halo pixel (r, p) takes coarse pixel
-                // ((y + r - 1) >> 1, (x0 + p - 1) >> 1); relative to the staged
-                // rows that is (cr(r), (p + 1) >> 1) since x0 is even
-                const Where w = where(i);
-                unsigned char *As = stg + st * STG;
-                const unsigned char *U = As + RA_BYTES;
-                const uint32_t hbase = smem_u32(As);
-                for (int r = 0; r < 3; ++r) {
-                    const int cr = ((w.y + r - 1) >> 1) - ((w.y - 1) >> 1);
-                    for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
-                        const int pix = r * RHALO + p;
-                        const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // 64-byte swizzle of the row
-                        *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
-                            *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
-                    }
-                }
-                fence_proxy_async();  // generic writes, for the tensor cores' reads
+            if (kc * 32 < a.c0) continue;
+            // this job's coarse rows have landed
+            if (!mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
+                give_up();
+                break;
             }
+            // nearest upsampling: halo pixel (r, p) takes coarse pixel
+            // ((y + r - 1) >> 1, (x0 + p - 1) >> 1); relative to the staged
+            // rows that is (cr(r), (p + 1) >> 1) since x0 is even
+            const Where w = where(i);
+            unsigned char *As = stg + st * STG;
+            const unsigned char *U = As + RA_BYTES;
+            const uint32_t hbase = smem_u32(As);
+            for (int r = 0; r < 3; ++r) {
+                const int cr = ((w.y + r - 1) >> 1) - ((w.y - 1) >> 1);
+                for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
+                    const int pix = r * RHALO + p;
+                    const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // 64-byte swizzle of the row
+                    *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
+                        *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
+                }
+            }
+            fence_proxy_async();  // generic writes, for the tensor cores' reads
             mbar_arrive(&expd[st]);
         }
     } else {
         // ---------------- epilogue (128 threads) ----------------
         const int ew = warp & 3;  // accumulator lanes 32 ew .. 32 ew + 31
         for (int i = 0; i < my_tiles && !stopped(); ++i) {
-            if (!mbar_wait(&accf[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS)) {
+            if (!mbar_wait_sleep(&accf[i & 1], (i >> 1) & 1, WAIT_LIMIT_NS)) {
                 give_up();
                 break;
             }

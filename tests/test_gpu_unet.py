@@ -34,11 +34,12 @@ def _x8(x4):
 
 
 # widths below 128 take the pixel-gather kernel, multiples of 128 the
-# persistent row-tile kernel (the last cases: 512, 256 and 128 over three
-# levels); max_ctas = 3 makes each of its CTAs walk up to 11 tiles, through
-# both accumulator buffers and every stage of its ring
+# persistent row-tile kernel (512, 256 and 128 over three levels; 1024 to 128
+# over four, whose level-2 decoder streams its weights through a two-stage
+# ring and expands the upsampled input); a small max_ctas makes each CTA walk
+# many tiles, through both accumulator buffers and every stage of its ring
 @pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 32, 48, 0), (4, 1, 64, 32, 0), (3, 1, 8, 512, 0),
-                                                   (3, 1, 8, 512, 3)])
+                                                   (3, 1, 8, 512, 3), (4, 1, 8, 1024, 0), (4, 1, 8, 1024, 2)])
 def test_forward_matches_reference(levels, b, h, w, max_ctas):
     base = 32
     theta, x4, _, _ = _problem(levels, base, b, h, w, seed=levels)
