@@ -29,7 +29,8 @@ class Params(C.Structure):
                 ("gx", C.c_double), ("gy", C.c_double),
                 ("rho_in1", C.c_double), ("rho_out2", C.c_double),
                 ("open_x", C.c_int), ("periodic_y", C.c_int),
-                ("vel_shift", C.c_int), ("pad", C.c_int)]
+                ("vel_shift", C.c_int), ("bc_set", C.c_int),
+                ("rho_in2", C.c_double), ("rho_out1", C.c_double)]
 
 
 def build(force: bool = False) -> Path:
@@ -110,7 +111,8 @@ class Oracle:
     def __init__(self, solid: np.ndarray, xi: np.ndarray, *, nu1: float, nu2: float,
                  g_coh: float = 3.5, g_ads: float | None = None, gx: float = 0.0,
                  gy: float = 0.0, rho_in1: float = -1.0, rho_out2: float = -1.0,
-                 periodic_y: bool = False, vel_shift: bool = True):
+                 periodic_y: bool = False, vel_shift: bool = True, bc_set: int = 3,
+                 rho_in2: float = 0.0, rho_out1: float = 0.0):
         self.solid = np.ascontiguousarray(solid, dtype=np.uint8)
         self.ny, self.nx = self.solid.shape
         self.xi = np.ascontiguousarray(xi, dtype=np.float32)
@@ -118,12 +120,20 @@ class Oracle:
         self.p = Params(self.nx, self.ny, nu1, nu2, g_coh,
                         g_coh if g_ads is None else g_ads, gx, gy,
                         rho_in1, rho_out2, int(open_x), int(periodic_y),
-                        int(vel_shift), 0)
+                        int(vel_shift), int(bc_set), rho_in2, rho_out1)
         self.f = np.zeros((2, 9, self.ny, self.nx))
-        self.d5 = np.zeros((3, self.ny))
+        # frozen boundary values: component 1's outlet f_{3,6,7} (Eq. 26, rows
+        # 0-2) and component 2's inlet f_{1,5,8} (Eq. 27, rows 3-5)
+        self.d5 = np.zeros((6, self.ny))
         self.ux = np.zeros((self.ny, self.nx))
         self.uy = np.zeros((self.ny, self.nx))
         self.steps = 0
+
+    def set_bc(self, bc_set: int, rho_in2: float = 0.0, rho_out1: float = 0.0) -> None:
+        """Inlet/outlet treatment of Sec. 2.3: Set-1, -2 or -3; Set-1 also
+        fixes component 2 at the inlet (rho_in2) and component 1 at the
+        outlet (rho_out1)."""
+        self.p.bc_set, self.p.rho_in2, self.p.rho_out1 = int(bc_set), rho_in2, rho_out1
 
     def set_pressure_bc(self, rho_in1: float, rho_out2: float) -> None:
         self.p.rho_in1, self.p.rho_out2 = rho_in1, rho_out2

@@ -26,9 +26,18 @@
  *    P = (rho1 + rho2)/3 + (G/3) rho1 rho2.
  *  - Eq. 26 (component 1 at the outlet): the missing f_{3,6,7} after
  *    streaming equal their pre-collision values of the previous step, which
- *    makes them constant from initialisation (array d5).
- *  - Eq. 28 (component 2 at the inlet): the missing f_{1,5,8} keep their own
- *    post-collision values.
+ *    makes them constant from initialisation (array d5, rows 0-2).
+ *  - Eq. 27 (component 2 at the inlet, Set-2) is read the same way: the
+ *    missing f_{1,5,8} are constant from initialisation (d5, rows 3-5).
+ *  - Eq. 28 (component 2 at the inlet, Set-3): the missing f_{1,5,8} keep
+ *    their own post-collision values.
+ *  - The three treatments of Sec. 2.3, selected by bc_set:
+ *      Set-1: Zou-He for both components at both ends, the other component's
+ *             density (rho_in2 at the inlet, rho_out1 at the outlet) fixed too;
+ *      Set-2: Zou-He for component 1 at the inlet and component 2 at the
+ *             outlet; Eq. 26 at the outlet and Eq. 27 at the inlet for the
+ *             other component;
+ *      Set-3 (the paper's, the default): as Set-2 but Eq. 28 at the inlet.
  *  - Zou-He (Eqs. 18-25) prescribes zero tangential velocity; u_x follows
  *    from the prescribed density.  Directions whose source lies beyond the
  *    open x ends are "missing"; directions whose source is solid are filled
@@ -64,7 +73,9 @@ typedef struct {
     int open_x;             /* 1: Set-3 at x=0 and x=nx-1; 0: periodic x */
     int periodic_y;         /* 1: periodic y; 0: rows 0 and ny-1 are solid */
     int vel_shift;          /* 1: u^eq carries +F/2 (default reading) */
-    int pad;
+    int bc_set;             /* 1, 2 or 3 (0 counts as 3): treatment of Sec. 2.3 */
+    double rho_in2;         /* Set-1 inlet density of component 2 */
+    double rho_out1;        /* Set-1 outlet density of component 1 */
 } oracle_params;
 
 #define IDX(p, y, x) ((size_t)(y) * (size_t)(p)->nx + (size_t)(x))
@@ -110,8 +121,9 @@ double oracle_pressure(double g_coh, double rho1, double rho2) {
 }
 
 /* Initial state: f = f^eq(rho^sigma, u = 0) on fluid nodes, taken as the
- * post-collision populations of step 0; d5 records component 1's f_{3,6,7}
- * on the outlet column (Eq. 26). */
+ * post-collision populations of step 0; d5 [6][ny] records component 1's
+ * f_{3,6,7} on the outlet column (Eq. 26, rows 0-2) and component 2's
+ * f_{1,5,8} on the inlet column (Eq. 27, rows 3-5). */
 void oracle_init(const oracle_params *p, const uint8_t *solid,
                  const double *rho1, const double *rho2, double *f, double *d5) {
     size_t n = (size_t)p->nx * p->ny;
@@ -127,20 +139,52 @@ void oracle_init(const oracle_params *p, const uint8_t *solid,
         }
     if (d5) {
         static const int OUT_MISSING[3] = {3, 6, 7};
+        static const int IN_MISSING[3] = {1, 5, 8};
         for (int k = 0; k < 3; ++k)
-            for (int y = 0; y < p->ny; ++y)
+            for (int y = 0; y < p->ny; ++y) {
                 d5[(size_t)k * p->ny + y] = f[FIDX(p, 0, OUT_MISSING[k], y, p->nx - 1)];
+                d5[(size_t)(3 + k) * p->ny + y] = f[FIDX(p, 1, IN_MISSING[k], y, 0)];
+            }
     }
 }
 
+/* Zou-He pressure condition at the inlet column x = 0 for component c with
+ * density rho (Eqs. 22-25; zero tangential velocity): fills the missing
+ * f_{1,5,8} of node (0, y) from the known ones. */
+static void zou_he_inlet(const oracle_params *p, double *fnew, int c, int y, double rho,
+                         const int *missing) {
+    double f0 = fnew[FIDX(p, c, 0, y, 0)], f2 = fnew[FIDX(p, c, 2, y, 0)];
+    double f3 = fnew[FIDX(p, c, 3, y, 0)], f4 = fnew[FIDX(p, c, 4, y, 0)];
+    double f6 = fnew[FIDX(p, c, 6, y, 0)], f7 = fnew[FIDX(p, c, 7, y, 0)];
+    double ux = 1.0 - (f0 + f2 + f4 + 2.0 * (f3 + f6 + f7)) / rho;
+    if (missing[1]) fnew[FIDX(p, c, 1, y, 0)] = f3 + 2.0 / 3.0 * rho * ux;
+    if (missing[5]) fnew[FIDX(p, c, 5, y, 0)] = f7 - 0.5 * (f2 - f4) + 1.0 / 6.0 * (rho * ux);
+    if (missing[8]) fnew[FIDX(p, c, 8, y, 0)] = f6 + 0.5 * (f2 - f4) + 1.0 / 6.0 * (rho * ux);
+}
+
+/* The same at the outlet column x = nx - 1 (Eqs. 18-21): fills f_{3,6,7}. */
+static void zou_he_outlet(const oracle_params *p, double *fnew, int c, int y, double rho,
+                          const int *missing) {
+    int x = p->nx - 1;
+    double f0 = fnew[FIDX(p, c, 0, y, x)], f1 = fnew[FIDX(p, c, 1, y, x)];
+    double f2 = fnew[FIDX(p, c, 2, y, x)], f4 = fnew[FIDX(p, c, 4, y, x)];
+    double f5 = fnew[FIDX(p, c, 5, y, x)], f8 = fnew[FIDX(p, c, 8, y, x)];
+    double ux = -1.0 + (f0 + f2 + f4 + 2.0 * (f1 + f5 + f8)) / rho;
+    if (missing[3]) fnew[FIDX(p, c, 3, y, x)] = f1 - 2.0 / 3.0 * rho * ux;
+    if (missing[6]) fnew[FIDX(p, c, 6, y, x)] = f8 - 0.5 * (f2 - f4) - 1.0 / 6.0 * (rho * ux);
+    if (missing[7]) fnew[FIDX(p, c, 7, y, x)] = f5 + 0.5 * (f2 - f4) - 1.0 / 6.0 * (rho * ux);
+}
+
 /*
- * Streaming (left side of Eq. 1) with half-way bounce-back, then the Set-3
- * boundary treatment of Sec. 2.3.  fpost holds post-collision populations of
- * step t; fnew receives the populations of step t+1 before collision.
+ * Streaming (left side of Eq. 1) with half-way bounce-back, then the inlet
+ * and outlet treatment of Sec. 2.3 (Set-1, -2 or -3, see bc_set).  fpost
+ * holds post-collision populations of step t; fnew receives the populations
+ * of step t+1 before collision.
  */
 void oracle_stream_bc(const oracle_params *p, const uint8_t *solid,
                       const double *d5, const double *fpost, double *fnew) {
     size_t n = (size_t)p->nx * p->ny;
+    const int set = p->bc_set == 1 || p->bc_set == 2 ? p->bc_set : 3;
     memset(fnew, 0, 18 * n * sizeof(double));
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < p->ny; ++y)
@@ -163,41 +207,35 @@ void oracle_stream_bc(const oracle_params *p, const uint8_t *solid,
             }
             if (!p->open_x) continue;
             if (x == 0) {
-                /* inlet, component 1: Zou-He with rho_in (Eqs. 22-25) */
-                double f0 = fnew[FIDX(p, 0, 0, y, x)], f2 = fnew[FIDX(p, 0, 2, y, x)];
-                double f3 = fnew[FIDX(p, 0, 3, y, x)], f4 = fnew[FIDX(p, 0, 4, y, x)];
-                double f6 = fnew[FIDX(p, 0, 6, y, x)], f7 = fnew[FIDX(p, 0, 7, y, x)];
-                double rin = p->rho_in1;
-                double ux = 1.0 - (f0 + f2 + f4 + 2.0 * (f3 + f6 + f7)) / rin;
-                if (missing[1]) fnew[FIDX(p, 0, 1, y, x)] = f3 + 2.0 / 3.0 * rin * ux;
-                if (missing[5])
-                    fnew[FIDX(p, 0, 5, y, x)] = f7 - 0.5 * (f2 - f4) + 1.0 / 6.0 * (rin * ux);
-                if (missing[8])
-                    fnew[FIDX(p, 0, 8, y, x)] = f6 + 0.5 * (f2 - f4) + 1.0 / 6.0 * (rin * ux);
-                /* inlet, component 2: keep own post-collision values (Eq. 28) */
+                /* inlet, component 1: Zou-He with rho_in1 (Eqs. 22-25) */
+                zou_he_inlet(p, fnew, 0, y, p->rho_in1, missing);
                 static const int IN_MISSING[3] = {1, 5, 8};
-                for (int k = 0; k < 3; ++k) {
-                    int i = IN_MISSING[k];
-                    if (missing[i]) fnew[FIDX(p, 1, i, y, x)] = fpost[FIDX(p, 1, i, y, x)];
+                if (set == 1) {
+                    /* Set-1: component 2 by the same equations, rho_in2 */
+                    zou_he_inlet(p, fnew, 1, y, p->rho_in2, missing);
+                } else {
+                    for (int k = 0; k < 3; ++k) {
+                        int i = IN_MISSING[k];
+                        if (!missing[i]) continue;
+                        fnew[FIDX(p, 1, i, y, x)] =
+                            set == 2 ? d5[(size_t)(3 + k) * p->ny + y] /* Set-2: Eq. 27 */
+                                     : fpost[FIDX(p, 1, i, y, x)];    /* Set-3: own post-collision, Eq. 28 */
+                    }
                 }
             }
             if (x == p->nx - 1) {
-                /* outlet, component 2: Zou-He with rho_out (Eqs. 18-21) */
-                double f0 = fnew[FIDX(p, 1, 0, y, x)], f1 = fnew[FIDX(p, 1, 1, y, x)];
-                double f2 = fnew[FIDX(p, 1, 2, y, x)], f4 = fnew[FIDX(p, 1, 4, y, x)];
-                double f5 = fnew[FIDX(p, 1, 5, y, x)], f8 = fnew[FIDX(p, 1, 8, y, x)];
-                double rout = p->rho_out2;
-                double ux = -1.0 + (f0 + f2 + f4 + 2.0 * (f1 + f5 + f8)) / rout;
-                if (missing[3]) fnew[FIDX(p, 1, 3, y, x)] = f1 - 2.0 / 3.0 * rout * ux;
-                if (missing[6])
-                    fnew[FIDX(p, 1, 6, y, x)] = f8 - 0.5 * (f2 - f4) - 1.0 / 6.0 * (rout * ux);
-                if (missing[7])
-                    fnew[FIDX(p, 1, 7, y, x)] = f5 + 0.5 * (f2 - f4) - 1.0 / 6.0 * (rout * ux);
-                /* outlet, component 1: open condition of Eq. 26 */
-                static const int OUT_MISSING[3] = {3, 6, 7};
-                for (int k = 0; k < 3; ++k) {
-                    int i = OUT_MISSING[k];
-                    if (missing[i]) fnew[FIDX(p, 0, i, y, x)] = d5[(size_t)k * p->ny + y];
+                /* outlet, component 2: Zou-He with rho_out2 (Eqs. 18-21) */
+                zou_he_outlet(p, fnew, 1, y, p->rho_out2, missing);
+                if (set == 1) {
+                    /* Set-1: component 1 by the same equations, rho_out1 */
+                    zou_he_outlet(p, fnew, 0, y, p->rho_out1, missing);
+                } else {
+                    /* Set-2 and Set-3: open condition of Eq. 26 */
+                    static const int OUT_MISSING[3] = {3, 6, 7};
+                    for (int k = 0; k < 3; ++k) {
+                        int i = OUT_MISSING[k];
+                        if (missing[i]) fnew[FIDX(p, 0, i, y, x)] = d5[(size_t)k * p->ny + y];
+                    }
                 }
             }
         }

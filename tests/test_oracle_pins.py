@@ -211,6 +211,67 @@ def test_zou_he_prescribes_density_and_zero_tangential_velocity():
     assert fs[0, 1, y, 5] == fpost[0, 1, y, 4]
 
 
+def test_set1_prescribes_both_components_at_both_ends():
+    """Set-1 (Sec. 2.3): Zou-He for the other component too, with its own
+    fixed density: every component's density is prescribed at both ends and
+    the tangential momentum vanishes there."""
+    o = _open_channel()
+    o.set_bc(1, rho_in2=0.031, rho_out1=0.024)
+    fs = o.stream_bc()
+    fluid_in = np.nonzero(o.solid[:, 0] == 0)[0]
+    fluid_out = np.nonzero(o.solid[:, -1] == 0)[0]
+    ey = E[1]
+    for c, rin, rout in ((0, 1.02, 0.024), (1, 0.031, 0.98)):
+        assert np.allclose(fs[c, :, fluid_in, 0].sum(axis=1), rin, rtol=0, atol=1e-15)
+        assert np.allclose(fs[c, :, fluid_out, -1].sum(axis=1), rout, rtol=0, atol=1e-15)
+        assert np.allclose(fs[c, :, fluid_in, 0] @ ey, 0.0, atol=1e-16)
+        assert np.allclose(fs[c, :, fluid_out, -1] @ ey, 0.0, atol=1e-16)
+
+
+def test_set2_freezes_the_inlet_populations_of_component2():
+    """Set-2 (Eq. 27): component 2's missing f_{1,5,8} at the inlet stay at
+    their initial values, f^eq_i(rho, 0) = w_i rho, whatever the state; all
+    else is as in Set-3."""
+    o = _open_channel()
+    fs3 = o.stream_bc()
+    o.set_bc(2)
+    fs2 = o.stream_bc()
+    fluid_in = np.nonzero(o.solid[:, 0] == 0)[0]
+    for k, i in enumerate((1, 5, 8)):
+        assert np.array_equal(fs2[1, i, fluid_in, 0], o.d5[3 + k, fluid_in])
+    mask = np.ones_like(fs2, dtype=bool)
+    mask[1, [1, 5, 8], :, 0] = False
+    assert np.array_equal(fs2[mask], fs3[mask])
+    # the recorded values are the initial equilibrium at rest, w_i rho2(t=0)
+    rng = np.random.default_rng(3)  # the draws of _open_channel
+    rng.random(o.solid.shape)
+    rho2_init = 0.027 + 0.9 * rng.random(o.solid.shape)
+    for k, w in enumerate((1 / 9, 1 / 36, 1 / 36)):
+        assert np.allclose(o.d5[3 + k, fluid_in], w * rho2_init[fluid_in, 0], rtol=1e-15, atol=0)
+
+
+def test_set1_component_swap_symmetry_with_open_ends():
+    """At equal viscosities Set-1 treats the components alike: swapping the
+    components, xi -> -xi and the four boundary densities swaps the solution
+    exactly, open ends included."""
+    n, m = 28, 20
+    solid = np.zeros((m, n), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    solid[7:12, 12:17] = 1
+    xi = media.uniform_xi(solid, 0.3)
+    rho1, rho2 = media.droplet_densities(n, m, 8, 10, 4, solid=solid)
+    a = oracle.Oracle(solid, xi, nu1=0.12, nu2=0.12, rho_in1=1.01, rho_out2=0.99, bc_set=1,
+                      rho_in2=0.03, rho_out1=0.025)
+    b = oracle.Oracle(solid, -xi, nu1=0.12, nu2=0.12, rho_in1=0.03, rho_out2=0.025, bc_set=1,
+                      rho_in2=1.01, rho_out1=0.99)
+    a.init(rho1, rho2)
+    b.init(rho2, rho1)
+    a.step(150)
+    b.step(150)
+    assert np.array_equal(a.f[0], b.f[1]) and np.array_equal(a.f[1], b.f[0])
+
+
 def test_bounce_back_reflects_own_population():
     o = _open_channel()
     fpost = o.f.copy()
