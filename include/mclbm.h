@@ -122,11 +122,30 @@ int mclbm_set_coupling(mclbm_lattice *lat, double g_coh, double g_ads);
 /* Body acceleration g: F^b,sigma = rho^sigma g (Eq. 12). */
 int mclbm_set_body_force(mclbm_lattice *lat, double gx, double gy);
 
-/* Set-3 pressure boundaries (Sec. 2.3): rho_in1 is the density of component
- * 1 imposed at x = 0 (Eqs. 22-25), rho_out2 that of component 2 at
- * x = nx-1 (Eqs. 18-21).  Either value < 0 switches the boundaries off and
- * makes x periodic. */
+/* Pressure boundaries (Sec. 2.3): rho_in1 is the density of component 1
+ * imposed at x = 0 (Eqs. 22-25), rho_out2 that of component 2 at x = nx-1
+ * (Eqs. 18-21).  Either value < 0 switches the boundaries off and makes x
+ * periodic.  The treatment of the other component at each end is chosen by
+ * mclbm_set_bc (Set-3 by default). */
 int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2);
+
+/* Inlet/outlet treatment of the other component (Sec. 2.3), in effect while
+ * the pressure boundaries are on:
+ *   bc_set 1 (Set-1): Zou-He for both components at both ends; component 2
+ *            at x = 0 with density rho_in2 (Eqs. 22-25 with the component
+ *            exchanged), component 1 at x = nx-1 with rho_out1 (Eqs. 18-21);
+ *   bc_set 2 (Set-2): component 1's missing f_{3,6,7} at the outlet (Eq. 26)
+ *            and component 2's missing f_{1,5,8} at the inlet (Eq. 27) keep
+ *            the values they had at initialisation;
+ *   bc_set 3 (Set-3, the paper's and the default): Eq. 26 at the outlet;
+ *            at the inlet component 2 keeps its own post-collision
+ *            f_{1,5,8} (Eq. 28).
+ * rho_in2 and rho_out1 are read for Set-1 only.  The frozen values of Eqs.
+ * 26-27 are recorded by every initialisation (mclbm_init_densities,
+ * mclbm_init_from_phase, mclbm_set_populations).  Errors: MCLBM_ERR_ARG for
+ * a set outside 1..3 or, with Set-1, densities that are not positive and
+ * finite. */
+int mclbm_set_bc(mclbm_lattice *lat, int bc_set, double rho_in2, double rho_out1);
 
 /* The same boundaries given as pressures: Eq. 14 is inverted for the
  * majority density with the minority density held at 0.027 (the dissolved

@@ -301,7 +301,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         (rc = dev_alloc(*L, &L->f[1], pop_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->err, sizeof(int))) ||
         (rc = dev_alloc(*L, (void **)&L->geo_pad, (size_t)L->geo_pad_rows * L->gpitch)) ||
-        (rc = dev_alloc(*L, &L->d5, 3 * (size_t)ny * L->real_bytes)) ||
+        (rc = dev_alloc(*L, &L->d5, 6 * (size_t)ny * L->real_bytes)) ||
         (rc = dev_alloc(*L, (void **)&L->diag_partial, (size_t)L->diag_blocks * 9 * sizeof(double))) ||
         (rc = dev_alloc(*L, (void **)&L->diag_out, 8 * sizeof(double))) ||
         (rc = dev_alloc(*L, (void **)&L->bad_flag, sizeof(unsigned long long)))) {
@@ -328,7 +328,7 @@ int mclbm_create(int nx, int ny, const uint8_t *solid, const float *xi, mclbm_pr
         (e = cudaMemsetAsync(L->f[0], 0, pop_bytes, L->stream)) ||
         (e = cudaMemsetAsync(L->f[1], 0, pop_bytes, L->stream)) ||
         (e = cudaMemsetAsync(L->err, 0, sizeof(int), L->stream)) ||
-        (e = cudaMemsetAsync(L->d5, 0, 3 * (size_t)ny * L->real_bytes, L->stream)) ||
+        (e = cudaMemsetAsync(L->d5, 0, 6 * (size_t)ny * L->real_bytes, L->stream)) ||
         (e = cudaMemsetAsync(L->bad_flag, 0, sizeof(unsigned long long), L->stream)) ||
         (e = cudaStreamSynchronize(L->stream))) {
         release(L);
@@ -423,6 +423,19 @@ int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2) {
     lat->p.open_x = 1;
     lat->p.rho_in1 = rho_in1;
     lat->p.rho_out2 = rho_out2;
+    lat->p.round_fp32();
+    return MCLBM_OK;
+}
+
+int mclbm_set_bc(mclbm_lattice *lat, int bc_set, double rho_in2, double rho_out1) {
+    if (int rc = check_lat(lat)) return rc;
+    if (bc_set < 1 || bc_set > 3) return fail(MCLBM_ERR_ARG, "bc_set must be 1, 2 or 3");
+    if (bc_set == 1 && !(std::isfinite(rho_in2) && std::isfinite(rho_out1) && rho_in2 > 0 && rho_out1 > 0))
+        return fail(MCLBM_ERR_ARG, "Set-1 needs positive finite rho_in2 and rho_out1");
+    ++lat->version;
+    lat->p.bc_set = bc_set;
+    lat->p.rho_in2 = bc_set == 1 ? rho_in2 : 0.0;
+    lat->p.rho_out1 = bc_set == 1 ? rho_out1 : 0.0;
     lat->p.round_fp32();
     return MCLBM_OK;
 }
@@ -541,7 +554,8 @@ int mclbm_get_populations(mclbm_lattice *lat, double *f) {
 }
 
 // Checkpoint file: header, Params, then the current population buffer and
-// the outlet record of Eq. 26 as raw device bytes (bit-exact restore).
+// the frozen boundary records of Eqs. 26-27 as raw device bytes (bit-exact
+// restore).  Version 2: Params carry the inlet/outlet treatment (Set-1/2/3).
 namespace {
 struct CheckpointHeader {
     char magic[8];
@@ -559,12 +573,12 @@ int mclbm_save(mclbm_lattice *lat, const char *path) {
     if (int rc = sparse_to_dense(*lat)) return rc;
     CheckpointHeader h{};
     std::memcpy(h.magic, CKPT_MAGIC, 8);
-    h.version = 1;
+    h.version = 2;
     h.nx = lat->nx;
     h.ny = lat->ny;
     h.prec = (int32_t)lat->prec;
     h.pop_bytes = (int64_t)lat->planes * lat->plane * (int64_t)lat->store_bytes;
-    h.d5_bytes = 3 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
+    h.d5_bytes = 6 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
     h.steps = lat->steps;
     std::vector<unsigned char> buf((size_t)(h.pop_bytes + h.d5_bytes));
     cudaError_t e = cudaMemcpyAsync(buf.data(), lat->f[lat->cur], (size_t)h.pop_bytes,
@@ -592,8 +606,8 @@ int mclbm_load(mclbm_lattice *lat, const char *path) {
     Params p;
     bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(&p, sizeof(Params), 1, fp) == 1;
     const int64_t pop_bytes = (int64_t)lat->planes * lat->plane * (int64_t)lat->store_bytes;
-    const int64_t d5_bytes = 3 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
-    ok = ok && std::memcmp(h.magic, CKPT_MAGIC, 8) == 0 && h.version == 1;
+    const int64_t d5_bytes = 6 * (int64_t)lat->ny * (int64_t)lat->real_bytes;
+    ok = ok && std::memcmp(h.magic, CKPT_MAGIC, 8) == 0 && h.version == 2;
     if (ok && (h.nx != lat->nx || h.ny != lat->ny || h.prec != (int32_t)lat->prec ||
                h.pop_bytes != pop_bytes || h.d5_bytes != d5_bytes)) {
         std::fclose(fp);

@@ -11,7 +11,8 @@ constexpr int BLK = 256;
 inline int blocks_for(long long n, int per = BLK) { return (int)((n + per - 1) / per); }
 
 // f_i = f_i^eq(rho^sigma, u = 0) = w_i rho^sigma (Eq. 2 at rest); records
-// component 1's outlet f_{3,6,7} for Eq. 26.
+// component 1's outlet f_{3,6,7} (Eq. 26) and component 2's inlet f_{1,5,8}
+// (Eq. 27, Set-2).
 template <class P>
 __global__ void init_equilibrium_kernel(Geometry g, Params p, const double *rho1,
                                         const double *rho2, typename P::store_t *f,
@@ -33,6 +34,11 @@ __global__ void init_equilibrium_kernel(Geometry g, Params p, const double *rho1
         d5[y] = fs[0][3];
         d5[g.ny + y] = fs[0][6];
         d5[2 * g.ny + y] = fs[0][7];
+    }
+    if (x == 0) {
+        d5[3 * g.ny + y] = fs[1][1];
+        d5[4 * g.ny + y] = fs[1][5];
+        d5[5 * g.ny + y] = fs[1][8];
     }
 }
 
@@ -59,6 +65,11 @@ __global__ void import_kernel(Geometry g, Params p, const double *src, typename 
         d5[y] = fs[0][3];
         d5[g.ny + y] = fs[0][6];
         d5[2 * g.ny + y] = fs[0][7];
+    }
+    if (x == 0) {
+        d5[3 * g.ny + y] = fs[1][1];
+        d5[4 * g.ny + y] = fs[1][5];
+        d5[5 * g.ny + y] = fs[1][8];
     }
 }
 

@@ -85,14 +85,16 @@ struct Params {
     double g_coh = 3.5, g_ads = 3.5;
     double gx = 0.0, gy = 0.0;
     double rho_in1 = -1.0, rho_out2 = -1.0;
-    int open_x = 0;      // Set-3 boundaries on at x = 0 and x = nx-1
+    int open_x = 0;      // pressure boundaries on at x = 0 and x = nx-1
     int periodic_y = 0;  // else rows 0 and ny-1 must be solid
     int vel_shift = 1;   // u carries F/2
+    int bc_set = 3;      // inlet/outlet treatment of Sec. 2.3: Set-1, -2 or -3
+    double rho_in2 = 0.0, rho_out1 = 0.0;  // Set-1: the other component's densities
     // the same values rounded to FP32 once on the host: the FP32 kernels
     // read these rather than converting from FP64 at every node (such a
     // conversion occupies the narrow FP64 pipe)
     float nu1_f = 0, nu2_f = 0, g_coh_f = 0, g_ads_f = 0, gx_f = 0, gy_f = 0;
-    float rho_in1_f = 0, rho_out2_f = 0;
+    float rho_in1_f = 0, rho_out2_f = 0, rho_in2_f = 0, rho_out1_f = 0;
     void round_fp32() {
         nu1_f = (float)nu1;
         nu2_f = (float)nu2;
@@ -102,6 +104,8 @@ struct Params {
         gy_f = (float)gy;
         rho_in1_f = (float)rho_in1;
         rho_out2_f = (float)rho_out2;
+        rho_in2_f = (float)rho_in2;
+        rho_out1_f = (float)rho_out1;
     }
 };
 
@@ -145,7 +149,8 @@ struct StepArgs {
     Params p;
     const void *fin;           // post-collision state of step t
     void *fout;                // post-collision state of step t+1
-    const void *d5;            // [3][ny] component-1 outlet f_{3,6,7} (real type)
+    const void *d5;            // [6][ny] (real type): component 1's outlet f_{3,6,7} (Eq. 26),
+                               // component 2's inlet f_{1,5,8} (Eq. 27), frozen at initialisation
     int *err;                  // device error word (bounded waits)
     int rows_per_cta;          // strip kernel: rows of one CTA
 };
@@ -176,7 +181,7 @@ struct Lattice {
     float *chi_f = nullptr;    // [256][2], rounded to FP32
     void *f[2] = {nullptr, nullptr};  // ping-pong population buffers
     int cur = 0;               // index of the buffer holding the state
-    void *d5 = nullptr;        // [3][ny] real type
+    void *d5 = nullptr;        // [6][ny] real type (see StepArgs::d5)
     int *err = nullptr;        // device error word
     double *diag_partial = nullptr;   // scratch of the diagnostics reduction
     int diag_blocks = 0;

@@ -105,47 +105,68 @@ __device__ __forceinline__ uint8_t geo_at(const Geometry &g, const Params &p, in
     return g.geo[(long long)y * g.gpitch + GEO_HX + x];
 }
 
-// ---------------------------------------------------------------------------
-// Set-3 boundary treatment (Sec. 2.3) on pulled populations f of a node at
-// an open end; own(c, i) returns the node's own post-collision f*.
-//   x = 0:     component 1 Zou-He with rho_in (Eqs. 22-25) for f_1, f_5, f_8;
-//              component 2 keeps its own post-collision f_1, f_5, f_8 (Eq. 28)
-//   x = nx-1:  component 2 Zou-He with rho_out (Eqs. 18-21) for f_3, f_6, f_7;
-//              component 1 takes the recorded values of Eq. 26.
-// ---------------------------------------------------------------------------
+// Inlet/outlet pressure treatment of Sec. 2.3 at a fluid node of the open
+// columns x = 0 and x = nx - 1, after streaming; f holds the streamed
+// populations, own(c, i) the node's own post-collision value.
+//   inlet:  component 1 by Zou-He with rho_in1 (Eqs. 22-25); component 2 by
+//           Zou-He with rho_in2 (Set-1), frozen at initialisation (Eq. 27,
+//           Set-2) or its own post-collision values (Eq. 28, Set-3);
+//   outlet: component 2 by Zou-He with rho_out2 (Eqs. 18-21); component 1 by
+//           Zou-He with rho_out1 (Set-1) or frozen at initialisation (Eq. 26,
+//           Sets 2 and 3).
+// Zou-He takes zero tangential velocity; u_x follows from the density.
+template <class R>
+__device__ __forceinline__ void zou_he_in(R g[9], R rin) {
+    const R ux = R(1) - (g[0] + g[2] + g[4] + R(2) * (g[3] + g[6] + g[7])) / rin;
+    const R d24 = R(0.5) * (g[2] - g[4]);
+    const R ru6 = rin * ux * (R(1) / R(6));
+    g[1] = g[3] + (R(2) / R(3)) * rin * ux;
+    g[5] = g[7] - d24 + ru6;
+    g[8] = g[6] + d24 + ru6;
+}
+template <class R>
+__device__ __forceinline__ void zou_he_out(R g[9], R rout) {
+    const R ux = R(-1) + (g[0] + g[2] + g[4] + R(2) * (g[1] + g[5] + g[8])) / rout;
+    const R d24 = R(0.5) * (g[2] - g[4]);
+    const R ru6 = rout * ux * (R(1) / R(6));
+    g[3] = g[1] - (R(2) / R(3)) * rout * ux;
+    g[6] = g[8] - d24 - ru6;
+    g[7] = g[5] + d24 - ru6;
+}
+
 template <class R, class Own>
-__device__ __forceinline__ void apply_set3(const StepArgs &a, int x, int y, Own own, R f[2][9]) {
+__device__ __forceinline__ void apply_open_bc(const StepArgs &a, int x, int y, Own own, R f[2][9]) {
     if (!a.p.open_x) return;
+    const R *d5 = static_cast<const R *>(a.d5);
     if (x == 0) {
-        const R rin = par<R>(a.p.rho_in1, a.p.rho_in1_f);
-        const R ux = R(1) - (f[0][0] + f[0][2] + f[0][4] + R(2) * (f[0][3] + f[0][6] + f[0][7])) / rin;
-        const R d24 = R(0.5) * (f[0][2] - f[0][4]);
-        const R ru6 = rin * ux * (R(1) / R(6));
-        f[0][1] = f[0][3] + (R(2) / R(3)) * rin * ux;
-        f[0][5] = f[0][7] - d24 + ru6;
-        f[0][8] = f[0][6] + d24 + ru6;
-        f[1][1] = own(1, 1);
-        f[1][5] = own(1, 5);
-        f[1][8] = own(1, 8);
+        zou_he_in<R>(f[0], par<R>(a.p.rho_in1, a.p.rho_in1_f));
+        if (a.p.bc_set == 1) {
+            zou_he_in<R>(f[1], par<R>(a.p.rho_in2, a.p.rho_in2_f));
+        } else if (a.p.bc_set == 2) {
+            f[1][1] = d5[3 * a.g.ny + y];
+            f[1][5] = d5[4 * a.g.ny + y];
+            f[1][8] = d5[5 * a.g.ny + y];
+        } else {
+            f[1][1] = own(1, 1);
+            f[1][5] = own(1, 5);
+            f[1][8] = own(1, 8);
+        }
     }
     if (x == a.g.nx - 1) {
-        const R rout = par<R>(a.p.rho_out2, a.p.rho_out2_f);
-        const R ux = R(-1) + (f[1][0] + f[1][2] + f[1][4] + R(2) * (f[1][1] + f[1][5] + f[1][8])) / rout;
-        const R d24 = R(0.5) * (f[1][2] - f[1][4]);
-        const R ru6 = rout * ux * (R(1) / R(6));
-        f[1][3] = f[1][1] - (R(2) / R(3)) * rout * ux;
-        f[1][6] = f[1][8] - d24 - ru6;
-        f[1][7] = f[1][5] + d24 - ru6;
-        const R *d5 = static_cast<const R *>(a.d5);
-        f[0][3] = d5[y];
-        f[0][6] = d5[a.g.ny + y];
-        f[0][7] = d5[2 * a.g.ny + y];
+        zou_he_out<R>(f[1], par<R>(a.p.rho_out2, a.p.rho_out2_f));
+        if (a.p.bc_set == 1) {
+            zou_he_out<R>(f[0], par<R>(a.p.rho_out1, a.p.rho_out1_f));
+        } else {
+            f[0][3] = d5[y];
+            f[0][6] = d5[a.g.ny + y];
+            f[0][7] = d5[2 * a.g.ny + y];
+        }
     }
 }
 
 // Populations f_i(x, t+1) of fluid node (x, y) before collision, pulled
 // from global memory: f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) when the source
-// is solid (half-way bounce-back), then Set-3 at the open ends.  srcgeo(i)
+// is solid (half-way bounce-back), then the open-end treatment (Sec. 2.3).  srcgeo(i)
 // returns the geometry code of the source x - e_i.
 template <class P, class SrcGeo>
 __device__ __forceinline__ void pull_node(const StepArgs &a, int x, int y, SrcGeo srcgeo,
@@ -179,7 +200,7 @@ __device__ __forceinline__ void pull_node(const StepArgs &a, int x, int y, SrcGe
             f[1][i] = pop_load<P>(fin, plane, 1, i, ss);
         }
     }
-    apply_set3<R>(a, x, y, [&](int c, int i) { return pop_load<P>(fin, plane, c, i, site); }, f);
+    apply_open_bc<R>(a, x, y, [&](int c, int i) { return pop_load<P>(fin, plane, c, i, site); }, f);
 }
 
 // e_i . (vx, vy) without multiplications by 0 or 1 (i is a constant in the

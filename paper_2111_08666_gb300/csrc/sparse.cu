@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             return v;
         };
         // f_i = f*_i(x - e_i), or the node's own f*_opp(i) where x - e_i is not
-        // fluid (half-way bounce-back), then Set-3 at the open ends
+        // fluid (half-way bounce-back), then the open-end treatment (Sec. 2.3)
         auto pull = [&](int fpos, int ooff, uint32_t e, int x, int y, R f[2][9]) {
             const uint32_t m = (e >> 12) & 0xffu;
             f[0][0] = val(0, 0, ooff, wgt<R>(0));
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
                 f[1][i] = val(pl, 1, off, wgt<R>(i));
             }
             if (e & SET3)
-                apply_set3<R>(a, x, y, [&](int comp, int i) { return val(i, comp, ooff, wgt<R>(i)); }, f);
+                apply_open_bc<R>(a, x, y, [&](int comp, int i) { return val(i, comp, ooff, wgt<R>(i)); }, f);
         };
 
         // ---- A: densities of the ring's fluid nodes and of the tile's own ------

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
         }
         // halo rows of a periodic-y lattice lie outside 0..ny-1: the outlet
         // values of Eq. 26 are indexed by the wrapped row
-        apply_set3<R>(a, x, pmod(q, g.ny), [&](int c, int i) { return dec(s0, c, i, lx + HX); }, f);
+        apply_open_bc<R>(a, x, pmod(q, g.ny), [&](int c, int i) { return dec(s0, c, i, lx + HX); }, f);
     };
 
     bool bad = false;    // this thread saw a wait run out

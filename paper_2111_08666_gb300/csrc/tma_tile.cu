@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
             return v;
         };
         // f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) where x - e_i is not fluid
-        // (half-way bounce-back), then Set-3 at the open ends; the node sits at
+        // (half-way bounce-back), then the open-end treatment (Sec. 2.3); the node sits at
         // staged row r, column cc, lattice column x and wrapped row y.  Where a
         // source lies beyond an open end the bounce-back value is a placeholder
         // that Set-3 replaces.
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
                 f[1][i] = dec(pl, 1, pos, wgt<R>(i));
             }
             if (e & SET3_BITS)
-                apply_set3<R>(a, x, y, [&](int comp, int i) { return dec(i, comp, own, wgt<R>(i)); },
+                apply_open_bc<R>(a, x, y, [&](int comp, int i) { return dec(i, comp, own, wgt<R>(i)); },
                               f);
         };
 

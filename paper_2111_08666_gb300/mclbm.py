@@ -66,6 +66,7 @@ _SIGS = {
     "mclbm_set_body_force": (C.c_int, [_vp, C.c_double, C.c_double]),
     "mclbm_set_pressure_bc": (C.c_int, [_vp, C.c_double, C.c_double]),
     "mclbm_set_pressure_bc_p": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "mclbm_set_bc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
     "mclbm_set_stream": (C.c_int, [_vp, _vp]),
     "mclbm_init_densities": (C.c_int, [_vp, _vp, _vp]),
     "mclbm_set_populations": (C.c_int, [_vp, _vp]),
@@ -204,6 +205,10 @@ def mclbm_set_body_force(h, gx: float, gy: float) -> None:
 
 def mclbm_set_pressure_bc(h, rho_in1: float, rho_out2: float) -> None:
     _check(load().mclbm_set_pressure_bc(h, rho_in1, rho_out2))
+
+
+def mclbm_set_bc(h, bc_set: int, rho_in2: float = 0.0, rho_out1: float = 0.0) -> None:
+    _check(load().mclbm_set_bc(h, int(bc_set), float(rho_in2), float(rho_out1)))
 
 
 def mclbm_set_pressure_bc_p(h, p_in: float, p_out: float) -> None:
@@ -375,7 +380,8 @@ class Lattice:
                  nu2: float = 1 / 6, g_coh: float = 3.5, g_ads: float | None = None,
                  rho_in1: float = -1.0, rho_out2: float = -1.0, periodic_y: bool = False,
                  vel_shift: bool = True, gx: float = 0.0, gy: float = 0.0, stream=None,
-                 kernel: int = 0, tile_shape: int = 0):
+                 kernel: int = 0, tile_shape: int = 0, bc_set: int = 3, rho_in2: float = 0.0,
+                 rho_out1: float = 0.0):
         self.h = None
         if isinstance(prec, str):
             prec = PRECISIONS[prec]
@@ -386,6 +392,7 @@ class Lattice:
         mclbm_set_viscosity(self.h, nu1, nu2)
         mclbm_set_coupling(self.h, g_coh, g_coh if g_ads is None else g_ads)
         mclbm_set_pressure_bc(self.h, rho_in1, rho_out2)
+        mclbm_set_bc(self.h, bc_set, rho_in2, rho_out1)
         mclbm_set_flag(self.h, MCLBM_FLAG_PERIODIC_Y, int(periodic_y))
         mclbm_set_flag(self.h, MCLBM_FLAG_VEL_SHIFT, int(vel_shift))
         mclbm_set_body_force(self.h, gx, gy)
@@ -452,6 +459,9 @@ class Lattice:
 
     def set_pressure_bc(self, rho_in1: float, rho_out2: float) -> None:
         mclbm_set_pressure_bc(self.h, rho_in1, rho_out2)
+
+    def set_bc(self, bc_set: int, rho_in2: float = 0.0, rho_out1: float = 0.0) -> None:
+        mclbm_set_bc(self.h, bc_set, rho_in2, rho_out1)
 
     def info(self) -> dict:
         return mclbm_info(self.h)

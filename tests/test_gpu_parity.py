@@ -309,6 +309,57 @@ def test_step_kernels_agree(prec, other):
     assert np.max(np.abs(fa - fb)) <= many * np.max(np.abs(fa))
 
 
+# --- inlet/outlet treatments Set-1 and Set-2 (Sec. 2.3) ------------------------
+
+BC_SETS = {1: dict(bc_set=1, rho_in2=0.03, rho_out1=0.025), 2: dict(bc_set=2)}
+
+
+@pytest.mark.parametrize("bc_set", [1, 2])
+def test_fp64_bc_sets_match_oracle(kernel, bc_set):
+    """The 128x64 disk medium of the FP64 parity case under Set-1 (Zou-He for
+    both components, the other component's densities fixed) and Set-2
+    (Eqs. 26-27 frozen from initialisation)."""
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], c["xi"], c["rho1"], c["rho2"], kernel=kernel, nu1=c["nu1"], nu2=c["nu2"],
+                rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], **BC_SETS[bc_set])
+    assert_fp64_parity(o, g, 200)
+
+
+@pytest.mark.parametrize("bc_set", [1, 2])
+def test_fp32_bc_sets_match_oracle(bc_set):
+    """FP32 (automatic kernel) against the oracle on the drainage medium
+    with viscosity ratio 10, 1000 steps: densities within 1e-4."""
+    m = media.make_disk_medium(160, 64, 7, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.4)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    o, g = pair(m.solid, xi, rho1, rho2, prec="fp32", nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
+                rho_in1=1.01, rho_out2=1.0, **BC_SETS[bc_set])
+    o.step(1000)
+    g.step(1000)
+    want = np.stack([o.f[0].sum(axis=0), o.f[1].sum(axis=0)])
+    got = g.density()
+    assert np.max(np.abs(got - want)) < 1e-4
+
+
+@pytest.mark.parametrize("other", [2, 3, 4])
+@pytest.mark.parametrize("bc_set", [1, 2])
+def test_bc_sets_step_kernels_agree(bc_set, other):
+    """Every step kernel applies Set-1 and Set-2 alike (FP32, to rounding)."""
+    m = media.make_disk_medium(150, 60, 13, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.4)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    kw = dict(prec="fp32", nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0,
+              **BC_SETS[bc_set])
+    a = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
+    b = mclbm.Lattice(m.solid, xi, kernel=other, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(300)
+    b.step(300)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= AGREE["fp32"][1] * np.max(np.abs(fa))
+
+
 @pytest.mark.parametrize("periodic_y,open_x", [(True, False), (True, True), (False, False)])
 def test_tma_kernel_ghost_frames_fp32(periodic_y, open_x):
     """The TMA tile kernel reads its ring from the ghost columns and rows at
@@ -359,15 +410,16 @@ def test_tile_shapes_agree(prec, open_x):
     assert np.max(np.abs(fa - fb)) <= AGREE[prec][1] * np.max(np.abs(fa))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16dev", "fp64"])
-def test_checkpoint_restores_bit_for_bit(prec, tmp_path):
+@pytest.mark.parametrize("prec,bc_set", [("fp32", 3), ("bf16dev", 3), ("fp64", 3), ("fp32", 2)])
+def test_checkpoint_restores_bit_for_bit(prec, bc_set, tmp_path):
     """A run saved and loaded into another lattice (created with other
-    parameters) continues exactly as the original."""
+    parameters) continues exactly as the original (with Set-2 this needs the
+    frozen inlet values of Eq. 27 restored as well)."""
     m = media.make_disk_medium(96, 48, 4, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
     xi = media.uniform_xi(m.solid, -0.3)
     rho1, rho2 = media.drainage_densities(m.solid)
     a = mclbm.Lattice(m.solid, xi, prec=prec, nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62),
-                      rho_in1=1.01, rho_out2=1.0)
+                      rho_in1=1.01, rho_out2=1.0, bc_set=bc_set)
     a.init(rho1, rho2)
     a.step(40)
     path = tmp_path / "state.ckpt"
