@@ -248,3 +248,44 @@ def config_batch(k: int):
                 xi=uniform_xi(m.solid, theta_to_xi(theta)), rho1=rho1, rho2=rho2,
                 nu1=(taus[0] - 0.5) / 3.0, nu2=(taus[1] - 0.5) / 3.0, g_coh=3.5,
                 rho_in1=1.005, rho_out2=1.0, porosity=m.porosity, theta=theta)
+
+
+def config_u_obstacle(nx: int = 800, ny: int = 200, arm: int = 10, r_drop: float = 30.0):
+    """Channel with a U-shaped wall (Sec. 4.1), a stand-in with dimensions of
+    our own: the paper gives the 800x200 channel, the droplet radius 30 and
+    the physics, not the obstacle's size.
+
+    Walls: rows 0-1 and ny-2..ny-1.  The U spans x in [nx/4, nx/4 + 80) and
+    the middle half of the channel (y in [ny/4, 3 ny/4)), its opening facing
+    the inlet and its closed side (thickness ``arm``) the outlet, so that the
+    invading component flows through the passages above and below while the
+    water inside the cup has nowhere to go.  A semicircular droplet of
+    component 1 (radius ``r_drop``) sits on the inner face of the closed
+    side; component 1 also fills the first 5 columns, component 2 the rest.
+    Physics of Sec. 4.1: tau1 = 3.5, tau2 = 0.62 (M = 25), xi = -0.4,
+    rho_in1 = 1.01, rho_out2 = 1.  ``cavity`` marks the inside of the cup."""
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[:2] = 1
+    solid[-2:] = 1
+    x0, x1 = nx // 4, nx // 4 + 80
+    y0, y1 = ny // 4, 3 * ny // 4
+    solid[y0:y1, x1 - arm:x1] = 1      # closed side
+    solid[y0:y0 + arm, x0:x1] = 1      # lower arm
+    solid[y1 - arm:y1, x0:x1] = 1      # upper arm
+    cavity = np.zeros((ny, nx), bool)
+    cavity[y0 + arm:y1 - arm, x0:x1 - arm] = True
+    front = np.zeros((ny, nx), bool)
+    front[y0:y1, x0 - 50:x0] = True
+    behind = np.zeros((ny, nx), bool)
+    behind[y0 - 10:y1 + 10, x1:x1 + 60] = True
+    rho1, rho2 = drainage_densities(solid)
+    # the droplet: tanh profile of Eq. 29 centred on the inner face
+    d1, d2 = droplet_densities(nx, ny, x1 - arm, 0.5 * (y0 + y1), r_drop, solid=solid)
+    inner = np.zeros((ny, nx), bool)
+    inner[:, : x1 - arm] = True
+    drop = inner & (d1 > rho1)
+    rho1 = np.where(drop, d1, rho1)
+    rho2 = np.where(drop, d2, rho2)
+    return dict(name=f"u_obstacle{nx}x{ny}", nx=nx, ny=ny, solid=solid, cavity=cavity, front=front, behind=behind,
+                xi=uniform_xi(solid, -0.4), rho1=rho1 * (solid == 0), rho2=rho2 * (solid == 0),
+                nu1=(3.5 - 0.5) / 3.0, nu2=(0.62 - 0.5) / 3.0, g=3.5, rho_in1=1.01, rho_out2=1.0)

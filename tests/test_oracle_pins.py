@@ -465,3 +465,4 @@ def test_contact_angle_neutral_and_symmetric():
     pairs = dict((round(a, 2), b) for a, b in GOLD["xi_theta_pairs"]["value"])
     assert tm == pytest.approx(pairs[-0.3], abs=8.0)
     assert tp == pytest.approx(pairs[0.3], abs=8.0)
+
