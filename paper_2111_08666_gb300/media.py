@@ -289,3 +289,61 @@ def config_u_obstacle(nx: int = 800, ny: int = 200, arm: int = 10, r_drop: float
     return dict(name=f"u_obstacle{nx}x{ny}", nx=nx, ny=ny, solid=solid, cavity=cavity, front=front, behind=behind,
                 xi=uniform_xi(solid, -0.4), rho1=rho1 * (solid == 0), rho2=rho2 * (solid == 0),
                 nu1=(3.5 - 0.5) / 3.0, nu2=(0.62 - 0.5) / 3.0, g=3.5, rho_in1=1.01, rho_out2=1.0)
+
+
+def make_block_medium(nx: int = 400, ny: int = 200, seed: int = 24, *, block: int = 10,
+                      porosity: float = 0.8117, gap: int = 3, wall_rows: int = 2,
+                      reservoir: int = 10, max_failures: int = 100_000) -> Medium:
+    """Random sequential addition of square solid blocks (side ``block``),
+    a stand-in for the block medium of Sec. 4.2 (400x200, 10x10 blocks,
+    porosity 0.8117, solid walls, block-free reservoirs of 10 columns at each
+    end; the paper takes its geometry from its ref. [24], which is not
+    available).  A corner is drawn uniformly on the integer grid of the
+    allowed box; the block is rejected when it comes closer than ``gap``
+    nodes to another block, a wall or a reservoir.  Placement stops once the
+    porosity (all nodes) is at or below the target, or after
+    ``max_failures`` consecutive rejections."""
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[:wall_rows, :] = 1
+    solid[ny - wall_rows:, :] = 1
+    # occupied: blocks grown by the gap, so that a new block must avoid it
+    keep_out = np.zeros((ny, nx), bool)
+    keep_out[: wall_rows + gap] = True
+    keep_out[ny - wall_rows - gap:] = True
+    keep_out[:, : reservoir + gap] = True
+    keep_out[:, nx - reservoir - gap:] = True
+    corners = []
+    failures = 0
+    n_all = nx * ny
+    while 1.0 - solid.sum() / n_all > porosity and failures < max_failures:
+        x0 = int(rng.integers(0, nx - block + 1))
+        y0 = int(rng.integers(0, ny - block + 1))
+        if keep_out[y0:y0 + block, x0:x0 + block].any():
+            failures += 1
+            continue
+        failures = 0
+        corners.append((x0, y0))
+        solid[y0:y0 + block, x0:x0 + block] = 1
+        keep_out[max(y0 - gap, 0):y0 + block + gap, max(x0 - gap, 0):x0 + block + gap] = True
+    return Medium(solid=solid, disks=np.asarray(corners, dtype=np.float64).reshape(-1, 2),
+                  porosity=1.0 - solid.sum() / n_all)
+
+
+# contact angle -> xi as Sec. 4.2 states them (22 deg: -0.55, 50 deg: -0.4,
+# 110 deg: 0.2)
+PAPER_XI = {22.0: -0.55, 50.0: -0.4, 110.0: 0.2}
+
+
+def config_block_hysteresis(theta: float, seed: int = 24):
+    """The drainage/imbibition workload of Sec. 4.2 on the block stand-in:
+    viscosity ratio 25 (tau1 = 3.5, tau2 = 0.62), contact angle ``theta``
+    (22, 50 or 110 deg, with the paper's xi for each), five oil layers at the
+    inlet, equal boundary densities to start."""
+    m = make_block_medium(seed=seed)
+    rho1, rho2 = drainage_densities(m.solid)
+    xi = PAPER_XI.get(float(theta), theta_to_xi(theta))
+    return dict(name=f"block400x200_theta{theta:g}", nx=400, ny=200, solid=m.solid,
+                xi=uniform_xi(m.solid, xi), xi_value=xi, rho1=rho1, rho2=rho2,
+                nu1=(3.5 - 0.5) / 3.0, nu2=(0.62 - 0.5) / 3.0, g=3.5, rho_in1=1.0, rho_out2=1.0,
+                porosity=m.porosity, theta=theta)

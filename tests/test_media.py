@@ -23,3 +23,19 @@ def test_u_obstacle_channel_layout():
     oil_in_cup = (c["rho1"] > c["rho2"]) & c["cavity"]
     assert abs(oil_in_cup.sum() - np.pi * 30 ** 2 / 2) < 0.05 * np.pi * 30 ** 2 / 2
     assert (c["rho1"][:, :5][fluid[:, :5]] == 1.0).all()
+
+
+def test_block_medium_stand_in():
+    """Block stand-in of Sec. 4.2: 10x10 blocks, porosity at the paper's
+    0.8117, solid walls, block-free reservoirs, gaps between blocks."""
+    m = media.make_block_medium()
+    s = m.solid
+    assert s.shape == (200, 400) and abs(m.porosity - 0.8117) < 0.002
+    assert s[:2].all() and s[-2:].all()
+    assert not s[2:-2, :10].any() and not s[2:-2, -10:].any()
+    for x0, y0 in m.disks.astype(int):
+        assert s[y0:y0 + 10, x0:x0 + 10].all()
+        ring = s[max(y0 - 3, 0):y0 + 13, max(x0 - 3, 0):x0 + 13].sum()
+        assert ring == 100  # nothing else within 3 nodes
+    c = media.config_block_hysteresis(110.0)
+    assert c["xi_value"] == 0.2 and c["xi"][s == 1].max() == np.float32(0.2)
