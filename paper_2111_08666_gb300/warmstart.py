@@ -168,13 +168,33 @@ def train(net, x, t, m, epochs: int = 10, batch: int = 16, lr: float = 1e-3, see
     return hist
 
 
+def blend_densities(rho_prev: np.ndarray, phi_prev: np.ndarray, phi_hat: np.ndarray, fluid: np.ndarray,
+                    flip: float = 0.0):
+    """Densities of a warm start that keeps the previous equilibrium
+    everywhere the network predicts no change of phase: nodes whose
+    predicted phase field has the other sign (by more than ``flip``) take
+    the separated-phase densities of the prediction, the others keep their
+    own (compressibility and interface profiles included)."""
+    p = np.clip(np.asarray(phi_hat, np.float64), -1.0, 1.0)
+    change = fluid & (np.sign(p) != np.sign(phi_prev)) & (np.abs(p) > flip)
+    r1 = RHO_LO + (RHO_HI - RHO_LO) * (1.0 + p) / 2.0
+    r2 = RHO_LO + (RHO_HI - RHO_LO) * (1.0 - p) / 2.0
+    rho1 = np.where(change, r1, rho_prev[0]) * fluid
+    rho2 = np.where(change, r2, rho_prev[1]) * fluid
+    return rho1, rho2, int(change.sum())
+
+
 def compare_warm_cold(net, case: dict, levels: int = 20, d_rho: float = 0.002, window: int = 1000,
-                      tol: float = 1e-6, max_steps: int = 40000, stream=None):
+                      tol: float = 1e-6, max_steps: int = 40000, stream=None, mode: str = "blend"):
     """Quasi-static drainage of one lattice, each pressure level relaxed twice
     from the same equilibrium: cold (the previous equilibrium under the new
-    boundary densities, the protocol of Sec. 4.2) and warm (the lattice
-    re-initialised from the network's predicted phase field).  The cold
-    branch carries the protocol forward.  Returns one record per level."""
+    boundary densities, the protocol of Sec. 4.2) and warm (started from the
+    network's predicted phase field).  mode "phase": the whole lattice
+    re-initialised at rest from the prediction (``mclbm_init_from_phase``);
+    mode "blend": only the nodes predicted to change phase are replaced,
+    the rest keep the previous equilibrium's densities (``blend_densities``).
+    The cold branch carries the protocol forward.  Returns one record per
+    level."""
     import time
 
     def make():
@@ -190,6 +210,7 @@ def compare_warm_cold(net, case: dict, levels: int = 20, d_rho: float = 0.002, w
         return l.diagnostics()["sw_mass"]
 
     relax(cold.step, lambda: sw(cold), window, tol, max_steps)
+    fluid = case["solid"] == 0
     out = []
     for lev in range(1, levels + 1):
         rho_in = case["rho_in1"] + lev * d_rho
@@ -201,7 +222,12 @@ def compare_warm_cold(net, case: dict, levels: int = 20, d_rho: float = 0.002, w
         phi = net.infer(x)[0]
         t_inf = time.perf_counter() - t0
         warm.set_pressure_bc(rho_in, case["rho_out2"])
-        mclbm.mclbm_init_from_phase(warm.h, phi)
+        changed = None
+        if mode == "phase":
+            mclbm.mclbm_init_from_phase(warm.h, phi)
+        else:
+            r1, r2, changed = blend_densities(cold.density(), phase, phi, fluid)
+            warm.init(r1, r2)
         t0 = time.perf_counter()
         n_w, sw_w, ok_w = relax(warm.step, lambda: sw(warm), window, tol, max_steps)
         t_w = time.perf_counter() - t0
@@ -212,7 +238,7 @@ def compare_warm_cold(net, case: dict, levels: int = 20, d_rho: float = 0.002, w
         t_c = time.perf_counter() - t0
         out.append(dict(level=lev, rho_in1=rho_in, sw_before=sw0, steps_cold=n_c, steps_warm=n_w,
                         sw_cold=sw_c, sw_warm=sw_w, converged_cold=ok_c, converged_warm=ok_w,
-                        sec_cold=t_c, sec_warm=t_w, sec_infer=t_inf))
+                        sec_cold=t_c, sec_warm=t_w, sec_infer=t_inf, nodes_changed=changed))
     cold.close()
     warm.close()
     return out
@@ -236,6 +262,7 @@ def main(argv=None) -> None:
     ap.add_argument("--max-steps", type=int, default=40000)
     ap.add_argument("--d-rho", type=float, default=0.002)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--warm-mode", choices=("blend", "phase"), default="blend")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
@@ -251,8 +278,9 @@ def main(argv=None) -> None:
     net.close()
     case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
     rec = compare_warm_cold(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
-                            max_steps=a.max_steps)
-    summary = dict(train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train, loss=hist,
+                            max_steps=a.max_steps, mode=a.warm_mode)
+    summary = dict(warm_mode=a.warm_mode, train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
+                   loss=hist,
                    pair_steps_mean=float(st.mean()),
                    steps_cold=int(sum(r["steps_cold"] for r in rec)),
                    steps_warm=int(sum(r["steps_warm"] for r in rec)),
