@@ -354,11 +354,13 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
                       mclbm_unet **out);
 int mclbm_unet_destroy(mclbm_unet *u);
 int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n);
-/* Upper bound on the CTAs of the persistent row-tile convolution (used for
- * image widths that are multiples of 128); 0 (the default) sizes it to one
- * wave of the GPU.  A small bound makes every CTA walk many tiles, which
- * lets a test cover the multi-tile schedule on small images.  Results do
- * not depend on it.  Errors: MCLBM_ERR_ARG for a NULL network or n < 0. */
+/* Upper bound on the CTAs of the persistent row-tile kernels (convolution
+ * and weight gradient, used for image widths that are multiples of 128); 0
+ * (the default) sizes them to one wave of the GPU.  A small bound makes
+ * every CTA walk many tiles, which lets a test cover the multi-tile
+ * schedule on small images.  Results do not depend on it beyond the order
+ * of the FP32 sums of the weight gradient.  Errors: MCLBM_ERR_ARG for a
+ * NULL network or n < 0. */
 int mclbm_unet_set_max_ctas(mclbm_unet *u, int n);
 /* Copy the parameter vector in (resets the Adam moments) or out. */
 int mclbm_unet_set_params(mclbm_unet *u, const float *theta);

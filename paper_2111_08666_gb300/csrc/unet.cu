@@ -687,6 +687,235 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores, for widths that are multiples of 128:
+//   dW[co][tap][ci] = sum_p dZ[p][co] X[p + d_tap][ci]
+// a GEMM per tap with M = co (a tile of 128, rows past co zero), N = 32
+// input channels, K = pixels.  Both operands stay pixel-major as the forward
+// pass wrote them, read MN-major: dZ of one row tile (128 pixels x 128
+// channels: two 64-channel boxes, 128-byte swizzle) and the same 3 x 130
+// halo of X as the forward convolution (64-byte swizzle), whose K start
+// moves by the tap's offset.  A CTA owns one (co tile, 32-channel chunk) and
+// a strided set of row tiles; its nine accumulators (9 x 32 tensor-memory
+// columns) sum over all of them and are added to dW with FP32 atomics at the
+// end (split K across CTAs).  Roles as in the forward kernel: producer,
+// MMA, expansion (coarse upsampled chunks), epilogue warps.
+// ---------------------------------------------------------------------------
+struct WgradRowArgs {
+    const bf16 *dz;       // [B][H][W][co]
+    int co;
+    const bf16 *x0, *x1;  // the layer's input, as in ConvArgs (x1 coarse, upsampled)
+    int c0, c1;
+    int B, H, W, M;
+    float *dw;            // [co][9][c0 + c1], accumulated into
+    int *err;
+};
+constexpr int WG_A_ATOM = 128 * 128;  // 128 pixels x 64 channels x 2 bytes
+constexpr int WG_A_BYTES = 2 * WG_A_ATOM;
+
+__host__ __device__ inline int wg_stage_bytes(int ux) { return WG_A_BYTES + RA_BYTES + (ux ? RU_BYTES : 0); }
+
+// MN-major shared-memory descriptor, swizzled (layout 2: 128-byte, 4: 64-byte):
+// lbo = stride between MN atoms, sbo = stride between 8-row K groups
+// (measured: these roles, base offset 0 for row-shifted starts)
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | (uint64_t)((lbo >> 4) & 0x3fffu) << 16 |
+           (uint64_t)((sbo >> 4) & 0x3fffu) << 32 | (uint64_t)1 << 46 | (uint64_t)layout << 61;
+}
+
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    wgrad_row_kernel(const WgradRowArgs a, const int S, const int ux, const __grid_constant__ CUtensorMap tdz,
+                     const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmu) {
+    constexpr uint32_t COLS = 512;  // nine 32-column accumulators
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (smem_u32(smem) & 1023u) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+        return;
+    }
+    const int K0 = a.c0 + a.c1;
+    const int STG = wg_stage_bytes(ux);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * STG);
+    uint64_t *done = full + 4, *expd = full + 8, *accf = full + 12, *drain = full + 13;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 14);
+    int *flag = reinterpret_cast<int *>(full + 15);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mtiles = (a.co + 127) / 128, chunks = K0 / 32, combos = mtiles * chunks;
+    const int combo = blockIdx.x % combos, mt = combo / chunks, cc = combo - mt * chunks;
+    const int m0 = mt * 128;
+    const int tile0 = blockIdx.x / combos, tstride = gridDim.x / combos;
+    const int segs = a.W / RW, ntiles = a.M / RW;
+    const int njobs = tile0 < ntiles ? (ntiles - tile0 + tstride - 1) / tstride : 0;
+    const bool direct = cc * 32 < a.c0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < 4; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&done[k], 1);
+            mbar_init(&expd[k], ROW_EXP);
+        }
+        mbar_init(accf, 1);
+        mbar_init(drain, 1);
+        *flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    struct Where {
+        int x0, y, b;
+    };
+    auto where = [&](int i) {
+        const int t = tile0 + i * tstride;
+        return Where{(t % segs) * RW, (t / segs) % a.H, t / (segs * a.H)};
+    };
+    auto give_up = [&]() {
+        *(volatile int *)flag = 1;
+        if (a.err) atomicExch(a.err, 1);
+    };
+    auto stopped = [&]() { return *(volatile int *)flag != 0; };
+
+    if (warp == 0) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int j = 0;
+            for (; j < njobs && !stopped(); ++j) {
+                const int st = j % S;
+                if (j >= S && !mbar_wait_sleep(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+                    give_up();
+                    break;
+                }
+                const Where w = where(j);
+                unsigned char *As = smem + st * STG, *Hs = As + WG_A_BYTES;
+                mbar_expect_tx(&full[st], 2 * (128 * 64 * 2) + (direct ? RHALO_TX : RU_TX));
+                tma_load_4d(As, &tdz, m0, w.x0, w.y, w.b, &full[st]);
+                tma_load_4d(As + WG_A_ATOM, &tdz, m0 + 64, w.x0, w.y, w.b, &full[st]);
+                if (direct)
+                    tma_load_4d(Hs, &tmx, cc * 32, w.x0 - 1, w.y - 1, w.b, &full[st]);
+                else
+                    tma_load_4d(Hs + RA_BYTES, &tmu, cc * 32 - a.c0, (w.x0 >> 1) - 1, (w.y - 1) >> 1, w.b,
+                                &full[st]);
+            }
+            for (int jb = j - 1; jb >= 0 && jb >= j - S; --jb) mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                       ((32u >> 3) << 17) | ((128u >> 4) << 24);  // MN-major A and B
+            bool ok = true;
+            for (int j = 0; j < njobs && !stopped(); ++j) {
+                const int st = j % S;
+                ok = mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
+                if (ok && !direct) ok = mbar_wait_sleep(&expd[st], (j / S) & 1, WAIT_LIMIT_NS);
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t As = smem_u32(smem + st * STG), Hs = As + WG_A_BYTES;
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int sh = (tap / 3) * RHALO + tap % 3;  // (dy + 1) rows, dx + 1 pixels
+#pragma unroll
+                    for (int k = 0; k < RW / 16; ++k) {
+                        const uint64_t ad = umma_desc_mn(As + k * 16 * 128, WG_A_ATOM, 1024, 2);
+                        const uint64_t bd = umma_desc_mn(Hs + (sh + k * 16) * 64, 16, 512, 4);
+                        const uint32_t accum = (j > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + tap * 32),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&done[st]))
+                             : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(accf))
+                         : "memory");
+        }
+    } else if (warp < 6) {
+        // ---------------- expansion of coarse upsampled chunks ----------------
+        const int et = tid - 64, qq = et & 3;
+        for (int j = 0; !direct && j < njobs && !stopped(); ++j) {
+            const int st = j % S;
+            if ((j >= S && !mbar_wait_sleep(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) ||
+                !mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
+                give_up();
+                break;
+            }
+            const Where w = where(j);
+            unsigned char *Hs = smem + st * STG + WG_A_BYTES;
+            const unsigned char *U = Hs + RA_BYTES;
+            const uint32_t hbase = smem_u32(Hs);
+            for (int r = 0; r < 3; ++r) {
+                const int cr = ((w.y + r - 1) >> 1) - ((w.y - 1) >> 1);
+                for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
+                    const int pix = r * RHALO + p;
+                    const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);
+                    *reinterpret_cast<uint4 *>(Hs + pix * 64 + ((qq ^ sw) << 4)) =
+                        *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&expd[st]);
+        }
+    } else {
+        // ---------------- epilogue: add the nine accumulators to dW ----------------
+        if (njobs > 0 && mbar_wait_sleep(accf, 0, WAIT_LIMIT_NS) && !stopped()) {
+            tc_fence_after();
+            const int ew = warp & 3;
+            const int row = m0 + ew * 32 + lane;  // output channel
+            for (int tap = 0; tap < 9; ++tap) {
+                uint32_t r[32];
+#pragma unroll
+                for (int c = 0; c < 32; c += 16) {
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(r[c]), "=r"(r[c + 1]), "=r"(r[c + 2]), "=r"(r[c + 3]), "=r"(r[c + 4]), "=r"(r[c + 5]),
+                          "=r"(r[c + 6]), "=r"(r[c + 7]), "=r"(r[c + 8]), "=r"(r[c + 9]), "=r"(r[c + 10]),
+                          "=r"(r[c + 11]), "=r"(r[c + 12]), "=r"(r[c + 13]), "=r"(r[c + 14]), "=r"(r[c + 15])
+                        : "r"(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(tap * 32 + c)));
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < a.co) {
+                    float *d = a.dw + ((size_t)row * 9 + tap) * K0 + cc * 32;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) atomicAdd(d + c, __uint_as_float(r[c]));
+                }
+            }
+            tc_fence_before();
+        } else if (njobs > 0 && !stopped()) {
+            give_up();
+        }
+    }
+    if (warp == 1 && lane == 0 && stopped()) {
+        // one last commit tracks every MMA issued: a short wait before the
+        // tensor memory is released
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(drain))
+                     : "memory");
+        mbar_wait(drain, 0, DRAIN_LIMIT_NS);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient of one tap: dW[co][tap][ci] += sum_pixel dZ[p][co] X[p + d][ci]
 // over a chunk of pixels per CTA (atomic FP32 accumulation of the chunks).
 // ---------------------------------------------------------------------------
@@ -1156,7 +1385,7 @@ struct mclbm_unet {
     float *xin_f = nullptr, *t_f = nullptr, *mask_f = nullptr;  // staging of host inputs
     double *loss_part = nullptr, *loss_stat = nullptr;
     int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
-    int max_ctas = 0;    // bound on the row-tile convolution's CTAs (0: one wave)
+    int max_ctas = 0;    // bound on the row-tile kernels' CTAs (0: one wave)
     std::vector<void *> allocs;
     int cur_b = 0, cur_h = 0, cur_w = 0;
 };
@@ -1246,21 +1475,33 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// tensor map of an NHWC BF16 tensor [B][H][W][C] read in boxes of 32
-// channels x bw pixels x bh rows x 1 image (64-byte rows, swizzled or not),
-// zero fill outside
-cudaError_t nhwc_map(const bf16 *base, int B, int H, int W, int C, int bw, int bh, bool sw64, CUtensorMap *m) {
+// tensor map of an NHWC BF16 tensor [B][H][W][C] read in boxes of box_c
+// channels x bw pixels x bh rows x 1 image, zero fill outside
+cudaError_t nhwc_map(const bf16 *base, int B, int H, int W, int C, int box_c, int bw, int bh,
+                     CUtensorMapSwizzle sw, CUtensorMap *m) {
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
     const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
-    const cuuint32_t box[4] = {32, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)bw, (cuuint32_t)bh, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// the halo maps of a convolution input: x0 in swizzled boxes of 32 channels
+// x 130 pixels x 3 rows; x1 likewise when at full resolution, else in plain
+// boxes of 66 coarse pixels x 2 rows
+cudaError_t halo_maps(const bf16 *x0, const bf16 *x1, int c0, int c1, int x1_full, int B, int H, int W,
+                      CUtensorMap *tmx, CUtensorMap *tmu) {
+    constexpr auto SW64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    cudaError_t e = nhwc_map(x0, B, H, W, c0, 32, RHALO, 3, SW64, tmx);
+    if (e != cudaSuccess) return e;
+    if (c1 == 0) return nhwc_map(x0, B, H, W, c0, 32, RHALO, 3, SW64, tmu);
+    if (x1_full) return nhwc_map(x1, B, H, W, c1, 32, RHALO, 3, SW64, tmu);
+    return nhwc_map(x1, B, H >> 1, W >> 1, c1, 32, 66, 2, CU_TENSOR_MAP_SWIZZLE_NONE, tmu);
 }
 
 template <int BN>
@@ -1293,14 +1534,8 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     if (grid > items) grid = items;
     grid -= grid % ntn;
     if (grid < ntn) grid = ntn;
-    // the direct input in swizzled halo boxes (130 pixels x 3 rows); the
-    // coarse input of an upsampled concat in plain boxes of 66 pixels x 2 rows
     CUtensorMap tmx, tmu;
-    cudaError_t e = nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmx);
-    if (e == cudaSuccess)
-        e = a.c1 == 0   ? nhwc_map(a.x0, a.B, a.H, a.W, a.c0, RHALO, 3, true, &tmu)
-            : a.x1_full ? nhwc_map(a.x1, a.B, a.H, a.W, a.c1, RHALO, 3, true, &tmu)
-                        : nhwc_map(a.x1, a.B, a.H >> 1, a.W >> 1, a.c1, 66, 2, false, &tmu);
+    cudaError_t e = halo_maps(a.x0, a.x1, a.c0, a.c1, a.x1_full, a.B, a.H, a.W, &tmx, &tmu);
     if (e != cudaSuccess) return e;
     conv_row_kernel<BN><<<(int)grid, ROW_THREADS, plan.smem, u.stream>>>(a, plan, a.wp, tmx, tmu);
     count_launch();
@@ -1333,7 +1568,54 @@ cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
     }
 }
 
+// the weight gradient on the tensor cores where the width is a multiple of
+// 128 (row tiles), else on mma.sync
+cudaError_t launch_wgrad_row(const mclbm_unet &u, const WgradArgs &w) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(wgrad_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ROW_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(wgrad_row_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    WgradRowArgs a{};
+    a.dz = w.dz;
+    a.co = w.co;
+    a.x0 = w.x0;
+    a.x1 = w.x1;
+    a.c0 = w.c0;
+    a.c1 = w.c1;
+    a.B = w.B;
+    a.H = w.H;
+    a.W = w.W;
+    a.M = w.M;
+    a.dw = w.dw;
+    a.err = u.err;
+    const int ux = w.c1 > 0 ? 1 : 0;
+    int S = (ROW_SMEM_MAX - 256) / wg_stage_bytes(ux);
+    if (S > 4) S = 4;
+    if (S < 2) return cudaErrorInvalidConfiguration;
+    const int smem = S * wg_stage_bytes(ux) + 256;
+    CUtensorMap tdz, tmx, tmu;
+    cudaError_t e = nhwc_map(w.dz, w.B, w.H, w.W, w.co, 64, RW, 1, CU_TENSOR_MAP_SWIZZLE_128B, &tdz);
+    if (e == cudaSuccess) e = halo_maps(w.x0, w.x1, w.c0, w.c1, 0, w.B, w.H, w.W, &tmx, &tmu);
+    if (e != cudaSuccess) return e;
+    const int combos = ((w.co + 127) / 128) * ((w.c0 + w.c1) / 32);
+    int grid = sm_count();
+    if (u.max_ctas > 0 && grid > u.max_ctas) grid = u.max_ctas;
+    if (grid > combos * (w.M / RW)) grid = combos * (w.M / RW);
+    grid -= grid % combos;
+    if (grid < combos) grid = combos;
+    wgrad_row_kernel<<<grid, ROW_THREADS, smem, u.stream>>>(a, S, ux, tdz, tmx, tmu);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wgrad(const mclbm_unet &u, WgradArgs a) {
+    if (a.W % RW == 0 && a.c0 % 32 == 0 && a.c1 % 32 == 0) return launch_wgrad_row(u, a);
     a.chunk = 4096;
     const int parts = (a.M + a.chunk - 1) / a.chunk;
     const dim3 grid((a.co + 63) / 64, (a.c0 + a.c1 + 63) / 64, 9 * parts);
