@@ -18,10 +18,11 @@
 //   wgrad    C[co][ci]    = sum_pixel dZ[pixel][co] X[pixel + d_tap][ci]  (per tap)
 // with operands gathered into shared memory by cp.async (zero fill at the
 // image border; the decoder's concat and upsampling are folded into the
-// gather).  Forward and dgrad run on tcgen05 (accumulator in tensor
-// memory); wgrad, a reduction over all pixels split across CTAs, on
-// mma.sync m16n8k16 with ldmatrix.trans fragments.  Pooling, the head, the
-// loss and Adam are elementwise kernels.
+// gather).  All three run on tcgen05 with accumulators in tensor memory:
+// for widths that are multiples of 128 as persistent row-tile kernels fed
+// by tensor copies (conv_row_kernel, wgrad_row_kernel), else as a per-pixel
+// gather kernel (forward, dgrad) and mma.sync m16n8k16 (wgrad).  Pooling,
+// the head, the loss and Adam are elementwise kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
