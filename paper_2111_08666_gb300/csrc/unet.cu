@@ -574,14 +574,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 const uint32_t As = smem_u32(stg + st * STG);
                 const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES + (plan.ux ? RU_BYTES : 0);
                 const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
-#pragma unroll 1
+                // descriptors of the stage's operands; a start moved by b bytes
+                // adds b / 16 to the address field (no carry: below 256 KB)
+                const uint64_t ad0 = umma_desc_sw64(As, 512), bd0 = umma_desc(Bs, 128, 512);
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
-                    const uint32_t a0 = As + ((dy + 1) * RHALO + dx + 1) * 64;
+                    const int aoff = ((dy + 1) * RHALO + dx + 1) * 64;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint64_t ad = umma_desc_sw64(a0 + h * 32, 512);
-                        const uint64_t bd = umma_desc(Bs + tap * BN * 64 + h * 256, 128, 512);
+                        const uint64_t ad = ad0 + (uint64_t)((aoff + h * 32) / 16);
+                        const uint64_t bd = bd0 + (uint64_t)((tap * BN * 64 + h * 256) / 16);
                         const uint32_t accum = (kc > 0 || tap > 0 || h > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -821,13 +824,17 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t As = smem_u32(smem + st * STG), Hs = As + WG_A_BYTES;
-#pragma unroll 1
+                // descriptors of the stage's operands; a start moved by b bytes
+                // adds b / 16 to the address field (no carry: below 256 KB)
+                const uint64_t ad0 = umma_desc_mn(As, WG_A_ATOM, 1024, 2);
+                const uint64_t bd0 = umma_desc_mn(Hs, 16, 512, 4);
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int sh = (tap / 3) * RHALO + tap % 3;  // (dy + 1) rows, dx + 1 pixels
 #pragma unroll
                     for (int k = 0; k < RW / 16; ++k) {
-                        const uint64_t ad = umma_desc_mn(As + k * 16 * 128, WG_A_ATOM, 1024, 2);
-                        const uint64_t bd = umma_desc_mn(Hs + (sh + k * 16) * 64, 16, 512, 4);
+                        const uint64_t ad = ad0 + (uint64_t)(k * 16 * 128 / 16);
+                        const uint64_t bd = bd0 + (uint64_t)((sh + k * 16) * 64 / 16);
                         const uint32_t accum = (j > 0 || k > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
