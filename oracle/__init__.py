@@ -30,7 +30,9 @@ class Params(C.Structure):
                 ("rho_in1", C.c_double), ("rho_out2", C.c_double),
                 ("open_x", C.c_int), ("periodic_y", C.c_int),
                 ("vel_shift", C.c_int), ("bc_set", C.c_int),
-                ("rho_in2", C.c_double), ("rho_out1", C.c_double)]
+                ("rho_in2", C.c_double), ("rho_out1", C.c_double),
+                ("mrt", C.c_int), ("pad2", C.c_int),
+                ("s_e", C.c_double), ("s_eps", C.c_double), ("s_q", C.c_double)]
 
 
 def build(force: bool = False) -> Path:
@@ -112,7 +114,8 @@ class Oracle:
                  g_coh: float = 3.5, g_ads: float | None = None, gx: float = 0.0,
                  gy: float = 0.0, rho_in1: float = -1.0, rho_out2: float = -1.0,
                  periodic_y: bool = False, vel_shift: bool = True, bc_set: int = 3,
-                 rho_in2: float = 0.0, rho_out1: float = 0.0):
+                 rho_in2: float = 0.0, rho_out1: float = 0.0, mrt: bool = False,
+                 s_e: float = 0.0, s_eps: float = 0.0, s_q: float = 0.0):
         self.solid = np.ascontiguousarray(solid, dtype=np.uint8)
         self.ny, self.nx = self.solid.shape
         self.xi = np.ascontiguousarray(xi, dtype=np.float32)
@@ -120,7 +123,8 @@ class Oracle:
         self.p = Params(self.nx, self.ny, nu1, nu2, g_coh,
                         g_coh if g_ads is None else g_ads, gx, gy,
                         rho_in1, rho_out2, int(open_x), int(periodic_y),
-                        int(vel_shift), int(bc_set), rho_in2, rho_out1)
+                        int(vel_shift), int(bc_set), rho_in2, rho_out1, int(mrt), 0,
+                        s_e, s_eps, s_q)
         self.f = np.zeros((2, 9, self.ny, self.nx))
         # frozen boundary values: component 1's outlet f_{3,6,7} (Eq. 26, rows
         # 0-2) and component 2's inlet f_{1,5,8} (Eq. 27, rows 3-5)
@@ -134,6 +138,12 @@ class Oracle:
         fixes component 2 at the inlet (rho_in2) and component 1 at the
         outlet (rho_out1)."""
         self.p.bc_set, self.p.rho_in2, self.p.rho_out1 = int(bc_set), rho_in2, rho_out1
+
+    def set_mrt(self, on: bool, s_e: float = 0.0, s_eps: float = 0.0, s_q: float = 0.0) -> None:
+        """MRT collision (not in the paper): rates of the energy, energy-square
+        and heat-flux moments; 0 ties a rate to 1/tau_s, s_q = -1 takes
+        8 (2 - w) / (8 - w)."""
+        self.p.mrt, self.p.s_e, self.p.s_eps, self.p.s_q = int(on), s_e, s_eps, s_q
 
     def set_pressure_bc(self, rho_in1: float, rho_out2: float) -> None:
         self.p.rho_in1, self.p.rho_out2 = rho_in1, rho_out2

@@ -38,6 +38,15 @@
  *             outlet; Eq. 26 at the outlet and Eq. 27 at the inlet for the
  *             other component;
  *      Set-3 (the paper's, the default): as Set-2 but Eq. 28 at the inlet.
+ *  - Multiple-relaxation-time collision (mrt = 1; not in the paper, which
+ *    uses the SRT of Eq. 1): Eq. 1 with the scalar 1/tau_s replaced by a
+ *    relaxation matrix diagonal in the moment basis of Lallemand and Luo,
+ *      f* = f - M^-1 S M (f - f^eq) + M^-1 (I - S/2) M S^F,
+ *    S = diag(1, s_e, s_eps, w, s_q, w, s_q, w, w) with w = 1/tau_s (Eq. 6)
+ *    on the momentum and stress moments; s_e, s_eps, s_q fixed rates, or 0
+ *    for "w" (then the operator is the SRT one exactly), s_q = -1 for
+ *    8 (2 - w) / (8 - w), which with s_e = s_eps = w puts half-way
+ *    bounce-back walls exactly half-way for Poiseuille flow at any tau.
  *  - Zou-He (Eqs. 18-25) prescribes zero tangential velocity; u_x follows
  *    from the prescribed density.  Directions whose source lies beyond the
  *    open x ends are "missing"; directions whose source is solid are filled
@@ -76,6 +85,9 @@ typedef struct {
     int bc_set;             /* 1, 2 or 3 (0 counts as 3): treatment of Sec. 2.3 */
     double rho_in2;         /* Set-1 inlet density of component 2 */
     double rho_out1;        /* Set-1 outlet density of component 1 */
+    int mrt;                /* 0: SRT collision of Eq. 1; 1: MRT (see header) */
+    int pad2;
+    double s_e, s_eps, s_q; /* MRT rates of the energy, energy-square and heat-flux moments */
 } oracle_params;
 
 #define IDX(p, y, x) ((size_t)(y) * (size_t)(p)->nx + (size_t)(x))
@@ -112,6 +124,41 @@ void oracle_source(double ux, double uy, double fx, double fy, double *s) {
         double ax = (EX[i] - ux) * INV_CS2 + eu * EX[i] * INV_CS4;
         double ay = (EY[i] - uy) * INV_CS2 + eu * EY[i] * INV_CS4;
         s[i] = WGT[i] * (ax * fx + ay * fy);
+    }
+}
+
+/* Moment basis of the MRT collision (Lallemand and Luo): rows rho, e, eps,
+ * j_x, q_x, j_y, q_y, p_xx, p_xy in the direction order of EX/EY; the rows
+ * are orthogonal, so M^-1 = M^T diag(1 / |row|^2). */
+static const double MRT_M[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},        {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},     {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},     {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+static const double MRT_NORM2[9] = {9, 36, 36, 6, 12, 6, 12, 4, 4};
+
+/* f* of one component at one node by the MRT operator (header): the
+ * deviation from equilibrium and the source are taken to moment space with
+ * M, weighted by S and (I - S/2), and brought back with M^-1. */
+static void mrt_collide(const oracle_params *p, double omega, const double *f, const double *feq,
+                        const double *src, double *out) {
+    double sq = p->s_q < 0.0 ? 8.0 * (2.0 - omega) / (8.0 - omega) : (p->s_q > 0.0 ? p->s_q : omega);
+    double rate[9] = {1.0, p->s_e > 0.0 ? p->s_e : omega, p->s_eps > 0.0 ? p->s_eps : omega, omega, sq,
+                      omega, sq, omega, omega};
+    double g[9];
+    for (int k = 0; k < 9; ++k) {
+        double dev = 0.0, sm = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            dev += MRT_M[k][i] * (f[i] - feq[i]);
+            sm += MRT_M[k][i] * src[i];
+        }
+        g[k] = rate[k] * dev - (1.0 - 0.5 * rate[k]) * sm;
+    }
+    for (int i = 0; i < 9; ++i) {
+        double back = 0.0;
+        for (int k = 0; k < 9; ++k) back += MRT_M[k][i] * g[k] / MRT_NORM2[k];
+        out[i] = f[i] - back;
     }
 }
 
@@ -385,6 +432,13 @@ void oracle_collide(const oracle_params *p, const uint8_t *solid, const double *
                 double feq[9], s[9];
                 oracle_feq(rho[(size_t)c * n + id], ux, uy, feq);
                 oracle_source(ux, uy, fx[(size_t)c * n + id], fy[(size_t)c * n + id], s);
+                if (p->mrt) {
+                    double fin[9], fout[9];
+                    for (int i = 0; i < 9; ++i) fin[i] = f[FIDX(p, c, i, y, x)];
+                    mrt_collide(p, omega, fin, feq, s, fout);
+                    for (int i = 0; i < 9; ++i) fpost[FIDX(p, c, i, y, x)] = fout[i];
+                    continue;
+                }
                 for (int i = 0; i < 9; ++i) {
                     double fi = f[FIDX(p, c, i, y, x)];
                     fpost[FIDX(p, c, i, y, x)] =

@@ -466,3 +466,67 @@ def test_contact_angle_neutral_and_symmetric():
     assert tm == pytest.approx(pairs[-0.3], abs=8.0)
     assert tp == pytest.approx(pairs[0.3], abs=8.0)
 
+
+
+# --- MRT collision (not in the paper; the SRT of Eq. 1 with a moment-space
+# --- relaxation matrix) ---------------------------------------------------------
+
+def test_mrt_with_all_rates_tied_is_the_srt_operator():
+    """With every free rate tied to 1/tau_s, M^-1 S M = S: the MRT step is
+    the SRT step of Eq. 1 up to rounding (a wrong row of M, of its norm or
+    of the source weighting breaks this)."""
+    a = _closed_droplet_box(-0.3, nu_of_tau(1.7), nu_of_tau(0.62))
+    b = _closed_droplet_box(-0.3, nu_of_tau(1.7), nu_of_tau(0.62))
+    b.set_mrt(True, 0.0, 0.0, 0.0)
+    a.step(300)
+    b.step(300)
+    assert np.max(np.abs(a.f - b.f)) < 1e-12 * np.max(np.abs(a.f))
+    c = _closed_droplet_box(-0.3, nu_of_tau(1.7), nu_of_tau(0.62))
+    c.set_mrt(True, 1.1, 1.2, -1.0)
+    c.step(300)
+    assert np.max(np.abs(c.f - a.f)) > 1e-6 * np.max(np.abs(a.f))  # and it is not the SRT otherwise
+
+
+@pytest.mark.parametrize("rates", [(1.0, 1.0, -1.0), (1.64, 1.54, 1.2)])
+def test_mrt_conserves_mass_and_momentum_balance(rates):
+    o = _closed_droplet_box(-0.4, nu_of_tau(3.5), nu_of_tau(0.62))
+    o.set_mrt(True, *rates)
+    d0 = o.diagnostics()
+    o.step(1500)
+    d1 = o.diagnostics()
+    assert abs(d1["mass1"] / d0["mass1"] - 1) < 1e-12 and abs(d1["mass2"] / d0["mass2"] - 1) < 1e-12
+    n = m = 24
+    g = (1e-5, -4e-6)
+    rho1, rho2 = media.droplet_densities(n, m, 12, 12, 6)
+    p = _periodic(n, m, nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), gx=g[0], gy=g[1], mrt=True,
+                  s_e=rates[0], s_eps=rates[1], s_q=rates[2])
+    p.init(rho1, rho2)
+    p.step(30)
+    mom = lambda f: np.einsum("ai,cixy->a", E, f)
+    p0, mass = mom(p.f), p.f.sum()
+    p.step(1)
+    assert mom(p.f) - p0 == pytest.approx([g[0] * mass, g[1] * mass], rel=1e-9, abs=1e-15)
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.9, 2.0])
+def test_mrt_poiseuille_exact_at_any_tau_with_tied_heat_flux_rate(tau):
+    """Even moments relaxed at w = 1/tau_s and the heat flux at s_q =
+    8 (2 - w) / (8 - w) (a two-relaxation-time operator whose odd- and
+    even-mode parameters multiply to 3/16): half-way bounce-back walls then
+    sit exactly half-way and the body-force parabola is exact for any tau,
+    where the SRT is exact only at tau = 1/2 + sqrt(3/16)."""
+    n, m = 4, 18
+    solid = np.zeros((m, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    nu, g = nu_of_tau(tau), 1e-6
+    o = oracle.Oracle(solid, np.zeros((m, n), np.float32), nu1=nu, nu2=0.1, gx=g, mrt=True,
+                      s_e=0.0, s_eps=0.0, s_q=-1.0)
+    o.init(np.ones((m, n)) * (solid == 0), np.zeros((m, n)))
+    o.step(int(6000 / min(1.0, nu * 6)))
+    y = np.arange(m, dtype=float)
+    u_exact = g / (2 * nu) * (y - 0.5) * (m - 1.5 - y)
+    assert np.max(np.abs(o.ux[1:-1, 2] - u_exact[1:-1])) < 1e-9 * u_exact.max()
+    s = oracle.Oracle(solid, np.zeros((m, n), np.float32), nu1=nu, nu2=0.1, gx=g)
+    s.init(np.ones((m, n)) * (solid == 0), np.zeros((m, n)))
+    s.step(int(6000 / min(1.0, nu * 6)))
+    assert np.max(np.abs(s.ux[1:-1, 2] - u_exact[1:-1])) > 1e-4 * u_exact.max()  # the SRT is not
