@@ -147,6 +147,19 @@ int mclbm_set_pressure_bc(mclbm_lattice *lat, double rho_in1, double rho_out2);
  * finite. */
 int mclbm_set_bc(mclbm_lattice *lat, int bc_set, double rho_in2, double rho_out1);
 
+/* Multiple-relaxation-time collision (not in the paper, which uses the SRT
+ * of Eq. 1; offered for viscosity ratios beyond its runs).  on = 0 restores
+ * Eq. 1.  With on = 1 the collision is
+ *   f* = f - M^-1 S M (f - f^eq) + M^-1 (I - S/2) M S^F
+ * in the D2Q9 moment basis of Lallemand and Luo (rho, e, eps, j_x, q_x,
+ * j_y, q_y, p_xx, p_xy), S = diag(-, s_e, s_eps, w, s_q, w, s_q, w, w) and
+ * w = 1/tau_s from Eq. 6, f^eq of Eq. 2 and S^F of Eq. 11 with the same
+ * velocity as the SRT.  Each rate lies in (0, 2), or is 0 for w (all three
+ * 0: the SRT operator, up to rounding); s_q = -1 selects 8 (2 - w) / (8 - w),
+ * which with s_e = s_eps = 0 makes half-way bounce-back exact for Poiseuille
+ * flow at any tau.  Errors: MCLBM_ERR_ARG for a rate outside those values. */
+int mclbm_set_mrt(mclbm_lattice *lat, int on, double s_e, double s_eps, double s_q);
+
 /* The same boundaries given as pressures: Eq. 14 is inverted for the
  * majority density with the minority density held at 0.027 (the dissolved
  * density at G = 3.5, Sec. 3.2).  A negative pressure switches them off. */

@@ -440,6 +440,20 @@ int mclbm_set_bc(mclbm_lattice *lat, int bc_set, double rho_in2, double rho_out1
     return MCLBM_OK;
 }
 
+int mclbm_set_mrt(mclbm_lattice *lat, int on, double s_e, double s_eps, double s_q) {
+    if (int rc = check_lat(lat)) return rc;
+    auto rate_ok = [](double s) { return s == 0.0 || (s > 0.0 && s < 2.0); };
+    if (on && (!rate_ok(s_e) || !rate_ok(s_eps) || !(rate_ok(s_q) || s_q == -1.0)))
+        return fail(MCLBM_ERR_ARG, "MRT rates must lie in (0, 2), or be 0 (1/tau_s); s_q may be -1");
+    ++lat->version;
+    lat->p.mrt = on ? 1 : 0;
+    lat->p.s_e = on ? s_e : 0.0;
+    lat->p.s_eps = on ? s_eps : 0.0;
+    lat->p.s_q = on ? s_q : 0.0;
+    lat->p.round_fp32();
+    return MCLBM_OK;
+}
+
 int mclbm_set_pressure_bc_p(mclbm_lattice *lat, double p_in, double p_out) {
     if (int rc = check_lat(lat)) return rc;
     if (p_in < 0 || p_out < 0) return mclbm_set_pressure_bc(lat, -1.0, -1.0);

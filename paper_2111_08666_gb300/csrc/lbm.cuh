@@ -90,11 +90,14 @@ struct Params {
     int vel_shift = 1;   // u carries F/2
     int bc_set = 3;      // inlet/outlet treatment of Sec. 2.3: Set-1, -2 or -3
     double rho_in2 = 0.0, rho_out1 = 0.0;  // Set-1: the other component's densities
+    int mrt = 0;         // 0: SRT collision of Eq. 1; 1: multiple-relaxation-time variant
+    double s_e = 0.0, s_eps = 0.0, s_q = 0.0;  // MRT rates (0: 1/tau_s; s_q -1: 8(2-w)/(8-w))
     // the same values rounded to FP32 once on the host: the FP32 kernels
     // read these rather than converting from FP64 at every node (such a
     // conversion occupies the narrow FP64 pipe)
     float nu1_f = 0, nu2_f = 0, g_coh_f = 0, g_ads_f = 0, gx_f = 0, gy_f = 0;
     float rho_in1_f = 0, rho_out2_f = 0, rho_in2_f = 0, rho_out1_f = 0;
+    float s_e_f = 0, s_eps_f = 0, s_q_f = 0;
     void round_fp32() {
         nu1_f = (float)nu1;
         nu2_f = (float)nu2;
@@ -106,6 +109,9 @@ struct Params {
         rho_out2_f = (float)rho_out2;
         rho_in2_f = (float)rho_in2;
         rho_out1_f = (float)rho_out1;
+        s_e_f = (float)s_e;
+        s_eps_f = (float)s_eps;
+        s_q_f = (float)s_q;
     }
 };
 

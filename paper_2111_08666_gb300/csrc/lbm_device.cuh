@@ -312,4 +312,71 @@ __device__ __forceinline__ void collide_pair(R f[2][9], R rho1, R rho2, R ux, R 
     f[1][0] = rho2 - r2;
 }
 
+// Multiple-relaxation-time variant of the collision (not in the paper,
+// which uses the SRT of Eq. 1): Eq. 1 with 1/tau_s replaced by a relaxation
+// matrix diagonal in the moment basis of Lallemand and Luo,
+//   m = (rho, e, eps, j_x, q_x, j_y, q_y, p_xx, p_xy) = M f,
+//   m* = m - S (m - m^eq) + (I - S/2) M S^F,   f* = M^-1 m*,
+// S = diag(-, s_e, s_eps, w, s_q, w, s_q, w, w), w = 1/tau_s.  The moments
+// of f^eq (Eq. 2) and of the source (Eq. 11) are taken in closed form:
+//   e^eq = rho (3 u.u - 2), eps^eq = rho (1 - 3 u.u), j^eq = rho u,
+//   q^eq = -rho u, p_xx^eq = rho (u_x^2 - u_y^2), p_xy^eq = rho u_x u_y;
+//   source: e 6 u.F, eps -6 u.F, j F, q -F, p_xx 2 (u_x F_x - u_y F_y),
+//   p_xy u_x F_y + u_y F_x.
+// The rows of M are orthogonal with squared norms (9, 36, 36, 6, 12, 6, 12,
+// 4, 4), which gives M^-1 = M^T diag(1 / norm).  f*_0 follows from mass.
+template <class R>
+__device__ __forceinline__ void mrt_one(R g[9], R rho, R ux, R uy, R fx, R fy, R w, R se, R seps, R sq) {
+    const R ax = g[1] + g[2] + g[3] + g[4], dg = g[5] + g[6] + g[7] + g[8];
+    const R uu = ux * ux + uy * uy, uf = ux * fx + uy * fy;
+    const R e = R(-4) * g[0] - ax + R(2) * dg;
+    const R eps = R(4) * g[0] - R(2) * ax + dg;
+    const R jx = g[1] - g[3] + g[5] - g[6] - g[7] + g[8];
+    const R jy = g[2] - g[4] + g[5] + g[6] - g[7] - g[8];
+    const R qx = R(-2) * (g[1] - g[3]) + g[5] - g[6] - g[7] + g[8];
+    const R qy = R(-2) * (g[2] - g[4]) + g[5] + g[6] - g[7] - g[8];
+    const R pxx = g[1] - g[2] + g[3] - g[4];
+    const R pxy = g[5] - g[6] + g[7] - g[8];
+    auto relax = [](R m, R meq, R s, R src) { return m - s * (m - meq) + (R(1) - R(0.5) * s) * src; };
+    const R e2 = relax(e, rho * (R(3) * uu - R(2)), se, R(6) * uf);
+    const R eps2 = relax(eps, rho * (R(1) - R(3) * uu), seps, R(-6) * uf);
+    const R jx2 = relax(jx, rho * ux, w, fx), jy2 = relax(jy, rho * uy, w, fy);
+    const R qx2 = relax(qx, -rho * ux, sq, -fx), qy2 = relax(qy, -rho * uy, sq, -fy);
+    const R pxx2 = relax(pxx, rho * (ux * ux - uy * uy), w, R(2) * (ux * fx - uy * fy));
+    const R pxy2 = relax(pxy, rho * ux * uy, w, ux * fy + uy * fx);
+    const R r9 = rho * (R(1) / R(9));
+    const R ea = r9 - e2 * (R(1) / R(36)) - eps2 * (R(1) / R(18));  // common part of the axis directions
+    const R ed = r9 + e2 * (R(1) / R(18)) + eps2 * (R(1) / R(36));  // of the diagonals
+    const R jx6 = jx2 * (R(1) / R(6)), jy6 = jy2 * (R(1) / R(6));
+    const R qx6 = qx2 * (R(1) / R(6)), qy6 = qy2 * (R(1) / R(6));
+    const R qx12 = qx2 * (R(1) / R(12)), qy12 = qy2 * (R(1) / R(12));
+    const R pxx4 = pxx2 * R(0.25), pxy4 = pxy2 * R(0.25);
+    g[1] = ea + jx6 - qx6 + pxx4;
+    g[2] = ea + jy6 - qy6 - pxx4;
+    g[3] = ea - jx6 + qx6 + pxx4;
+    g[4] = ea - jy6 + qy6 - pxx4;
+    g[5] = ed + jx6 + qx12 + jy6 + qy12 + pxy4;
+    g[6] = ed - jx6 - qx12 + jy6 + qy12 - pxy4;
+    g[7] = ed - jx6 - qx12 - jy6 - qy12 + pxy4;
+    g[8] = ed + jx6 + qx12 - jy6 - qy12 - pxy4;
+    g[0] = rho - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8]);
+}
+
+// The collision of both components: the SRT of Eq. 1 (collide_pair), or the
+// MRT variant when the lattice asks for it.
+template <class R>
+__device__ __forceinline__ void collide(const Params &p, R f[2][9], R rho1, R rho2, R ux, R uy, R fx1, R fy1,
+                                        R fx2, R fy2, R omega) {
+    if (!p.mrt) {
+        collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+        return;
+    }
+    const R se = p.s_e > 0 ? par<R>(p.s_e, p.s_e_f) : omega;
+    const R seps = p.s_eps > 0 ? par<R>(p.s_eps, p.s_eps_f) : omega;
+    const R sq = p.s_q > 0 ? par<R>(p.s_q, p.s_q_f)
+                           : (p.s_q < 0 ? R(8) * (R(2) - omega) / (R(8) - omega) : omega);
+    mrt_one<R>(f[0], rho1, ux, uy, fx1, fy1, omega, se, seps, sq);
+    mrt_one<R>(f[1], rho2, ux, uy, fx2, fy2, omega, se, seps, sq);
+}
+
 }  // namespace mclbm

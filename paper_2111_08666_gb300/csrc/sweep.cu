@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
                               fx1, fy1, fx2, fy2);
                 R omega, ux, uy;
                 node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
-                collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+                collide<R>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
                 pop_store_node<P>(g, a.p, static_cast<S *>(a.fout), x, qC, f, rho1, rho2);
             }
         }

@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
             }
             R omega, ux, uy;
             node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
-            collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+            collide<R>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
             // output tile: planes of TY x TX in the layout of the store box
             const int o = ty * TX + tx;
             constexpr int OSTR = TX * TY;

@@ -67,6 +67,7 @@ _SIGS = {
     "mclbm_set_pressure_bc": (C.c_int, [_vp, C.c_double, C.c_double]),
     "mclbm_set_pressure_bc_p": (C.c_int, [_vp, C.c_double, C.c_double]),
     "mclbm_set_bc": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double]),
+    "mclbm_set_mrt": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_double]),
     "mclbm_set_stream": (C.c_int, [_vp, _vp]),
     "mclbm_init_densities": (C.c_int, [_vp, _vp, _vp]),
     "mclbm_set_populations": (C.c_int, [_vp, _vp]),
@@ -205,6 +206,10 @@ def mclbm_set_body_force(h, gx: float, gy: float) -> None:
 
 def mclbm_set_pressure_bc(h, rho_in1: float, rho_out2: float) -> None:
     _check(load().mclbm_set_pressure_bc(h, rho_in1, rho_out2))
+
+
+def mclbm_set_mrt(h, on: bool, s_e: float = 0.0, s_eps: float = 0.0, s_q: float = 0.0) -> None:
+    _check(load().mclbm_set_mrt(h, int(bool(on)), float(s_e), float(s_eps), float(s_q)))
 
 
 def mclbm_set_bc(h, bc_set: int, rho_in2: float = 0.0, rho_out1: float = 0.0) -> None:
@@ -381,7 +386,8 @@ class Lattice:
                  rho_in1: float = -1.0, rho_out2: float = -1.0, periodic_y: bool = False,
                  vel_shift: bool = True, gx: float = 0.0, gy: float = 0.0, stream=None,
                  kernel: int = 0, tile_shape: int = 0, bc_set: int = 3, rho_in2: float = 0.0,
-                 rho_out1: float = 0.0):
+                 rho_out1: float = 0.0, mrt: bool = False, s_e: float = 0.0, s_eps: float = 0.0,
+                 s_q: float = 0.0):
         self.h = None
         if isinstance(prec, str):
             prec = PRECISIONS[prec]
@@ -393,6 +399,7 @@ class Lattice:
         mclbm_set_coupling(self.h, g_coh, g_coh if g_ads is None else g_ads)
         mclbm_set_pressure_bc(self.h, rho_in1, rho_out2)
         mclbm_set_bc(self.h, bc_set, rho_in2, rho_out1)
+        mclbm_set_mrt(self.h, mrt, s_e, s_eps, s_q)
         mclbm_set_flag(self.h, MCLBM_FLAG_PERIODIC_Y, int(periodic_y))
         mclbm_set_flag(self.h, MCLBM_FLAG_VEL_SHIFT, int(vel_shift))
         mclbm_set_body_force(self.h, gx, gy)
@@ -462,6 +469,9 @@ class Lattice:
 
     def set_bc(self, bc_set: int, rho_in2: float = 0.0, rho_out1: float = 0.0) -> None:
         mclbm_set_bc(self.h, bc_set, rho_in2, rho_out1)
+
+    def set_mrt(self, on: bool, s_e: float = 0.0, s_eps: float = 0.0, s_q: float = 0.0) -> None:
+        mclbm_set_mrt(self.h, on, s_e, s_eps, s_q)
 
     def info(self) -> dict:
         return mclbm_info(self.h)

@@ -360,6 +360,51 @@ def test_bc_sets_step_kernels_agree(bc_set, other):
     assert np.max(np.abs(fa - fb)) <= AGREE["fp32"][1] * np.max(np.abs(fa))
 
 
+# --- multiple-relaxation-time collision (not in the paper) ------------------------
+
+MRT = dict(mrt=True, s_e=1.1, s_eps=1.2, s_q=-1.0)
+
+
+def test_fp64_mrt_matches_oracle(kernel):
+    """The MRT variant (closed-form moments on the GPU, the matrix form in
+    the oracle) on the FP64 disk-medium drainage case at viscosity ratio 25."""
+    c = media.config_small_fp64()
+    o, g = pair(c["solid"], media.uniform_xi(c["solid"], -0.3), c["rho1"], c["rho2"], kernel=kernel,
+                nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), rho_in1=c["rho_in1"], rho_out2=c["rho_out2"],
+                **MRT)
+    assert_fp64_parity(o, g, 200)
+
+
+@pytest.mark.parametrize("other", [2, 3, 4])
+def test_mrt_step_kernels_agree(other):
+    """Every step kernel collides alike under MRT (FP32, to rounding)."""
+    m = media.make_disk_medium(150, 60, 17, radius="uniform", r_lo=3.0, r_hi=6.0, porosity=0.7)
+    xi = media.uniform_xi(m.solid, -0.4)
+    rho1, rho2 = media.drainage_densities(m.solid)
+    kw = dict(prec="fp32", nu1=nu_of_tau(3.5), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0, **MRT)
+    a = mclbm.Lattice(m.solid, xi, kernel=1, **kw)
+    b = mclbm.Lattice(m.solid, xi, kernel=other, **kw)
+    a.init(rho1, rho2)
+    b.init(rho1, rho2)
+    a.step(300)
+    b.step(300)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) <= AGREE["fp32"][1] * np.max(np.abs(fa))
+
+
+def test_mrt_with_tied_rates_is_the_srt_step():
+    c = media.config_small_fp64()
+    kw = dict(prec="fp64", nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), rho_in1=1.01, rho_out2=1.0)
+    a = mclbm.Lattice(c["solid"], c["xi"], **kw)
+    b = mclbm.Lattice(c["solid"], c["xi"], mrt=True, **kw)
+    a.init(c["rho1"], c["rho2"])
+    b.init(c["rho1"], c["rho2"])
+    a.step(200)
+    b.step(200)
+    fa, fb = a.populations(), b.populations()
+    assert np.max(np.abs(fa - fb)) < 1e-12 * np.max(np.abs(fa))
+
+
 @pytest.mark.parametrize("periodic_y,open_x", [(True, False), (True, True), (False, False)])
 def test_tma_kernel_ghost_frames_fp32(periodic_y, open_x):
     """The TMA tile kernel reads its ring from the ghost columns and rows at
