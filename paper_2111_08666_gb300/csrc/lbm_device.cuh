@@ -362,21 +362,34 @@ __device__ __forceinline__ void mrt_one(R g[9], R rho, R ux, R uy, R fx, R fy, R
     g[0] = rho - (g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8]);
 }
 
-// The collision of both components: the SRT of Eq. 1 (collide_pair), or the
-// MRT variant when the lattice asks for it.
+// The MRT collision of both components with the lattice's rates.
 template <class R>
-__device__ __forceinline__ void collide(const Params &p, R f[2][9], R rho1, R rho2, R ux, R uy, R fx1, R fy1,
-                                        R fx2, R fy2, R omega) {
-    if (!p.mrt) {
-        collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
-        return;
-    }
+__device__ __forceinline__ void collide_mrt(const Params &p, R f[2][9], R rho1, R rho2, R ux, R uy, R fx1,
+                                            R fy1, R fx2, R fy2, R omega) {
     const R se = p.s_e > 0 ? par<R>(p.s_e, p.s_e_f) : omega;
     const R seps = p.s_eps > 0 ? par<R>(p.s_eps, p.s_eps_f) : omega;
     const R sq = p.s_q > 0 ? par<R>(p.s_q, p.s_q_f)
                            : (p.s_q < 0 ? R(8) * (R(2) - omega) / (R(8) - omega) : omega);
     mrt_one<R>(f[0], rho1, ux, uy, fx1, fy1, omega, se, seps, sq);
     mrt_one<R>(f[1], rho2, ux, uy, fx2, fy2, omega, se, seps, sq);
+}
+
+// The collision of both components: the SRT of Eq. 1 (collide_pair), or the
+// MRT variant when the lattice asks for it.  CM selects at compile time:
+// 0 SRT only, 1 MRT only, 2 by the lattice's flag.
+template <class R, int CM = 2>
+__device__ __forceinline__ void collide(const Params &p, R f[2][9], R rho1, R rho2, R ux, R uy, R fx1, R fy1,
+                                        R fx2, R fy2, R omega) {
+    if constexpr (CM == 0) {
+        collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+    } else if constexpr (CM == 1) {
+        collide_mrt<R>(p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+    } else {
+        if (p.mrt)
+            collide_mrt<R>(p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+        else
+            collide_pair<R>(f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+    }
 }
 
 }  // namespace mclbm

@@ -137,7 +137,9 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-template <class P, int STY, int N>
+// CM: collision chosen at compile time (0 SRT of Eq. 1, 1 MRT) for a
+// single lattice, by each case's flag (2) in a batch
+template <class P, int STY, int N, int CM>
 __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs<N> s) {
     using L = SLayout<P, STY>;
     constexpr int SFH = L::SFH, SN1 = L::SN1;
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             }
             R omega, ux, uy;
             node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
-            collide<R>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
+            collide<R, CM>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
             S *o = out + bidx * NPL;
             if constexpr (P::ref) {
                 const S h1 = from_real<S>(rho1), h2 = from_real<S>(rho2);
@@ -730,12 +732,12 @@ int sparse_to_dense(Lattice &L) {
 namespace {
 // one launch advancing lattices cases[0..n) by one step (all share the
 // precision, the tile height and have their fluid-only state current)
-template <class P, int STY, int N>
+template <class P, int STY, int N, int CM>
 cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t stream, int *slots_out) {
     using Lay = SLayout<P, STY>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(sparse_kernel<P, STY, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(sparse_kernel<P, STY, N, CM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Lay::total);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -776,13 +778,13 @@ cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t s
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY, N>, STX * STY, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY, N, CM>, STX * STY, bytes);
         slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
         last_bytes = bytes;
     }
     if (slots_out) *slots_out = slots;
     const int g = grid > 0 ? std::min(grid, total) : std::min(slots, total);
-    sparse_kernel<P, STY, N><<<g, STX * STY, bytes, stream>>>(s);
+    sparse_kernel<P, STY, N, CM><<<g, STX * STY, bytes, stream>>>(s);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
@@ -798,8 +800,11 @@ cudaError_t launch_step_sparse(Lattice &L) {
     Lattice *one = &L;
     return dispatch_prec(L.prec, [&](auto tag) {
         using P = decltype(tag);
-        return L.sparse_ty == 8 ? launch_sparse<P, 8, 1>(&one, 1, 0, L.stream, nullptr)
-                                : launch_sparse<P, 12, 1>(&one, 1, 0, L.stream, nullptr);
+        if (L.p.mrt)
+            return L.sparse_ty == 8 ? launch_sparse<P, 8, 1, 1>(&one, 1, 0, L.stream, nullptr)
+                                    : launch_sparse<P, 12, 1, 1>(&one, 1, 0, L.stream, nullptr);
+        return L.sparse_ty == 8 ? launch_sparse<P, 8, 1, 0>(&one, 1, 0, L.stream, nullptr)
+                                : launch_sparse<P, 12, 1, 0>(&one, 1, 0, L.stream, nullptr);
     });
 }
 
@@ -808,8 +813,8 @@ cudaError_t launch_step_sparse_batch(Lattice *const *cases, int n, int grid, cud
     const int ty = cases[0]->sparse_ty;
     return dispatch_prec(cases[0]->prec, [&](auto tag) {
         using P = decltype(tag);
-        return ty == 8 ? launch_sparse<P, 8, MAX_BATCH>(cases, n, grid, stream, nullptr)
-                       : launch_sparse<P, 12, MAX_BATCH>(cases, n, grid, stream, nullptr);
+        return ty == 8 ? launch_sparse<P, 8, MAX_BATCH, 2>(cases, n, grid, stream, nullptr)
+                       : launch_sparse<P, 12, MAX_BATCH, 2>(cases, n, grid, stream, nullptr);
     });
 }
 
