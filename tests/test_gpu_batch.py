@@ -68,3 +68,32 @@ def test_batch_rejects_fp64_and_too_many_cases():
         mclbm.mclbm_batch_create(c, mclbm.MCLBM_FP64)
     with pytest.raises(mclbm.MclbmError):
         mclbm.mclbm_batch_create(c * 33, mclbm.MCLBM_FP32)
+
+
+def test_batch_cases_keep_their_own_collision_and_boundary_treatment():
+    """Per-case parameters set through views: one case on the MRT variant,
+    one on Set-1, one on Set-2, one unchanged; each matches the same lattice
+    stepped alone with the same settings."""
+    cases = _cases()
+    p = mclbm.PRECISIONS["fp32"]
+    settings = [dict(mrt=True, s_e=1.1, s_eps=1.2, s_q=1.5), dict(bc_set=1, rho_in2=0.03, rho_out1=0.025),
+                dict(bc_set=2), dict()]
+    b = mclbm.mclbm_batch_create(cases, p)
+    try:
+        views = [mclbm.LatticeView(b, k, *c["solid"].shape, p) for k, c in enumerate(cases)]
+        for v, st in zip(views, settings):
+            if "mrt" in st:
+                v.set_mrt(True, st["s_e"], st["s_eps"], st["s_q"])
+            if "bc_set" in st:  # the Eq. 26/27 records were taken when the batch was created
+                v.set_bc(st["bc_set"], st.get("rho_in2", 0.0), st.get("rho_out1", 0.0))
+        steps = 16 * 3 + 5
+        mclbm.mclbm_batch_step(b, steps)
+        for k, (c, st) in enumerate(zip(cases, settings)):
+            alone = mclbm.Lattice(c["solid"], c["xi"], prec=p, nu1=c["nu1"], nu2=c["nu2"],
+                                  rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], kernel=3, **st)
+            alone.init(c["rho1"], c["rho2"])
+            alone.step(steps)
+            fa, fb = alone.populations(), views[k].populations()
+            assert np.max(np.abs(fa - fb)) <= 4e-6 * np.max(np.abs(fa)), (k, np.max(np.abs(fa - fb)))
+    finally:
+        mclbm.mclbm_batch_destroy(b)
