@@ -711,6 +711,7 @@ struct WgradRowArgs {
     int c0, c1;
     int B, H, W, M;
     float *dw;            // [co][9][c0 + c1], accumulated into
+    float *part;          // shared-tap kernel: per-CTA partial sums [grid][32][9][32]
     int *err;
 };
 constexpr int WG_A_ATOM = 128 * 128;  // 128 pixels x 64 channels x 2 bytes
@@ -920,6 +921,330 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient with the nine taps sharing one MMA, per slice of 32 output
+// channels.  With dZ rows y-1, y, y+1 of a row tile as the M atoms of A (64-byte
+// swizzle, atom stride one row tile; the fourth atom's products are not
+// used) and X row y with a one-pixel halo as B, read as three N atoms that
+// start one pixel apart (atom stride 64 bytes), one M = 128, N = 96 product of
+// K = 128 pixels gives
+//   D[32 jy + co][32 jx + ci] = sum_x dZ[y - 1 + jy][x][co] X[y][x + jx - 1][ci],
+// the contribution of X row y to the tap (dy, dx) = (1 - jy, jx - 1) of
+//   dW[co][tap][ci] = sum_p dZ[p][co] X[p + d_tap][ci].
+// Summed over all rows y of the image this is the whole gradient: rows of dZ
+// outside the image are zero-filled by the tensor copy, and so are pixels of
+// X outside it.  A CTA owns one (32-channel slice of dZ, 32-channel chunk of
+// X) pair and a contiguous run of row tiles taken down each 128-pixel column
+// strip, so consecutive tiles share two of their three dZ rows: the dZ rows
+// live in a ring of R = S + 2 row slots (slots R and R + 1 repeat slots 0 and
+// 1, so that any three consecutive rows are evenly spaced) and each tile
+// loads one new dZ row and its X row.  Eight MMAs per tile, where the per-tap
+// kernel above issues 72 of N = 32 (a quarter of them useful when the layer
+// has 32 output channels), and half its copy traffic.
+// ---------------------------------------------------------------------------
+constexpr int WT_ROW = RW * 64;    // one dZ row tile: 128 pixels x 32 channels
+constexpr int WT_B_BYTES = 9216;   // X row y, 130 pixels x 64 bytes (8320), rounded up to 1024
+constexpr int WT_U_BYTES = 5120;   // one coarse row, 66 pixels x 64 bytes (4224), rounded up
+constexpr int WT_MAX_STAGES = 8;
+constexpr int WT_BAR_BYTES = 256;  // 3 x 8 + 2 barriers, the tensor-memory slot and the stop flag
+constexpr int WT_MAX_CO = 128;     // wider layers keep the per-tap kernel
+constexpr int WT_PRODUCERS = 5;    // warps issuing the tensor copies: 0 and 6-9
+constexpr int WT_PART = 32 * 9 * 32;  // one CTA's partial sums: [co][tap][ci]
+static_assert(WT_PRODUCERS <= 5, "producer warps 0 and 6-9");
+// shared memory of S stages: R + 2 ring slots, S X-row stages, barriers.  The
+// fourth A atom of a window at slot R - 1 reads slot R + 2, the first X stage
+__host__ __device__ inline int wt_stage_bytes(int ux) { return WT_B_BYTES + (ux ? WT_U_BYTES : 0); }
+__host__ __device__ inline int wt_smem(int S, int ux) { return (S + 4) * WT_ROW + S * wt_stage_bytes(ux) + WT_BAR_BYTES; }
+
+__global__ void __launch_bounds__(ROW_THREADS, 1)
+    wgrad_tap_kernel(const WgradRowArgs a, const int S, const int ux, const __grid_constant__ CUtensorMap tdz,
+                     const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmu) {
+    constexpr uint32_t COLS = 128;  // one 96-column accumulator
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (smem_u32(smem) & 1023u) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+        return;
+    }
+    const int K0 = a.c0 + a.c1;
+    const int R = S + 2, SB = wt_stage_bytes(ux);
+    unsigned char *ring = smem, *stg = smem + (R + 2) * WT_ROW;
+    uint64_t *full = reinterpret_cast<uint64_t *>(stg + S * SB);
+    uint64_t *done = full + WT_MAX_STAGES, *expd = done + WT_MAX_STAGES, *accf = expd + WT_MAX_STAGES,
+             *drain = accf + 1;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(drain + 1);
+    int *flag = reinterpret_cast<int *>(drain + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chunks = K0 / 32, combos = (a.co / 32) * chunks;
+    const int combo = blockIdx.x % combos, mt = combo / chunks, cc = combo - mt * chunks;
+    const int per = gridDim.x / combos, q = blockIdx.x / combos;
+    const int segs = a.W / RW, ntiles = a.M / RW;  // tiles in (image, strip, row) order
+    const int t_begin = (int)((long long)ntiles * q / per), t_end = (int)((long long)ntiles * (q + 1) / per);
+    const int njobs = t_end - t_begin;
+    const bool direct = cc * 32 < a.c0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&done[k], 1);
+            mbar_init(&expd[k], ROW_EXP / 32);  // one arrival per expansion warp
+        }
+        mbar_init(accf, 1);
+        mbar_init(drain, 1);
+        *flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    struct Where {
+        int x0, y, b;
+    };
+    auto where = [&](int j) {
+        const int t = t_begin + j, strip = t / a.H;
+        return Where{(strip % segs) * RW, t - strip * a.H, strip / segs};
+    };
+    // a tile starts a new window (three fresh dZ rows at slot 0) at the
+    // start of the CTA's run and of each strip (row 0), else the window
+    // moves down one slot of the ring
+    auto give_up = [&]() {
+        *(volatile int *)flag = 1;
+        if (a.err) atomicExch(a.err, 1);
+    };
+    auto stopped = [&]() { return *(volatile int *)flag != 0; };
+
+    // ---------------- producers: warp 0 and the epilogue warps ----------------
+    // A warp's tensor copies are served one after another, so one issuing
+    // thread would cap the CTA at a few boxes per microsecond: tile j's copies
+    // come from producer j % WT_PRODUCERS, lane 0 of its warp.
+    const int prod = warp == 0 ? 0 : warp >= 6 ? warp - 5 : -1;
+    if (prod >= 0 && lane == 0) {
+        // row, strip, window, stage and phase advance tile by tile (as in the
+        // MMA loop); only a producer's own tiles pay for their coordinates
+        int last = -1, run = 0, ws = 0, st = 0;
+        int yc = njobs > 0 ? where(0).y : 0, strip = (t_begin - yc) / a.H;
+        uint32_t ph = 0;
+        for (int j = 0; j < njobs && !stopped(); ++j) {
+            if (j > 0) {
+                ws = ++yc == a.H ? 0 : (ws + 1 == R ? 0 : ws + 1);
+                if (yc == a.H) {
+                    yc = 0;
+                    ++strip;
+                }
+                if (++st == S) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+            const bool fresh = j == 0 || yc == 0;
+            if (fresh) run = j;
+            if (j % WT_PRODUCERS != prod) continue;
+            const Where w{(strip % segs) * RW, yc, strip / segs};
+            // the stage's X row, and the slot of the new dZ row: both were
+            // last read by tile j - S (the ring holds S + 2 rows) or, early in
+            // a run, by any tile of the run before (up to tile run - 1).  The
+            // waits go in order up to the later of the two (a producer has
+            // seen tile j - WT_PRODUCERS - S complete, so the previous phase
+            // of each barrier waited on is complete and its parity
+            // unambiguous: S >= WT_PRODUCERS)
+            bool ok = j < S || mbar_wait_sleep(&done[st], ph ^ 1u, WAIT_LIMIT_NS);
+            for (int k = j - S + 1 < 0 ? 0 : j - S + 1; ok && k < run; ++k)
+                ok = mbar_wait_sleep(&done[k % S], (k / S) & 1, WAIT_LIMIT_NS);
+            if (!ok) {
+                give_up();
+                break;
+            }
+            unsigned char *Bs = stg + st * SB;
+            const int s_new = ws + 2 < R ? ws + 2 : ws + 2 - R;  // slot of row y + 1
+            const int nrows = fresh ? 5 : (s_new < 2 ? 2 : 1);
+            mbar_expect_tx(&full[st], nrows * WT_ROW + (direct ? RHALO * 64 : 66 * 64));
+            if (fresh) {
+                // rows y - 1, y, y + 1 into slots 0, 1, 2; rows y - 1 and y
+                // again into slots R and R + 1
+                for (int r = 0; r < 3; ++r)
+                    tma_load_4d(ring + r * WT_ROW, &tdz, mt * 32, w.x0, w.y - 1 + r, w.b, &full[st]);
+                for (int r = 0; r < 2; ++r)
+                    tma_load_4d(ring + (R + r) * WT_ROW, &tdz, mt * 32, w.x0, w.y - 1 + r, w.b, &full[st]);
+            } else {
+                tma_load_4d(ring + s_new * WT_ROW, &tdz, mt * 32, w.x0, w.y + 1, w.b, &full[st]);
+                if (s_new < 2)
+                    tma_load_4d(ring + (R + s_new) * WT_ROW, &tdz, mt * 32, w.x0, w.y + 1, w.b, &full[st]);
+            }
+            if (direct)
+                tma_load_4d(Bs, &tmx, cc * 32, w.x0 - 1, w.y, w.b, &full[st]);
+            else
+                tma_load_4d(Bs + WT_B_BYTES, &tmu, cc * 32 - a.c0, (w.x0 >> 1) - 1, w.y >> 1, w.b, &full[st]);
+            last = j;
+        }
+        // after a stop, copies still in flight land before the CTA exits (a
+        // normal run needs no drain: the MMA thread has waited for every
+        // copy; nor could it wait here, as another producer may already have
+        // reused the stage, putting the barrier a phase further on)
+        for (int jb = last; stopped() && jb >= 0 && jb > last - S; jb -= WT_PRODUCERS)
+            mbar_wait(&full[jb % S], (jb / S) & 1, DRAIN_LIMIT_NS);
+    }
+    __syncwarp();
+    if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                       ((96u >> 3) << 17) | ((128u >> 4) << 24);  // MN-major A and B
+            // the issuing thread paces the tensor core: its per-tile work is
+            // kept to the waits (spinning, for the shortest hand-over), two
+            // descriptor adds and the MMAs (stage, phase, row and window
+            // advance incrementally, no divisions)
+            const uint64_t ad_ring = umma_desc_mn(smem_u32(ring), WT_ROW, 512, 4);
+            const uint64_t bd_stg = umma_desc_mn(smem_u32(stg), 64, 512, 4);
+            int st = 0, ws = 0, yc = njobs > 0 ? where(0).y : 0;
+            uint32_t ph = 0, accum = 0;
+            for (int j = 0; j < njobs && !stopped(); ++j) {
+                if (j > 0) {
+                    ws = ++yc == a.H ? 0 : (ws + 1 == R ? 0 : ws + 1);
+                    if (yc == a.H) yc = 0;
+                }
+                bool ok = mbar_wait(&full[st], ph, WAIT_LIMIT_NS);
+                if (ok && !direct) ok = mbar_wait(&expd[st], ph, WAIT_LIMIT_NS);
+                if (!ok) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                // A: atoms one row slot apart from the window's first slot; B:
+                // atoms one pixel apart.  Each K step of 16 pixels moves both
+                // starts by 1024 bytes (64 in the address field: no carry
+                // below 256 KB)
+                const uint64_t ad0 = ad_ring + (uint64_t)((ws * WT_ROW) >> 4);
+                const uint64_t bd0 = bd_stg + (uint64_t)((st * SB) >> 4);
+#pragma unroll
+                for (int k = 0; k < RW / 16; ++k) {
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad0 + (uint64_t)(k * 64)), "l"(bd0 + (uint64_t)(k * 64)), "r"(idesc), "r"(accum)
+                        : "memory");
+                    accum = 1u;
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&done[st]))
+                             : "memory");
+                if (++st == S) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(accf))
+                         : "memory");
+        }
+    } else if (warp >= 2 && warp < 6) {
+        // ---------------- expansion of the coarse upsampled row ----------------
+        // a thread writes 16-byte chunk qq of pixels p = et / 4 + 32 i of the
+        // fine row (stage bases are 1024-byte aligned, so the 64-byte swizzle
+        // of pixel p is (p / 2) & 3); each thread fences its writes for the
+        // tensor core, and one lane per warp arrives
+        const int et = tid - 64, qq = et & 3;
+        int st = 0;
+        uint32_t ph = 0;
+        for (int j = 0; !direct && j < njobs && !stopped(); ++j) {
+            if ((j >= S && !mbar_wait_sleep(&done[st], ph ^ 1u, WAIT_LIMIT_NS)) ||
+                !mbar_wait_sleep(&full[st], ph, WAIT_LIMIT_NS)) {
+                give_up();
+                break;
+            }
+            unsigned char *Bs = stg + st * SB;
+            const unsigned char *U = Bs + WT_B_BYTES;
+            for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4)
+                *reinterpret_cast<uint4 *>(Bs + p * 64 + ((qq ^ ((p >> 1) & 3)) << 4)) =
+                    *reinterpret_cast<const uint4 *>(U + ((p + 1) >> 1) * 64 + qq * 16);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&expd[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1u;
+            }
+        }
+    } else if (warp >= 6) {
+        // ---------------- epilogue: the CTA's nine 32 x 32 blocks ----------------
+        // stored as this CTA's partial sums (plain stores: every CTA finishing
+        // at once with FP32 atomics on the same 36 KB of dW would serialise in
+        // the L2); wgrad_reduce_kernel adds them up
+        const int ew = warp & 3;  // accumulator lanes 32 ew..: dZ row y - 1 + ew, i.e. dy = 1 - ew
+        float *part = a.part + (size_t)blockIdx.x * WT_PART;
+        if (njobs == 0 && ew < 3) {
+            for (int jx = 0; jx < 3; ++jx) {
+                float4 *d = reinterpret_cast<float4 *>(part + ((size_t)lane * 9 + (2 - ew) * 3 + jx) * 32);
+                for (int c = 0; c < 8; ++c) d[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else if (njobs > 0 && mbar_wait_sleep(accf, 0, WAIT_LIMIT_NS) && !stopped()) {
+            tc_fence_after();
+            if (ew < 3) {
+                for (int jx = 0; jx < 3; ++jx) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int c = 0; c < 32; c += 16) {
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+                            "%14,%15}, [%16];"
+                            : "=r"(r[c]), "=r"(r[c + 1]), "=r"(r[c + 2]), "=r"(r[c + 3]), "=r"(r[c + 4]),
+                              "=r"(r[c + 5]), "=r"(r[c + 6]), "=r"(r[c + 7]), "=r"(r[c + 8]), "=r"(r[c + 9]),
+                              "=r"(r[c + 10]), "=r"(r[c + 11]), "=r"(r[c + 12]), "=r"(r[c + 13]), "=r"(r[c + 14]),
+                              "=r"(r[c + 15])
+                            : "r"(tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(jx * 32 + c)));
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int tap = (2 - ew) * 3 + jx;
+                    float4 *d = reinterpret_cast<float4 *>(part + ((size_t)lane * 9 + tap) * 32);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        d[c] = make_float4(__uint_as_float(r[4 * c]), __uint_as_float(r[4 * c + 1]),
+                                           __uint_as_float(r[4 * c + 2]), __uint_as_float(r[4 * c + 3]));
+                }
+            }
+            tc_fence_before();
+        } else if (njobs > 0 && !stopped()) {
+            give_up();
+        }
+    }
+    if (warp == 1 && lane == 0 && stopped()) {
+        // one last commit tracks every MMA issued: a short wait before the
+        // tensor memory is released
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(drain))
+                     : "memory");
+        mbar_wait(drain, 0, DRAIN_LIMIT_NS);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    }
+}
+
+// dW += the shared-tap kernel's partial sums: CTA q * combos + combo holds
+// [co][tap][ci] of the (32-channel slice of dZ, 32-channel chunk of X) pair
+// combo; a thread sums one element over the per CTAs of its pair, in a fixed
+// order
+__global__ void wgrad_reduce_kernel(const float *part, int combos, int per, int chunks, int K0, float *dw) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)combos * WT_PART;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int combo = (int)(i / WT_PART), e = (int)(i - (long long)combo * WT_PART);
+        float sum = 0.f;
+        for (int q = 0; q < per; ++q) sum += part[((size_t)q * combos + combo) * WT_PART + e];
+        const int co = e / (9 * 32), tap = (e / 32) % 9, ci = e % 32;
+        const int mt = combo / chunks, cc = combo - mt * chunks;
+        dw[((size_t)(mt * 32 + co) * 9 + tap) * K0 + cc * 32 + ci] += sum;
     }
 }
 
@@ -1394,6 +1719,9 @@ struct mclbm_unet {
     double *loss_part = nullptr, *loss_stat = nullptr;
     int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
     int max_ctas = 0;    // bound on the row-tile kernels' CTAs (0: one wave)
+    int shared_taps = 1;  // weight gradients of <= 128 output channels on the shared-tap kernel
+    float *wg_part = nullptr;  // the shared-tap kernel's per-CTA partial sums
+    int wg_part_ctas = 0;
     std::vector<void *> allocs;
     int cur_b = 0, cur_h = 0, cur_w = 0;
 };
@@ -1576,6 +1904,46 @@ cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
     }
 }
 
+// the weight gradient with the taps sharing one MMA (co a multiple of 32)
+cudaError_t launch_wgrad_tap(const mclbm_unet &u, const WgradRowArgs &a, int ux) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(wgrad_tap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ROW_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(wgrad_tap_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int S = WT_MAX_STAGES;
+    while (S > 2 && wt_smem(S, ux) > ROW_SMEM_MAX) --S;
+    if (wt_smem(S, ux) > ROW_SMEM_MAX || S < WT_PRODUCERS) return cudaErrorInvalidConfiguration;
+    const int smem = wt_smem(S, ux);
+    constexpr auto SW64 = CU_TENSOR_MAP_SWIZZLE_64B;
+    CUtensorMap tdz, tmx, tmu;
+    cudaError_t e = nhwc_map(a.dz, a.B, a.H, a.W, a.co, 32, RW, 1, SW64, &tdz);
+    if (e == cudaSuccess) e = nhwc_map(a.x0, a.B, a.H, a.W, a.c0, 32, RHALO, 1, SW64, &tmx);
+    if (e == cudaSuccess)
+        e = ux ? nhwc_map(a.x1, a.B, a.H >> 1, a.W >> 1, a.c1, 32, 66, 1, CU_TENSOR_MAP_SWIZZLE_NONE, &tmu)
+               : nhwc_map(a.x0, a.B, a.H, a.W, a.c0, 32, RHALO, 1, SW64, &tmu);
+    if (e != cudaSuccess) return e;
+    const int combos = (a.co / 32) * ((a.c0 + a.c1) / 32);
+    int grid = sm_count();
+    if (u.max_ctas > 0 && grid > u.max_ctas) grid = u.max_ctas;
+    if (grid > combos * (a.M / RW)) grid = combos * (a.M / RW);
+    grid -= grid % combos;
+    if (grid < combos) grid = combos;
+    if (grid > u.wg_part_ctas) return cudaErrorInvalidConfiguration;
+    WgradRowArgs b = a;
+    b.part = u.wg_part;
+    wgrad_tap_kernel<<<grid, ROW_THREADS, smem, u.stream>>>(b, S, ux, tdz, tmx, tmu);
+    wgrad_reduce_kernel<<<blocks_for((long long)combos * WT_PART), 256, 0, u.stream>>>(
+        u.wg_part, combos, grid / combos, (a.c0 + a.c1) / 32, a.c0 + a.c1, a.dw);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
 // the weight gradient on the tensor cores where the width is a multiple of
 // 128 (row tiles), else on mma.sync
 cudaError_t launch_wgrad_row(const mclbm_unet &u, const WgradArgs &w) {
@@ -1603,6 +1971,7 @@ cudaError_t launch_wgrad_row(const mclbm_unet &u, const WgradArgs &w) {
     a.dw = w.dw;
     a.err = u.err;
     const int ux = w.c1 > 0 ? 1 : 0;
+    if (u.shared_taps && w.co % 32 == 0 && w.co <= WT_MAX_CO) return launch_wgrad_tap(u, a, ux);
     int S = (ROW_SMEM_MAX - 256) / wg_stage_bytes(ux);
     if (S > 4) S = 4;
     if (S < 2) return cudaErrorInvalidConfiguration;
@@ -2017,6 +2386,8 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     A((void **)&u->loss_part, LOSS_BLOCKS * 2 * sizeof(double));
     A((void **)&u->loss_stat, 2 * sizeof(double));
     A((void **)&u->err, sizeof(int));
+    u->wg_part_ctas = sm_count();
+    A((void **)&u->wg_part, (size_t)u->wg_part_ctas * WT_PART * sizeof(float));
     if (rc == MCLBM_OK) {
         cudaError_t e = cudaMemsetAsync(u->theta, 0, u->nparam * 4, u->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream);
@@ -2047,6 +2418,12 @@ int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n) {
 int mclbm_unet_set_max_ctas(mclbm_unet *u, int n) {
     if (!u || n < 0) return fail(MCLBM_ERR_ARG, "NULL network or negative bound");
     u->max_ctas = n;
+    return MCLBM_OK;
+}
+
+int mclbm_unet_set_shared_taps(mclbm_unet *u, int enable) {
+    if (!u || (enable != 0 && enable != 1)) return fail(MCLBM_ERR_ARG, "NULL network or flag not 0/1");
+    u->shared_taps = enable;
     return MCLBM_OK;
 }
 

@@ -95,6 +95,7 @@ _SIGS = {
     "mclbm_unet_destroy": (C.c_int, [_vp]),
     "mclbm_unet_param_count": (C.c_int, [_vp, _P(_i64)]),
     "mclbm_unet_set_max_ctas": (C.c_int, [_vp, C.c_int]),
+    "mclbm_unet_set_shared_taps": (C.c_int, [_vp, C.c_int]),
     "mclbm_unet_set_params": (C.c_int, [_vp, _vp]),
     "mclbm_unet_get_params": (C.c_int, [_vp, _vp]),
     "mclbm_unet_infer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
@@ -512,6 +513,10 @@ def mclbm_unet_param_count(h) -> int:
 
 def mclbm_unet_set_max_ctas(h, n: int) -> None:
     _check(load().mclbm_unet_set_max_ctas(h, int(n)))
+
+
+def mclbm_unet_set_shared_taps(h, enable: int) -> None:
+    _check(load().mclbm_unet_set_shared_taps(h, int(enable)))
 
 
 def mclbm_unet_set_params(h, theta) -> None:

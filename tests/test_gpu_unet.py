@@ -57,9 +57,16 @@ def test_forward_matches_reference(levels, b, h, w, max_ctas):
     net.close()
 
 
-@pytest.mark.parametrize("b,h,w,max_ctas", [(2, 32, 32, 0), (1, 8, 512, 0), (1, 8, 512, 3)])
-def test_gradient_matches_reference(b, h, w, max_ctas):
-    levels, base = 3, 32
+# at width 512 the weight gradients of levels 0-2 (32, 64 and 128 output
+# channels) take the shared-tap kernel.  Its CTAs walk runs of row tiles down
+# 128-pixel strips with the dZ rows in a ring: 24 rows with max_ctas 3 make
+# runs long enough to wrap the ring and cross strips and images (the rows
+# above and below a tile come from its own image); four levels at width 1024
+# add the 256-channel level, which keeps the per-tap kernel
+@pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 32, 32, 0), (3, 1, 8, 512, 0), (3, 1, 8, 512, 3),
+                                                   (3, 2, 24, 512, 0), (3, 2, 24, 512, 3), (4, 1, 8, 1024, 0)])
+def test_gradient_matches_reference(levels, b, h, w, max_ctas):
+    base = 32
     theta, x4, target, mask = _problem(levels, base, b, h, w, seed=7)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
     mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
@@ -78,6 +85,30 @@ def test_gradient_matches_reference(b, h, w, max_ctas):
             cos = a @ r / (np.linalg.norm(a) * nr)
             assert cos > 0.99, (name, part, cos)
             assert abs(np.linalg.norm(a) / nr - 1) < 0.1, (name, part)
+    net.close()
+
+
+# the shared-tap weight gradient against the per-tap kernel on the same
+# network and data: the same BF16 products summed in another order, so they
+# agree to FP32 rounding (a wrong dZ row in some ring windows would show as
+# a gross difference in the affected taps, which the oracle comparison above,
+# loose enough for BF16 error propagation, could let through)
+@pytest.mark.parametrize("b,h,w,max_ctas", [(2, 24, 512, 3), (2, 24, 512, 0), (1, 40, 256, 1)])
+def test_shared_tap_wgrad_matches_per_tap(b, h, w, max_ctas):
+    levels, base = 3, 32
+    theta, x4, target, mask = _problem(levels, base, b, h, w, seed=11)
+    net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
+    mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
+    net.set_params(theta)
+    loss_a, g_shared = net.gradient(x4, target, mask)
+    mclbm.mclbm_unet_set_shared_taps(net.h, 0)
+    loss_b, g_tap = net.gradient(x4, target, mask)
+    assert loss_a == pytest.approx(loss_b, rel=1e-6)  # the forward pass does not use the switch
+    for name, (ws, _) in warmstart.layer_slices(levels, base).items():
+        a, r = g_shared[ws].astype(np.float64), g_tap[ws].astype(np.float64)
+        scale = np.max(np.abs(r))
+        assert scale > 0, name
+        assert np.max(np.abs(a - r)) <= 1e-3 * scale, (name, np.max(np.abs(a - r)) / scale)
     net.close()
 
 
