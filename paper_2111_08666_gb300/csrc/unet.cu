@@ -557,29 +557,38 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         if (lane == 0) {
             bool ok = !(wres && njobs > 0) || mbar_wait_sleep(wfull, 0, WAIT_LIMIT_NS);
             if (!ok) give_up();
+            // this thread paces the tensor core: per job it only waits
+            // (spinning, for the shortest hand-over), adds to two descriptors
+            // and issues; stage, phase, tile and chunk advance incrementally
             uint32_t xpar = 0;  // bit st: parity of the upsampled-coarse jobs seen on stage st (expd phases)
+            const uint64_t ad_stg = umma_desc_sw64(smem_u32(stg), 512);
+            const uint64_t bd_w = wres ? umma_desc(smem_u32(wsm), 128, 512)
+                                       : umma_desc(smem_u32(stg) + RA_BYTES + (plan.ux ? RU_BYTES : 0), 128, 512);
+            // the taps' A offsets (64-byte pixels of the 130-wide halo; the data
+            // gradient runs the taps mirrored)
+            const int tap_dir = a.sign;
+            int st = 0, i = 0, kc = 0;
+            uint32_t ph = 0;
             for (int j = 0; ok && j < njobs && !stopped(); ++j) {
-                const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
-                ok = mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS);
+                ok = mbar_wait(&full[st], ph, WAIT_LIMIT_NS);
                 if (ok && plan.ux && kc * 32 >= a.c0) {
-                    ok = mbar_wait_sleep(&expd[st], (xpar >> st) & 1u, WAIT_LIMIT_NS);
+                    ok = mbar_wait(&expd[st], (xpar >> st) & 1u, WAIT_LIMIT_NS);
                     xpar ^= 1u << st;
                 }
-                if (ok && kc == 0 && i >= 2) ok = mbar_wait_sleep(&acce[i & 1], ((i - 2) >> 1) & 1, WAIT_LIMIT_NS);
+                if (ok && kc == 0 && i >= 2) ok = mbar_wait(&acce[i & 1], ((i - 2) >> 1) & 1, WAIT_LIMIT_NS);
                 if (!ok) {
                     give_up();
                     break;
                 }
                 tc_fence_after();
-                const uint32_t As = smem_u32(stg + st * STG);
-                const uint32_t Bs = wres ? smem_u32(wsm + kc * WTILE) : As + RA_BYTES + (plan.ux ? RU_BYTES : 0);
-                const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
                 // descriptors of the stage's operands; a start moved by b bytes
                 // adds b / 16 to the address field (no carry: below 256 KB)
-                const uint64_t ad0 = umma_desc_sw64(As, 512), bd0 = umma_desc(Bs, 128, 512);
+                const uint32_t d = tmem + (uint32_t)((i & 1) * BN);
+                const uint64_t ad0 = ad_stg + (uint64_t)((st * STG) >> 4);
+                const uint64_t bd0 = bd_w + (uint64_t)(((wres ? kc * WTILE : st * STG)) >> 4);
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
-                    const int dy = (tap / 3 - 1) * a.sign, dx = (tap % 3 - 1) * a.sign;
+                    const int dy = (tap / 3 - 1) * tap_dir, dx = (tap % 3 - 1) * tap_dir;
                     const int aoff = ((dy + 1) * RHALO + dx + 1) * 64;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -601,6 +610,14 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
                         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                             smem_u32(&accf[i & 1]))
                         : "memory");
+                if (++st == S) {
+                    st = 0;
+                    ph ^= 1u;
+                }
+                if (++kc == kchunks) {
+                    kc = 0;
+                    ++i;
+                }
             }
             // every MMA issued has completed before the tensor memory is freed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -1862,6 +1879,14 @@ cudaError_t launch_row(const mclbm_unet &u, ConvArgs a) {
     constexpr int cols = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 256;
     int per_sm = (228 * 1024) / (plan.smem + 1024);
     if (per_sm > 512 / cols) per_sm = 512 / cols;
+    // and 64 K registers, allocated per warp in units of 256
+    static int regs_per_cta = 0;
+    if (!regs_per_cta) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, conv_row_kernel<BN>) != cudaSuccess) return cudaErrorInvalidConfiguration;
+        regs_per_cta = (ROW_THREADS / 32) * ((fa.numRegs * 32 + 255) / 256 * 256);
+    }
+    if (per_sm > 65536 / regs_per_cta) per_sm = 65536 / regs_per_cta;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int ntn = a.N / BN;
     const long long items = (long long)(a.M / RW) * ntn;
