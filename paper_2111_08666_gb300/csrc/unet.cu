@@ -1484,55 +1484,111 @@ __global__ void loss_final_kernel(const double *part, int nblocks, double *out) 
     out[1] = b / n;
 }
 
-// head backward: dz = dL/dphi (1 - phi^2) with dL/dphi = 2 mask (phi - t) / n;
-// dd[p][c] = dz w[c]; gradients of the head weights and bias (block sums)
-// head backward: dz = d loss / d (w . d + b) per pixel, dd = dz w (input
-// gradient), and the head's weight and bias gradients.  One warp per pixel
-// (strided), lane c and c + 32 own channels c and c + 32 (C <= 64).
+// head backward: per pixel dz = d loss / d (w . d + b) = 2 mask (phi - t) (1 - phi^2) / n,
+// the input gradient dd[p][c] = dz w[c], and the head's gradients
+// gw[c] += sum_p dz d[p][c], gb += sum_p dz.  A thread owns 8 channels of a
+// strided set of pixels (C / 8 threads share a pixel); the block reduces by
+// channel in shared memory and adds to gwb
 __global__ void head_backward_kernel(const float *phi, const float *t, const float *mask, const double *stat,
                                      const bf16 *d, const float *wb, int C, long long P, float *dd,
                                      float *gwb) {
+    __shared__ float part[256 * 9];
     const float inv_n = (float)(1.0 / stat[0]);
-    const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    const bool has0 = lane < C, has1 = lane + 32 < C;
-    const float w0 = has0 ? wb[lane] : 0.f, w1 = has1 ? wb[lane + 32] : 0.f;
-    float a0 = 0.f, a1 = 0.f, ab = 0.f;
-    for (long long p = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
-        const float f = phi[p];
-        const float dz = 2.f * mask[p] * (f - t[p]) * inv_n * (1.f - f * f);
-        if (has0) {
-            dd[p * C + lane] = dz * w0;
-            a0 += dz * __bfloat162float(d[p * C + lane]);
-        }
-        if (has1) {
-            dd[p * C + lane + 32] = dz * w1;
-            a1 += dz * __bfloat162float(d[p * C + lane + 32]);
-        }
-        ab += dz;
+    const int g8 = C / 8;
+    const int lanes = blockDim.x / g8;
+    const int grp = threadIdx.x % g8, sub = threadIdx.x / g8;
+    float w[8], acc[9];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        w[k] = wb[grp * 8 + k];
+        acc[k] = 0.f;
     }
-    if (has0) atomicAdd(gwb + lane, a0);
-    if (has1) atomicAdd(gwb + lane + 32, a1);
-    if (lane == 0) atomicAdd(gwb + C, ab);
+    acc[8] = 0.f;
+    if (sub < lanes)
+        for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes) {
+            const float f = phi[p];
+            const float dz = 2.f * mask[p] * (f - t[p]) * inv_n * (1.f - f * f);
+            const long long i = p * g8 + grp;
+            const uint4 dv = reinterpret_cast<const uint4 *>(d)[i];
+            const uint32_t *dp = &dv.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 df = bf2_to_f2(dp[k]);
+                acc[2 * k] += dz * df.x;
+                acc[2 * k + 1] += dz * df.y;
+            }
+            float4 *o = reinterpret_cast<float4 *>(dd) + 2 * i;
+            o[0] = make_float4(dz * w[0], dz * w[1], dz * w[2], dz * w[3]);
+            o[1] = make_float4(dz * w[4], dz * w[5], dz * w[6], dz * w[7]);
+            if (grp == 0) acc[8] += dz;
+        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) part[threadIdx.x * 9 + k] = acc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c <= C; c += blockDim.x) {
+        float sum = 0.f;
+        if (c < C)
+            for (int l = 0; l < lanes; ++l) sum += part[(l * g8 + c / 8) * 9 + (c & 7)];
+        else
+            for (int l = 0; l < lanes; ++l) sum += part[(l * g8) * 9 + 8];
+        atomicAdd(gwb + c, sum);
+    }
 }
 
-// dz = g (h > 0), as BF16 (h: the ReLU output the gradient flows into)
-// dz = g where the forward activation h > 0, else 0 (BF16); 8 elements a thread
-__global__ void relu_mask_kernel(const float *g, const bf16 *h, bf16 *dz, long long n) {
-    GRID_STRIDE(i, n / 8) {
-        const float4 g0 = reinterpret_cast<const float4 *>(g)[2 * i], g1 = reinterpret_cast<const float4 *>(g)[2 * i + 1];
-        const uint4 hv = reinterpret_cast<const uint4 *>(h)[i];
-        const uint32_t *hp = &hv.x;
-        const float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-        uint4 o;
-        uint32_t *op = &o.x;
+// dz = g where the forward activation h > 0, else 0 (BF16), and the bias
+// gradient gb[c] += sum over pixels of that BF16 dz[p][c], in one pass: a
+// thread owns 8 channels of a strided set of pixels, the block reduces by
+// channel in shared memory and adds to gb.  With gc, the gradient that
+// flows back through the 2 x 2 average pooling of this activation is added
+// first: g[p] + gc[coarse pixel of p] / 4 (gc [B][H/2][W/2][C])
+__global__ void relu_mask_bias_kernel(const float *g, const float *gc, int H, int W, const bf16 *h, bf16 *dz,
+                                      long long P, int C, float *gb) {
+    __shared__ float part[256 * 8];
+    const int g8 = C / 8;
+    const int lanes = blockDim.x / g8;  // pixels in flight per block
+    const int grp = threadIdx.x % g8, sub = threadIdx.x / g8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (sub < lanes)
+        for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes) {
+            const long long i = p * g8 + grp;  // 8-channel group index
+            const float4 g0 = reinterpret_cast<const float4 *>(g)[2 * i], g1 = reinterpret_cast<const float4 *>(g)[2 * i + 1];
+            const uint4 hv = reinterpret_cast<const uint4 *>(h)[i];
+            const uint32_t *hp = &hv.x;
+            float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+            if (gc) {
+                const int pi = (int)p, x = pi % W, r = pi / W, y = r % H, b = r / H;
+                const long long ic = ((long long)(b * (H >> 1) + (y >> 1)) * (W >> 1) + (x >> 1)) * g8 + grp;
+                const float4 c0 = reinterpret_cast<const float4 *>(gc)[2 * ic],
+                             c1 = reinterpret_cast<const float4 *>(gc)[2 * ic + 1];
+                gv[0] += 0.25f * c0.x;
+                gv[1] += 0.25f * c0.y;
+                gv[2] += 0.25f * c0.z;
+                gv[3] += 0.25f * c0.w;
+                gv[4] += 0.25f * c1.x;
+                gv[5] += 0.25f * c1.y;
+                gv[6] += 0.25f * c1.z;
+                gv[7] += 0.25f * c1.w;
+            }
+            uint4 o;
+            uint32_t *op = &o.x;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 hf = bf2_to_f2(hp[k]);
-            __nv_bfloat162 r = __floats2bfloat162_rn(hf.x > 0.f ? gv[2 * k] : 0.f, hf.y > 0.f ? gv[2 * k + 1] : 0.f);
-            op[k] = *reinterpret_cast<uint32_t *>(&r);
+            for (int k = 0; k < 4; ++k) {
+                const float2 hf = bf2_to_f2(hp[k]);
+                __nv_bfloat162 r = __floats2bfloat162_rn(hf.x > 0.f ? gv[2 * k] : 0.f, hf.y > 0.f ? gv[2 * k + 1] : 0.f);
+                op[k] = *reinterpret_cast<uint32_t *>(&r);
+                const float2 rf = bf2_to_f2(op[k]);
+                acc[2 * k] += rf.x;
+                acc[2 * k + 1] += rf.y;
+            }
+            reinterpret_cast<uint4 *>(dz)[i] = o;
         }
-        reinterpret_cast<uint4 *>(dz)[i] = o;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[threadIdx.x * 8 + k] = acc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float sum = 0.f;
+        for (int l = 0; l < lanes; ++l) sum += part[(l * g8 + c / 8) * 8 + (c & 7)];
+        atomicAdd(gb + c, sum);
     }
 }
 
@@ -1575,27 +1631,6 @@ __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, in
                 s4.w += v.w;
             }
         *reinterpret_cast<float4 *>(dd + (((long long)b * h2 + y) * w2 + x) * cu + c) = s4;
-    }
-}
-
-// encoder pooling backward: de_fine [B][H][W][C] += dx_coarse / 4
-// de += 2x2 average-pooling backward of dx; 4 channels a thread
-__global__ void pool_backward_add_kernel(const float *dx, int B, int H, int W, int C, float *de) {
-    GRID_STRIDE(i, (long long)B * H * W * (C / 4)) {
-        const int c = (int)(i % (C / 4)) * 4;
-        long long t = i / (C / 4);
-        const int x = (int)(t % W);
-        t /= W;
-        const int y = (int)(t % H);
-        const int b = (int)(t / H);
-        const float4 v = *reinterpret_cast<const float4 *>(dx + (((long long)b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c);
-        float4 *o = reinterpret_cast<float4 *>(de + i * 4);
-        float4 r = *o;
-        r.x += 0.25f * v.x;
-        r.y += 0.25f * v.y;
-        r.z += 0.25f * v.z;
-        r.w += 0.25f * v.w;
-        *o = r;
     }
 }
 
@@ -1651,36 +1686,6 @@ __global__ void grad_pack_kernel(const float *dw, int co, int ci, int cpad, floa
         const int c = (int)(i % ci);
         const long long t = i / ci;
         g[i] = dw[t * cpad + c];
-    }
-}
-
-// per-channel sums of a BF16 [P][C] gradient (bias gradient)
-// gb[c] += sum over pixels of dz[p][c]: a thread sums 8 channels of a
-// strided set of pixels, the block reduces by channel in shared memory
-__global__ void bias_grad_kernel(const bf16 *dz, long long P, int C, float *gb) {
-    __shared__ float part[256 * 8];
-    const int g8 = C / 8;
-    const int lanes = blockDim.x / g8;  // pixels in flight per block
-    const int grp = threadIdx.x % g8, sub = threadIdx.x / g8;
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (sub < lanes)
-        for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes) {
-            const uint4 v = reinterpret_cast<const uint4 *>(dz + p * C)[grp];
-            const uint32_t *vp = &v.x;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 f = bf2_to_f2(vp[k]);
-                acc[2 * k] += f.x;
-                acc[2 * k + 1] += f.y;
-            }
-        }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) part[threadIdx.x * 8 + k] = acc[k];
-    __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float sum = 0.f;
-        for (int l = 0; l < lanes; ++l) sum += part[(l * g8 + c / 8) * 8 + (c & 7)];
-        atomicAdd(gb + c, sum);
     }
 }
 
@@ -2060,6 +2065,7 @@ cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W
 // backward of conv layer li: dz (BF16 [P][co]) -> weight and bias gradients,
 // and, if dx, the input gradient (FP32 [P][cpad])
 cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, const bf16 *dz, float *dx) {
+    // the bias gradient comes with dz (mask_and_bias)
     UnetLayer &L = u.layers[li];
     const int M = B * H * W;
     cudaError_t e = cudaMemsetAsync(L.dw, 0, (size_t)L.co * 9 * L.cpad * sizeof(float), u.stream);
@@ -2079,11 +2085,7 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
     if ((e = launch_wgrad(u, w)) != cudaSuccess) return e;
     float *gw = u.grad + L.off;
     grad_pack_kernel<<<blocks_for((long long)L.co * 9 * L.ci), 256, 0, u.stream>>>(L.dw, L.co, L.ci, L.cpad, gw);
-    float *gb = gw + (long long)L.co * 9 * L.ci;
-    e = cudaMemsetAsync(gb, 0, L.co * sizeof(float), u.stream);
-    if (e != cudaSuccess) return e;
-    bias_grad_kernel<<<256, 256, 0, u.stream>>>(dz, M, L.co, gb);
-    count_launch(2);
+    count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!dx) return cudaSuccess;
     ConvArgs a{};
@@ -2168,6 +2170,19 @@ cudaError_t forward(mclbm_unet &u, int B, int H, int W) {
     return cudaGetLastError();
 }
 
+// dz (u.z) = (g + gc / 4 upsampled, if gc) masked by the forward activation
+// h > 0, and layer li's bias gradient from the same pass (images H x W)
+cudaError_t mask_and_bias(mclbm_unet &u, int li, const float *g, const float *gc, int H, int W, const bf16 *h,
+                          long long P, int C) {
+    const UnetLayer &L = u.layers[li];
+    float *gb = u.grad + L.off + (long long)L.co * 9 * L.ci;
+    cudaError_t e = cudaMemsetAsync(gb, 0, C * sizeof(float), u.stream);
+    if (e != cudaSuccess) return e;
+    relu_mask_bias_kernel<<<4 * sm_count(), 256, 0, u.stream>>>(g, gc, H, W, h, u.z, P, C, gb);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
     const int Lv = u.levels;
     const long long P = (long long)B * H * W;
@@ -2175,9 +2190,8 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
     cudaError_t e = cudaMemsetAsync(u.grad + hd.off, 0, (u.base + 1) * sizeof(float), u.stream);
     if (e != cudaSuccess) return e;
     const bf16 *d0 = Lv > 1 ? u.d_out[0] : u.e_out[0];
-    head_backward_kernel<<<blocks_for(P * 32 < 152LL * 8 * 256 ? P * 32 : 152LL * 8 * 256), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
-                                                              u.theta + hd.off, u.base, P, u.dd,
-                                                              u.grad + hd.off);
+    head_backward_kernel<<<4 * sm_count(), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
+                                                               u.theta + hd.off, u.base, P, u.dd, u.grad + hd.off);
     count_launch();
     for (int l = 0; l < Lv; ++l) {
         const long long n = (P >> (2 * l)) * ch(u, l);
@@ -2189,12 +2203,10 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         const long long Pl = (long long)B * h * w;
         const int cl = ch(u, l), cu = ch(u, l + 1);
         const int li = 2 * Lv + 2 * (Lv - 2 - l);
-        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.dd, u.d_out[l], u.z, Pl * cl);
-        count_launch();
+        if ((e = mask_and_bias(u, li + 1, u.dd, nullptr, h, w, u.d_out[l], Pl, cl)) != cudaSuccess) return e;
         if ((e = conv_backward(u, li + 1, In{u.d_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
             return e;
-        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.s2, u.d_ha[l], u.z, Pl * cl);
-        count_launch();
+        if ((e = mask_and_bias(u, li, u.s2, nullptr, h, w, u.d_ha[l], Pl, cl)) != cudaSuccess) return e;
         const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
         if ((e = conv_backward(u, li, In{u.e_out[l], coarse, cl, cu}, B, h, w, u.z, u.s1)) != cudaSuccess)
             return e;
@@ -2215,22 +2227,18 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         const int h = H >> l, w = W >> l;
         const long long Pl = (long long)B * h * w;
         const int cl = ch(u, l);
-        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.de[l], u.e_out[l], u.z, Pl * cl);
-        count_launch();
+        // below the coarsest level, the gradient through the pooling into
+        // level l + 1 (in s1, from its first convolution) joins de[l] here
+        if ((e = mask_and_bias(u, 2 * l + 1, u.de[l], l < Lv - 1 ? u.s1 : nullptr, h, w, u.e_out[l], Pl, cl)) !=
+            cudaSuccess)
+            return e;
         if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
             return e;
-        relu_mask_kernel<<<blocks_for(Pl * cl / 8), 256, 0, u.stream>>>(u.s2, u.e_ha[l], u.z, Pl * cl);
-        count_launch();
+        if ((e = mask_and_bias(u, 2 * l, u.s2, nullptr, h, w, u.e_ha[l], Pl, cl)) != cudaSuccess) return e;
         const int cin = l == 0 ? UNET_PAD0 : ch(u, l - 1);
         if ((e = conv_backward(u, 2 * l, In{u.a_in[l], nullptr, cin, 0}, B, h, w, u.z, l > 0 ? u.s1 : nullptr)) !=
             cudaSuccess)
             return e;
-        if (l > 0) {
-            const int cp = ch(u, l - 1);
-            pool_backward_add_kernel<<<blocks_for(Pl * cp), 256, 0, u.stream>>>(u.s1, B, 2 * h, 2 * w, cp,
-                                                                                  u.de[l - 1]);
-            count_launch();
-        }
     }
     return cudaGetLastError();
 }
