@@ -1251,18 +1251,23 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 
 // dW += the shared-tap kernel's partial sums: CTA q * combos + combo holds
 // [co][tap][ci] of the (32-channel slice of dZ, 32-channel chunk of X) pair
-// combo; a thread sums one element over the per CTAs of its pair, in a fixed
-// order
+// combo.  Thread (element, split) sums the CTAs q = split, split + splits, ...
+// of its pair and adds the sum to dW (dW starts at zero)
 __global__ void wgrad_reduce_kernel(const float *part, int combos, int per, int chunks, int K0, float *dw) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)combos * WT_PART;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int combo = (int)(i / WT_PART), e = (int)(i - (long long)combo * WT_PART);
-        float sum = 0.f;
-        for (int q = 0; q < per; ++q) sum += part[((size_t)q * combos + combo) * WT_PART + e];
-        const int co = e / (9 * 32), tap = (e / 32) % 9, ci = e % 32;
-        const int mt = combo / chunks, cc = combo - mt * chunks;
-        dw[((size_t)(mt * 32 + co) * 9 + tap) * K0 + cc * 32 + ci] += sum;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)combos * WT_PART) return;
+    const int combo = (int)(i / WT_PART), e = (int)(i - (long long)combo * WT_PART);
+    const int split = blockIdx.y, splits = gridDim.y;
+    float s0 = 0.f, s1 = 0.f;
+    int q = split;
+    for (; q + splits < per; q += 2 * splits) {
+        s0 += part[((size_t)q * combos + combo) * WT_PART + e];
+        s1 += part[((size_t)(q + splits) * combos + combo) * WT_PART + e];
     }
+    if (q < per) s0 += part[((size_t)q * combos + combo) * WT_PART + e];
+    const int co = e / (9 * 32), tap = (e / 32) % 9, ci = e % 32;
+    const int mt = combo / chunks, cc = combo - mt * chunks;
+    atomicAdd(dw + ((size_t)(mt * 32 + co) * 9 + tap) * K0 + cc * 32 + ci, s0 + s1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1592,25 +1597,17 @@ __global__ void relu_mask_bias_kernel(const float *g, const float *gc, int H, in
     }
 }
 
-// decoder concat backward: de [P][cs] += dcat[:, :cs]; dd (coarse
-// [B][H/2][W/2][cu]) = sum over the 2x2 block of dcat[:, cs:]
-// gradient of concat(e, up(d)): de += first cs channels; dd = the last cu
-// channels summed over each 2x2 block (nearest-upsampling backward); 4
-// channels a thread
+// gradient of concat(e, up(d)) from dcat [P][cs + cu]: de [P][cs] = the first
+// cs channels (the skip connection's gradient; de has no other writer); dd
+// (coarse [B][H/2][W/2][cu]) = the last cu channels summed over each 2 x 2
+// block (nearest-upsampling backward); 4 channels a thread
 __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, int H, int W, float *de,
                                     float *dd) {
     const int ct = cs + cu;
     GRID_STRIDE(i, (long long)B * H * W * (cs / 4)) {
         const long long p = i / (cs / 4);
         const int c = (int)(i - p * (cs / 4)) * 4;
-        float4 *o = reinterpret_cast<float4 *>(de + p * cs + c);
-        const float4 v = *reinterpret_cast<const float4 *>(dcat + p * ct + c);
-        float4 r = *o;
-        r.x += v.x;
-        r.y += v.y;
-        r.z += v.z;
-        r.w += v.w;
-        *o = r;
+        *reinterpret_cast<float4 *>(de + p * cs + c) = *reinterpret_cast<const float4 *>(dcat + p * ct + c);
     }
     const int h2 = H / 2, w2 = W / 2;
     GRID_STRIDE(i, (long long)B * h2 * w2 * (cu / 4)) {
@@ -1631,19 +1628,6 @@ __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, in
                 s4.w += v.w;
             }
         *reinterpret_cast<float4 *>(dd + (((long long)b * h2 + y) * w2 + x) * cu + c) = s4;
-    }
-}
-
-__global__ void add_kernel(float *a, const float *b, long long n) {
-    GRID_STRIDE(i, n / 4) {
-        float4 *o = reinterpret_cast<float4 *>(a) + i;
-        const float4 v = reinterpret_cast<const float4 *>(b)[i];
-        float4 r = *o;
-        r.x += v.x;
-        r.y += v.y;
-        r.z += v.z;
-        r.w += v.w;
-        *o = r;
     }
 }
 
@@ -1968,8 +1952,15 @@ cudaError_t launch_wgrad_tap(const mclbm_unet &u, const WgradRowArgs &a, int ux)
     WgradRowArgs b = a;
     b.part = u.wg_part;
     wgrad_tap_kernel<<<grid, ROW_THREADS, smem, u.stream>>>(b, S, ux, tdz, tmx, tmu);
-    wgrad_reduce_kernel<<<blocks_for((long long)combos * WT_PART), 256, 0, u.stream>>>(
-        u.wg_part, combos, grid / combos, (a.c0 + a.c1) / 32, a.c0 + a.c1, a.dw);
+    // enough threads for the GPU: the partials of each pair split over up to
+    // 16 groups of CTAs
+    const int per = grid / combos;
+    const long long nel = (long long)combos * WT_PART;
+    int splits = (int)((8LL * 152 * 256 + nel - 1) / nel);
+    if (splits > 16) splits = 16;
+    if (splits > per) splits = per;
+    wgrad_reduce_kernel<<<dim3((unsigned)((nel + 255) / 256), (unsigned)splits), 256, 0, u.stream>>>(
+        u.wg_part, combos, per, (a.c0 + a.c1) / 32, a.c0 + a.c1, a.dw);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -2193,10 +2184,6 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
     head_backward_kernel<<<4 * sm_count(), 256, 0, u.stream>>>(u.phi, u.t_f, u.mask_f, u.loss_stat, d0,
                                                                u.theta + hd.off, u.base, P, u.dd, u.grad + hd.off);
     count_launch();
-    for (int l = 0; l < Lv; ++l) {
-        const long long n = (P >> (2 * l)) * ch(u, l);
-        if ((e = cudaMemsetAsync(u.de[l], 0, n * sizeof(float), u.stream)) != cudaSuccess) return e;
-    }
     // decoder, fine to coarse: the layer index of dec(l)a is 2L + 2 (L - 2 - l)
     for (int l = 0; l <= Lv - 2; ++l) {
         const int h = H >> l, w = W >> l;
@@ -2213,23 +2200,18 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         split_concat_kernel<<<blocks_for(Pl * cl / 4), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l], u.dd);
         count_launch();
     }
-    if (Lv > 1) {
-        const long long n = (P >> (2 * (Lv - 1))) * ch(u, Lv - 1);
-        add_kernel<<<blocks_for(n / 4), 256, 0, u.stream>>>(u.de[Lv - 1], u.dd, n);
-        count_launch();
-    } else {
-        const long long n = P * ch(u, 0);
-        add_kernel<<<blocks_for(n / 4), 256, 0, u.stream>>>(u.de[0], u.dd, n);
-        count_launch();
-    }
     // encoder, coarse to fine
     for (int l = Lv - 1; l >= 0; --l) {
         const int h = H >> l, w = W >> l;
         const long long Pl = (long long)B * h * w;
         const int cl = ch(u, l);
-        // below the coarsest level, the gradient through the pooling into
-        // level l + 1 (in s1, from its first convolution) joins de[l] here
-        if ((e = mask_and_bias(u, 2 * l + 1, u.de[l], l < Lv - 1 ? u.s1 : nullptr, h, w, u.e_out[l], Pl, cl)) !=
+        // the gradient reaching e_out[l]: at the coarsest level the decoder's
+        // (dd: the upsampling backward of the last split, or the head's when
+        // there is one level); below it the skip connection's (de[l]) plus
+        // the gradient through the pooling into level l + 1 (in s1, from that
+        // level's first convolution)
+        const float *g_out = l == Lv - 1 ? u.dd : u.de[l];
+        if ((e = mask_and_bias(u, 2 * l + 1, g_out, l < Lv - 1 ? u.s1 : nullptr, h, w, u.e_out[l], Pl, cl)) !=
             cudaSuccess)
             return e;
         if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
