@@ -1631,36 +1631,32 @@ __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, in
     }
 }
 
-// FP32 master weights [co][3][3][ci] -> BF16 [co][9][cpad] (forward) and
-// [cpad][9][co] (data gradient), zero in the padded channels
-__global__ void weights_bf16_kernel(const float *w, int co, int ci, int cpad, bf16 *wf, bf16 *wt) {
+// index of element (n_all, tap, k_all) of BF16 weights [N][9][K0] in the row
+// kernel's shared-memory image (per N tile of BN and chunk of 32 input channels,
+// [tap][n / 8][k / 8][n % 8][k % 8]: the K-major core-matrix layout of the B
+// operand; tiles and chunks in (N tile, chunk) order)
+__device__ __forceinline__ long long row_pack_index(int n_all, int tap, int k_all, int K0, int BN) {
+    const int nt = n_all / BN, n = n_all - nt * BN, kc = k_all / 32, k = k_all - kc * 32;
+    return ((long long)(nt * (K0 / 32) + kc) * 9 + tap) * BN * 32 + ((n >> 3) * 4 + (k >> 3)) * 64 + (n & 7) * 8 +
+           (k & 7);
+}
+
+// all four BF16 images of a layer's FP32 master weights w [co][3][3][ci] in
+// one pass: wf [co][9][cpad] (forward), wt [cpad][9][co] (data gradient) and,
+// where the row kernel takes the layer (bn_f, bn_t nonzero), the same two in
+// its packed layout; zero in the padded channels
+__global__ void weights_prep_kernel(const float *w, int co, int ci, int cpad, int bn_f, int bn_t, bf16 *wf,
+                                    bf16 *wt, bf16 *wpf, bf16 *wpt) {
     GRID_STRIDE(i, (long long)co * 9 * cpad) {
         const int c = (int)(i % cpad);
         const long long t = i / cpad;
         const int tap = (int)(t % 9);
         const int o = (int)(t / 9);
-        const float v = c < ci ? w[((long long)o * 9 + tap) * ci + c] : 0.f;
-        const bf16 h = __float2bfloat16_rn(v);
+        const bf16 h = __float2bfloat16_rn(c < ci ? w[((long long)o * 9 + tap) * ci + c] : 0.f);
         wf[i] = h;
-        if (wt) wt[((long long)c * 9 + tap) * co + o] = h;
-    }
-}
-
-// BF16 weights w [N][9][K0] -> the row kernel's shared-memory image: per N
-// tile of BN and chunk of 32 input channels, [tap][n / 8][k / 8][n % 8][k % 8]
-// (the K-major core-matrix layout of the B operand), tiles and chunks in
-// (N tile, chunk) order
-__global__ void pack_row_kernel(const bf16 *w, int N, int K0, int BN, bf16 *out) {
-    const int kchunks = K0 / 32;
-    GRID_STRIDE(i, (long long)N * 9 * K0) {
-        const int k_all = (int)(i % K0);
-        const long long t = i / K0;
-        const int tap = (int)(t % 9);
-        const int n_all = (int)(t / 9);
-        const int nt = n_all / BN, n = n_all - nt * BN, kc = k_all / 32, k = k_all - kc * 32;
-        const long long dst = ((long long)(nt * kchunks + kc) * 9 + tap) * BN * 32 +
-                              ((n >> 3) * 4 + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7);
-        out[dst] = w[i];
+        wt[((long long)c * 9 + tap) * co + o] = h;
+        if (bn_f) wpf[row_pack_index(o, tap, c, cpad, bn_f)] = h;
+        if (bn_t) wpt[row_pack_index(c, tap, o, co, bn_t)] = h;
     }
 }
 
@@ -2101,19 +2097,9 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
 cudaError_t refresh_weights(mclbm_unet &u) {
     for (auto &L : u.layers) {
         if (L.k != 3) continue;
-        weights_bf16_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
-            u.theta + L.off, L.co, L.ci, L.cpad, L.wf, L.wt);
+        weights_prep_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
+            u.theta + L.off, L.co, L.ci, L.cpad, row_bn(L.co), row_bn(L.cpad), L.wf, L.wt, L.wpf, L.wpt);
         count_launch();
-        if (row_bn(L.co)) {
-            pack_row_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
-                L.wf, L.co, L.cpad, row_bn(L.co), L.wpf);
-            count_launch();
-        }
-        if (row_bn(L.cpad)) {
-            pack_row_kernel<<<blocks_for((long long)L.co * 9 * L.cpad), 256, 0, u.stream>>>(
-                L.wt, L.cpad, L.co, row_bn(L.cpad), L.wpt);
-            count_launch();
-        }
     }
     return cudaGetLastError();
 }
