@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         for (int k = 0; k < 4; ++k) {
             mbar_init(&full[k], 1);
             mbar_init(&done[k], 1);
-            mbar_init(&expd[k], ROW_EXP);
+            mbar_init(&expd[k], ROW_EXP / 32);  // one arrival per expansion warp
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(&accf[k], 1);
@@ -632,37 +632,48 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
         // no parity wait here is ever two phases ahead (a wait for parity P
         // passes whenever the barrier is not in a phase of parity P)
         const int et = tid - 64, qq = et & 3;
+        int st = 0, i = 0, kc = 0;  // advance incrementally, as in the MMA loop
+        uint32_t ph = 0;
         for (int j = 0; plan.ux && j < njobs && !stopped(); ++j) {
-            const int st = j % S, i = j / kchunks, kc = j - i * kchunks;
             // the stage's previous job has been read by its MMAs
-            if (j >= S && !mbar_wait_sleep(&done[st], ((j - S) / S) & 1, WAIT_LIMIT_NS)) {
+            if (j >= S && !mbar_wait_sleep(&done[st], ph ^ 1u, WAIT_LIMIT_NS)) {
                 give_up();
                 break;
             }
-            if (kc * 32 < a.c0) continue;
-            // this job's coarse rows have landed
-            if (!mbar_wait_sleep(&full[st], (j / S) & 1, WAIT_LIMIT_NS)) {
-                give_up();
-                break;
-            }
-            // nearest upsampling: halo pixel (r, p) takes coarse pixel
-            // ((y + r - 1) >> 1, (x0 + p - 1) >> 1); relative to the staged
-            // rows that is (cr(r), (p + 1) >> 1) since x0 is even
-            const Where w = where(i);
-            unsigned char *As = stg + st * STG;
-            const unsigned char *U = As + RA_BYTES;
-            const uint32_t hbase = smem_u32(As);
-            for (int r = 0; r < 3; ++r) {
-                const int cr = ((w.y + r - 1) >> 1) - ((w.y - 1) >> 1);
-                for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
-                    const int pix = r * RHALO + p;
-                    const int sw = (int)(((hbase + pix * 64) >> 7) & 3u);  // 64-byte swizzle of the row
-                    *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ sw) << 4)) =
-                        *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
+            if (kc * 32 >= a.c0) {
+                // this job's coarse rows have landed
+                if (!mbar_wait_sleep(&full[st], ph, WAIT_LIMIT_NS)) {
+                    give_up();
+                    break;
                 }
+                // nearest upsampling: halo pixel (r, p) takes coarse pixel
+                // ((y + r - 1) >> 1, (x0 + p - 1) >> 1); relative to the staged
+                // rows that is (cr(r), (p + 1) >> 1) since x0 is even.  Stages
+                // are 1024-byte aligned, so the 64-byte swizzle of halo pixel
+                // pix is (pix / 2) & 3
+                const int y = where(i).y;
+                unsigned char *As = stg + st * STG;
+                const unsigned char *U = As + RA_BYTES;
+                for (int r = 0; r < 3; ++r) {
+                    const int cr = ((y + r - 1) >> 1) - ((y - 1) >> 1);
+                    for (int p = et >> 2; p < RHALO; p += ROW_EXP / 4) {
+                        const int pix = r * RHALO + p;
+                        *reinterpret_cast<uint4 *>(As + pix * 64 + ((qq ^ ((pix >> 1) & 3)) << 4)) =
+                            *reinterpret_cast<const uint4 *>(U + (cr * 66 + ((p + 1) >> 1)) * 64 + qq * 16);
+                    }
+                }
+                fence_proxy_async();  // each thread's generic writes, for the tensor cores' reads
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&expd[st]);
             }
-            fence_proxy_async();  // generic writes, for the tensor cores' reads
-            mbar_arrive(&expd[st]);
+            if (++st == S) {
+                st = 0;
+                ph ^= 1u;
+            }
+            if (++kc == kchunks) {
+                kc = 0;
+                ++i;
+            }
         }
     } else {
         // ---------------- epilogue (128 threads) ----------------
