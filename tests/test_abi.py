@@ -62,3 +62,12 @@ def test_unet_rejects_bad_shapes_without_a_device():
         rc = lib.mclbm_unet_create(levels, base, b, hh, ww, None, C.byref(h))
         assert rc == mclbm.MCLBM_ERR_ARG
         assert h.value is None
+
+
+def test_unet_switches_reject_bad_arguments_without_a_device():
+    lib = mclbm.load()
+    assert lib.mclbm_unet_set_max_ctas(None, 4) == mclbm.MCLBM_ERR_ARG
+    assert lib.mclbm_unet_set_shared_taps(None, 1) == mclbm.MCLBM_ERR_ARG
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_unet_set_shared_taps(None, 0)
+    assert e.value.code == mclbm.MCLBM_ERR_ARG
