@@ -93,6 +93,12 @@ struct ConvArgs {
     bf16 *ybf;            // ReLU(C + bias) as BF16 [M][N], or null
     bf16 *yup;            // the same, nearest-upsampled to [B][2H][2W][N] (the next decoder's input), or null
     float *yf;            // C as FP32 [M][N], or null
+    // concat data gradient (row kernel only; 0 = off): columns n < split_cs
+    // go to yf as [M][split_cs], the others summed over each horizontal pixel
+    // pair to yh [B][H][W/2][N - split_cs] (the first half of the
+    // nearest-upsampling backward)
+    int split_cs;
+    float *yh;
     int *err;             // set when a bounded wait gives up
 };
 
@@ -146,7 +152,26 @@ __device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n
     float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-    if (a.yf) {
+    if (a.yf && a.split_cs) {
+        // n is the same in the whole warp and the split falls on a 16-column
+        // boundary; lanes 2j, 2j + 1 hold pixels 2x, 2x + 1 of one row (row
+        // tiles start at multiples of 128)
+        if (n < a.split_cs) {
+            float4 *d = reinterpret_cast<float4 *>(a.yf + row * a.split_cs + n);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+            if (!(row & 1)) {
+                float4 *d = reinterpret_cast<float4 *>(a.yh + (row >> 1) * (size_t)(a.N - a.split_cs) +
+                                                       (n - a.split_cs));
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            }
+        }
+    } else if (a.yf) {
         float4 *d = reinterpret_cast<float4 *>(a.yf + row * a.N + n);
 #pragma unroll
         for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
@@ -1643,6 +1668,25 @@ __global__ void split_concat_kernel(const float *dcat, int cs, int cu, int B, in
     }
 }
 
+// second half of the nearest-upsampling backward after a split epilogue:
+// dd [B][H/2][W/2][cu] = dh [B][H][W/2][cu] summed over each vertical row
+// pair (dh already holds the horizontal pair sums); 4 channels a thread
+__global__ void pair_rows_kernel(const float *dh, int cu, int B, int H, int Wh, float *dd) {
+    const int h2 = H / 2;
+    GRID_STRIDE(i, (long long)B * h2 * Wh * (cu / 4)) {
+        const int c = (int)(i % (cu / 4)) * 4;
+        long long t = i / (cu / 4);
+        const int x = (int)(t % Wh);
+        t /= Wh;
+        const int y = (int)(t % h2);
+        const int b = (int)(t / h2);
+        const float4 u = *reinterpret_cast<const float4 *>(dh + (((long long)b * H + 2 * y) * Wh + x) * cu + c);
+        const float4 v = *reinterpret_cast<const float4 *>(dh + (((long long)b * H + 2 * y + 1) * Wh + x) * cu + c);
+        *reinterpret_cast<float4 *>(dd + (((long long)b * h2 + y) * Wh + x) * cu + c) =
+            make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+    }
+}
+
 // index of element (n_all, tap, k_all) of BF16 weights [N][9][K0] in the row
 // kernel's shared-memory image (per N tile of BN and chunk of 32 input channels,
 // [tap][n / 8][k / 8][n % 8][k % 8]: the K-major core-matrix layout of the B
@@ -1915,6 +1959,7 @@ cudaError_t launch_conv(const mclbm_unet &u, ConvArgs a) {
             default: break;
         }
     }
+    if (a.split_cs) return cudaErrorInvalidValue;  // the split epilogue is the row kernel's
     switch (a.N) {
         case 32: return launch_tc<32>(u, a);
         case 64: return launch_tc<64>(u, a);
@@ -2063,7 +2108,11 @@ cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W
 
 // backward of conv layer li: dz (BF16 [P][co]) -> weight and bias gradients,
 // and, if dx, the input gradient (FP32 [P][cpad])
-cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, const bf16 *dz, float *dx) {
+// With split_cs (a decoder's concat input, row kernel only), the input
+// gradient goes out split: the first split_cs channels to dx as [P][split_cs],
+// the upsampled channels pair-summed along x to dh (see ConvArgs)
+cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, const bf16 *dz, float *dx,
+                          int split_cs = 0, float *dh = nullptr) {
     // the bias gradient comes with dz (mask_and_bias)
     UnetLayer &L = u.layers[li];
     const int M = B * H * W;
@@ -2103,6 +2152,8 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
     a.bias = nullptr;
     a.ybf = nullptr;
     a.yf = dx;
+    a.split_cs = split_cs;
+    a.yh = dh;
     return launch_conv(u, a);
 }
 
@@ -2193,9 +2244,18 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
             return e;
         if ((e = mask_and_bias(u, li, u.s2, nullptr, h, w, u.d_ha[l], Pl, cl)) != cudaSuccess) return e;
         const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
-        if ((e = conv_backward(u, li, In{u.e_out[l], coarse, cl, cu}, B, h, w, u.z, u.s1)) != cudaSuccess)
-            return e;
-        split_concat_kernel<<<blocks_for(Pl * cl / 4), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l], u.dd);
+        const In in_a{u.e_out[l], coarse, cl, cu};
+        if (w % RW == 0 && row_bn(u.layers[li].cpad)) {
+            // the row kernel's epilogue writes the skip gradient to de[l] and
+            // the pair sums along x to s1; the row pairs finish the
+            // upsampling backward
+            if ((e = conv_backward(u, li, in_a, B, h, w, u.z, u.de[l], cl, u.s1)) != cudaSuccess) return e;
+            pair_rows_kernel<<<blocks_for(Pl * cu / 16), 256, 0, u.stream>>>(u.s1, cu, B, h, w / 2, u.dd);
+        } else {
+            if ((e = conv_backward(u, li, in_a, B, h, w, u.z, u.s1)) != cudaSuccess) return e;
+            split_concat_kernel<<<blocks_for(Pl * cl / 4), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l],
+                                                                                u.dd);
+        }
         count_launch();
     }
     // encoder, coarse to fine
