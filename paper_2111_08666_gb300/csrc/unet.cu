@@ -99,6 +99,10 @@ struct ConvArgs {
     // nearest-upsampling backward)
     int split_cs;
     float *yh;
+    // data gradient into a ReLU layer: C masked by the forward activation
+    // mask_h > 0 ([M][N]) as BF16 into ydz, or null
+    const bf16 *mask_h;
+    bf16 *ydz;
     int *err;             // set when a bounded wait gives up
 };
 
@@ -152,6 +156,21 @@ __device__ __forceinline__ void store_row16(const ConvArgs &a, size_t row, int n
     float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+    if (a.ydz) {
+        const uint4 *hp = reinterpret_cast<const uint4 *>(a.mask_h + row * a.N + n);
+        const uint4 h0 = hp[0], h1 = hp[1];
+        const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+        uint32_t o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[k]));
+            __nv_bfloat162 q = __floats2bfloat162_rn(hf.x > 0.f ? v[2 * k] : 0.f, hf.y > 0.f ? v[2 * k + 1] : 0.f);
+            o[k] = *reinterpret_cast<uint32_t *>(&q);
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(a.ydz + row * a.N + n);
+        d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
     if (a.yf && a.split_cs) {
         // n is the same in the whole warp and the split falls on a 16-column
         // boundary; lanes 2j, 2j + 1 hold pixels 2x, 2x + 1 of one row (row
@@ -1577,6 +1596,36 @@ __global__ void head_backward_kernel(const float *phi, const float *t, const flo
     }
 }
 
+// gb[c] += sum over pixels of dz[p][c] (BF16 [P][C]): a thread sums 8
+// channels of a strided set of pixels, the block reduces by channel in
+// shared memory and adds to gb
+__global__ void bias_sum_kernel(const bf16 *dz, long long P, int C, float *gb) {
+    __shared__ float part[256 * 8];
+    const int g8 = C / 8;
+    const int lanes = blockDim.x / g8;
+    const int grp = threadIdx.x % g8, sub = threadIdx.x / g8;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (sub < lanes)
+        for (long long p = (long long)blockIdx.x * lanes + sub; p < P; p += (long long)gridDim.x * lanes) {
+            const uint4 v = reinterpret_cast<const uint4 *>(dz)[p * g8 + grp];
+            const uint32_t *vp = &v.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f = bf2_to_f2(vp[k]);
+                acc[2 * k] += f.x;
+                acc[2 * k + 1] += f.y;
+            }
+        }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[threadIdx.x * 8 + k] = acc[k];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float sum = 0.f;
+        for (int l = 0; l < lanes; ++l) sum += part[(l * g8 + c / 8) * 8 + (c & 7)];
+        atomicAdd(gb + c, sum);
+    }
+}
+
 // dz = g where the forward activation h > 0, else 0 (BF16), and the bias
 // gradient gb[c] += sum over pixels of that BF16 dz[p][c], in one pass: a
 // thread owns 8 channels of a strided set of pixels, the block reduces by
@@ -1772,7 +1821,7 @@ struct mclbm_unet {
     std::vector<bf16 *> up;  // up[0]: d_1 (or e_1) upsampled to level 0, the finest decoder's input
     std::vector<float *> de;                              // per level
     float *phi = nullptr, *s1 = nullptr, *s2 = nullptr, *dd = nullptr;
-    bf16 *z = nullptr;
+    bf16 *z = nullptr, *z2 = nullptr;  // dz of a layer; z2 takes the next one's while z is read
     float *xin_f = nullptr, *t_f = nullptr, *mask_f = nullptr;  // staging of host inputs
     double *loss_part = nullptr, *loss_stat = nullptr;
     int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
@@ -2111,8 +2160,11 @@ cudaError_t conv_forward(const mclbm_unet &u, int li, In in, int B, int H, int W
 // With split_cs (a decoder's concat input, row kernel only), the input
 // gradient goes out split: the first split_cs channels to dx as [P][split_cs],
 // the upsampled channels pair-summed along x to dh (see ConvArgs)
+// With mask_h, the input gradient goes out masked by that forward
+// activation, as BF16 into ydz (the next layer's dz)
 cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, const bf16 *dz, float *dx,
-                          int split_cs = 0, float *dh = nullptr) {
+                          int split_cs = 0, float *dh = nullptr, const bf16 *mask_h = nullptr,
+                          bf16 *ydz = nullptr) {
     // the bias gradient comes with dz (mask_and_bias)
     UnetLayer &L = u.layers[li];
     const int M = B * H * W;
@@ -2135,7 +2187,7 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
     grad_pack_kernel<<<blocks_for((long long)L.co * 9 * L.ci), 256, 0, u.stream>>>(L.dw, L.co, L.ci, L.cpad, gw);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (!dx) return cudaSuccess;
+    if (!dx && !ydz) return cudaSuccess;
     ConvArgs a{};
     a.x0 = dz;
     a.x1 = nullptr;
@@ -2154,7 +2206,20 @@ cudaError_t conv_backward(mclbm_unet &u, int li, In in, int B, int H, int W, con
     a.yf = dx;
     a.split_cs = split_cs;
     a.yh = dh;
+    a.mask_h = mask_h;
+    a.ydz = ydz;
     return launch_conv(u, a);
+}
+
+// layer li's bias gradient from its BF16 dz [P][C]
+cudaError_t bias_grad(mclbm_unet &u, int li, const bf16 *dz, long long P, int C) {
+    const UnetLayer &L = u.layers[li];
+    float *gb = u.grad + L.off + (long long)L.co * 9 * L.ci;
+    cudaError_t e = cudaMemsetAsync(gb, 0, C * sizeof(float), u.stream);
+    if (e != cudaSuccess) return e;
+    bias_sum_kernel<<<4 * sm_count(), 256, 0, u.stream>>>(dz, P, C, gb);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t refresh_weights(mclbm_unet &u) {
@@ -2240,19 +2305,21 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         const int cl = ch(u, l), cu = ch(u, l + 1);
         const int li = 2 * Lv + 2 * (Lv - 2 - l);
         if ((e = mask_and_bias(u, li + 1, u.dd, nullptr, h, w, u.d_out[l], Pl, cl)) != cudaSuccess) return e;
-        if ((e = conv_backward(u, li + 1, In{u.d_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
+        // the data gradient of dec(l)b leaves masked by d_ha[l], as dec(l)a's dz
+        if ((e = conv_backward(u, li + 1, In{u.d_ha[l], nullptr, cl, 0}, B, h, w, u.z, nullptr, 0, nullptr,
+                               u.d_ha[l], u.z2)) != cudaSuccess)
             return e;
-        if ((e = mask_and_bias(u, li, u.s2, nullptr, h, w, u.d_ha[l], Pl, cl)) != cudaSuccess) return e;
+        if ((e = bias_grad(u, li, u.z2, Pl, cl)) != cudaSuccess) return e;
         const bf16 *coarse = l == Lv - 2 ? u.e_out[Lv - 1] : u.d_out[l + 1];
         const In in_a{u.e_out[l], coarse, cl, cu};
         if (w % RW == 0 && row_bn(u.layers[li].cpad)) {
             // the row kernel's epilogue writes the skip gradient to de[l] and
             // the pair sums along x to s1; the row pairs finish the
             // upsampling backward
-            if ((e = conv_backward(u, li, in_a, B, h, w, u.z, u.de[l], cl, u.s1)) != cudaSuccess) return e;
+            if ((e = conv_backward(u, li, in_a, B, h, w, u.z2, u.de[l], cl, u.s1)) != cudaSuccess) return e;
             pair_rows_kernel<<<blocks_for(Pl * cu / 16), 256, 0, u.stream>>>(u.s1, cu, B, h, w / 2, u.dd);
         } else {
-            if ((e = conv_backward(u, li, in_a, B, h, w, u.z, u.s1)) != cudaSuccess) return e;
+            if ((e = conv_backward(u, li, in_a, B, h, w, u.z2, u.s1)) != cudaSuccess) return e;
             split_concat_kernel<<<blocks_for(Pl * cl / 4), 256, 0, u.stream>>>(u.s1, cl, cu, B, h, w, u.de[l],
                                                                                 u.dd);
         }
@@ -2272,11 +2339,13 @@ cudaError_t backward(mclbm_unet &u, int B, int H, int W) {
         if ((e = mask_and_bias(u, 2 * l + 1, g_out, l < Lv - 1 ? u.s1 : nullptr, h, w, u.e_out[l], Pl, cl)) !=
             cudaSuccess)
             return e;
-        if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, u.s2)) != cudaSuccess)
+        // the data gradient of enc(l)b leaves masked by e_ha[l], as enc(l)a's dz
+        if ((e = conv_backward(u, 2 * l + 1, In{u.e_ha[l], nullptr, cl, 0}, B, h, w, u.z, nullptr, 0, nullptr,
+                               u.e_ha[l], u.z2)) != cudaSuccess)
             return e;
-        if ((e = mask_and_bias(u, 2 * l, u.s2, nullptr, h, w, u.e_ha[l], Pl, cl)) != cudaSuccess) return e;
+        if ((e = bias_grad(u, 2 * l, u.z2, Pl, cl)) != cudaSuccess) return e;
         const int cin = l == 0 ? UNET_PAD0 : ch(u, l - 1);
-        if ((e = conv_backward(u, 2 * l, In{u.a_in[l], nullptr, cin, 0}, B, h, w, u.z, l > 0 ? u.s1 : nullptr)) !=
+        if ((e = conv_backward(u, 2 * l, In{u.a_in[l], nullptr, cin, 0}, B, h, w, u.z2, l > 0 ? u.s1 : nullptr)) !=
             cudaSuccess)
             return e;
     }
@@ -2453,6 +2522,7 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     A((void **)&u->s2, (size_t)P * UNET_PAD0 * 4 + (size_t)P * base * 4);
     A((void **)&u->dd, (size_t)P * base * 4);
     A((void **)&u->z, (size_t)P * base * 2);
+    A((void **)&u->z2, (size_t)P * base * 2);
     A((void **)&u->xin_f, (size_t)P * 4 * 4);
     A((void **)&u->t_f, (size_t)P * 4);
     A((void **)&u->mask_f, (size_t)P * 4);
