@@ -376,10 +376,10 @@ int mclbm_unet_param_count(const mclbm_unet *u, int64_t *n);
  * NULL network or n < 0. */
 int mclbm_unet_set_max_ctas(mclbm_unet *u, int n);
 /* Weight-gradient kernel choice for image widths that are multiples of 128.
- * enable = 1 (the default): layers of up to 128 output channels take the
- * shared-tap kernel (the nine taps of a 32-channel slice in one tensor-core
- * product, dZ rows kept in a ring down 128-pixel strips); enable = 0: every
- * layer takes the per-tap kernel.  The two give the same gradient up to the
+ * enable = 1 (the default): every layer takes the shared-tap kernel (the
+ * nine taps of a 32-output-channel slice in one tensor-core product, dZ rows
+ * kept in a ring down 128-pixel strips); enable = 0: every layer takes the
+ * per-tap kernel (one product per tap).  The two give the same gradient up to the
  * order of the FP32 sums, which lets a test cross-check them.  Errors:
  * MCLBM_ERR_ARG for a NULL network or enable not 0 or 1. */
 int mclbm_unet_set_shared_taps(mclbm_unet *u, int enable);

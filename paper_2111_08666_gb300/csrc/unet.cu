@@ -763,7 +763,8 @@ __global__ void __launch_bounds__(ROW_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient on the tensor cores, for widths that are multiples of 128:
+// Weight gradient on the tensor cores, per tap (widths that are multiples of
+// 128 with the shared-tap kernel below switched off; it cross-checks that one):
 //   dW[co][tap][ci] = sum_p dZ[p][co] X[p + d_tap][ci]
 // a GEMM per tap with M = co (a tile of 128, rows past co zero), N = 32
 // input channels, K = pixels.  Both operands stay pixel-major as the forward
@@ -1022,7 +1023,7 @@ constexpr int WT_B_BYTES = 9216;   // X row y, 130 pixels x 64 bytes (8320), rou
 constexpr int WT_U_BYTES = 5120;   // one coarse row, 66 pixels x 64 bytes (4224), rounded up
 constexpr int WT_MAX_STAGES = 8;
 constexpr int WT_BAR_BYTES = 256;  // 3 x 8 + 2 barriers, the tensor-memory slot and the stop flag
-constexpr int WT_MAX_CO = 128;     // wider layers keep the per-tap kernel
+constexpr int WT_MAX_CO = 256;     // the widest layer of the networks built here
 constexpr int WT_PRODUCERS = 5;    // warps issuing the tensor copies: 0 and 6-9
 static_assert(WT_PRODUCERS >= 1 && WT_PRODUCERS <= 5, "producer warps 0 and 6-9");
 constexpr int WT_PART = 32 * 9 * 32;  // one CTA's partial sums: [co][tap][ci]
@@ -1826,7 +1827,7 @@ struct mclbm_unet {
     double *loss_part = nullptr, *loss_stat = nullptr;
     int *err = nullptr;  // device: set by a tensor-core kernel whose bounded wait gave up
     int max_ctas = 0;    // bound on the row-tile kernels' CTAs (0: one wave)
-    int shared_taps = 1;  // weight gradients of <= 128 output channels on the shared-tap kernel
+    int shared_taps = 1;  // weight gradients on the shared-tap kernel (else the per-tap one)
     float *wg_part = nullptr;  // the shared-tap kernel's per-CTA partial sums
     int wg_part_ctas = 0;
     std::vector<void *> allocs;

@@ -57,12 +57,12 @@ def test_forward_matches_reference(levels, b, h, w, max_ctas):
     net.close()
 
 
-# at width 512 the weight gradients of levels 0-2 (32, 64 and 128 output
-# channels) take the shared-tap kernel.  Its CTAs walk runs of row tiles down
-# 128-pixel strips with the dZ rows in a ring: 24 rows with max_ctas 3 make
-# runs long enough to wrap the ring and cross strips and images (the rows
-# above and below a tile come from its own image); four levels at width 1024
-# add the 256-channel level, which keeps the per-tap kernel
+# widths that are multiples of 128 take the shared-tap weight-gradient
+# kernel at every level (32 to 256 output channels, in 32-channel slices).
+# Its CTAs walk runs of row tiles down 128-pixel strips with the dZ rows in a
+# ring: 24 rows with max_ctas 3 make runs long enough to wrap the ring and
+# cross strips and images (the rows above and below a tile come from its own
+# image); four levels at width 1024 add the 256-channel level
 @pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 32, 32, 0), (3, 1, 8, 512, 0), (3, 1, 8, 512, 3),
                                                    (3, 2, 24, 512, 0), (3, 2, 24, 512, 3), (4, 1, 8, 1024, 0)])
 def test_gradient_matches_reference(levels, b, h, w, max_ctas):
@@ -93,9 +93,10 @@ def test_gradient_matches_reference(levels, b, h, w, max_ctas):
 # agree to FP32 rounding (a wrong dZ row in some ring windows would show as
 # a gross difference in the affected taps, which the oracle comparison above,
 # loose enough for BF16 error propagation, could let through)
-@pytest.mark.parametrize("b,h,w,max_ctas", [(2, 24, 512, 3), (2, 24, 512, 0), (1, 40, 256, 1)])
-def test_shared_tap_wgrad_matches_per_tap(b, h, w, max_ctas):
-    levels, base = 3, 32
+@pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 24, 512, 3), (3, 2, 24, 512, 0), (3, 1, 40, 256, 1),
+                                                   (4, 1, 16, 1024, 0)])
+def test_shared_tap_wgrad_matches_per_tap(levels, b, h, w, max_ctas):
+    base = 32
     theta, x4, target, mask = _problem(levels, base, b, h, w, seed=11)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
     mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
