@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -2530,7 +2531,12 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     A((void **)&u->loss_part, LOSS_BLOCKS * 2 * sizeof(double));
     A((void **)&u->loss_stat, 2 * sizeof(double));
     A((void **)&u->err, sizeof(int));
+    // the shared-tap kernel's partial sums: one block per CTA, and a launch
+    // has at least one CTA per (32-channel slice, 32-channel chunk) pair
     u->wg_part_ctas = sm_count();
+    for (const auto &L : u->layers)
+        if (L.k == 3 && L.co % 32 == 0 && L.co <= WT_MAX_CO)
+            u->wg_part_ctas = std::max(u->wg_part_ctas, (L.co / 32) * (L.cpad / 32));
     A((void **)&u->wg_part, (size_t)u->wg_part_ctas * WT_PART * sizeof(float));
     if (rc == MCLBM_OK) {
         cudaError_t e = cudaMemsetAsync(u->theta, 0, u->nparam * 4, u->stream);

@@ -62,11 +62,14 @@ def test_forward_matches_reference(levels, b, h, w, max_ctas):
 # Its CTAs walk runs of row tiles down 128-pixel strips with the dZ rows in a
 # ring: 24 rows with max_ctas 3 make runs long enough to wrap the ring and
 # cross strips and images (the rows above and below a tile come from its own
-# image); four levels at width 1024 add the 256-channel level
-@pytest.mark.parametrize("levels,b,h,w,max_ctas", [(3, 2, 32, 32, 0), (3, 1, 8, 512, 0), (3, 1, 8, 512, 3),
-                                                   (3, 2, 24, 512, 0), (3, 2, 24, 512, 3), (4, 1, 8, 1024, 0)])
-def test_gradient_matches_reference(levels, b, h, w, max_ctas):
-    base = 32
+# image); four levels at width 1024 add the 256-channel level; base 64 makes
+# a decoder with more (slice, chunk) pairs (8 x 24) than the GPU has SMs, and
+# a 512-channel level on the per-tap kernel
+@pytest.mark.parametrize("levels,b,h,w,max_ctas,base", [(3, 2, 32, 32, 0, 32), (3, 1, 8, 512, 0, 32),
+                                                        (3, 1, 8, 512, 3, 32), (3, 2, 24, 512, 0, 32),
+                                                        (3, 2, 24, 512, 3, 32), (4, 1, 8, 1024, 0, 32),
+                                                        (4, 1, 8, 1024, 0, 64)])
+def test_gradient_matches_reference(levels, b, h, w, max_ctas, base):
     theta, x4, target, mask = _problem(levels, base, b, h, w, seed=7)
     net = mclbm.UNet(levels, base, max_batch=b, max_h=h, max_w=w)
     mclbm.mclbm_unet_set_max_ctas(net.h, max_ctas)
