@@ -362,7 +362,11 @@ typedef struct mclbm_unet mclbm_unet;
 
 /* Network for batches up to max_batch of images up to max_h x max_w,
  * parameters zero until mclbm_unet_set_params.  cuda_stream NULL: own
- * stream. */
+ * stream.  Errors: MCLBM_ERR_ARG for levels outside 1..6, base not 32 or
+ * 64 (or base 2^(levels-1) above 1024), sizes that are not positive
+ * multiples of 2^(levels-1), or max_batch x max_h x max_w of 2^31 pixels or
+ * more (pixel indices are 32-bit); MCLBM_ERR_NOMEM / MCLBM_ERR_CUDA when
+ * the allocation fails. */
 int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w, void *cuda_stream,
                       mclbm_unet **out);
 int mclbm_unet_destroy(mclbm_unet *u);

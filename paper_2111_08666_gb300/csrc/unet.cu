@@ -2443,6 +2443,8 @@ int mclbm_unet_create(int levels, int base, int max_batch, int max_h, int max_w,
     const int q = 1 << (levels - 1);
     if (max_batch < 1 || max_h < q || max_w < q || max_h % q || max_w % q)
         return fail(MCLBM_ERR_ARG, "maximum sizes must be positive multiples of 2^(levels-1)");
+    if ((long long)max_batch * max_h * max_w > 0x7fffffffLL)
+        return fail(MCLBM_ERR_ARG, "at most 2^31 - 1 pixels per batch (32-bit pixel indices)");
     mclbm_unet *u = new (std::nothrow) mclbm_unet;
     if (!u) return fail(MCLBM_ERR_NOMEM, "host allocation failed");
     u->levels = levels;

@@ -58,7 +58,7 @@ def test_unet_rejects_bad_shapes_without_a_device():
     lib = mclbm.load()
     h = C.c_void_p()
     for levels, base, b, hh, ww in [(0, 32, 1, 64, 64), (4, 16, 1, 64, 64), (4, 32, 0, 64, 64),
-                                    (4, 32, 1, 60, 64), (7, 32, 1, 256, 256)]:
+                                    (4, 32, 1, 60, 64), (7, 32, 1, 256, 256), (4, 32, 1024, 2048, 1024)]:
         rc = lib.mclbm_unet_create(levels, base, b, hh, ww, None, C.byref(h))
         assert rc == mclbm.MCLBM_ERR_ARG
         assert h.value is None
