@@ -63,3 +63,42 @@ def test_gradient_matches_finite_differences(levels, base):
         lm = unet.loss_and_gradient(tm, x, target, mask, levels, base)[0]
         fd = (lp - lm) / (2 * eps)
         assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-8), k
+
+
+# Nearest upsampling followed by a 3x3 convolution, per output phase
+# (py, px) = (y mod 2, x mod 2): the fine taps dy of an even output row land
+# on coarse rows Y - 1 (dy = -1) and Y (dy = 0, +1); of an odd row on Y
+# (dy = -1, 0) and Y + 1 (dy = +1); likewise along x.  Each phase is then a
+# 2 x 2 convolution of the coarse input with summed weights: 4 taps instead
+# of 9 per output, and no upsampled tensor.  (A reformulation for the
+# decoders' upsampled inputs; pinned here against the textbook operations.)
+_LAND = {(0, -1): (-1,), (0, 0): (0, 1), (1, 0): (-1, 0), (1, 1): (1,)}
+_OFFS = {0: (-1, 0), 1: (0, 1)}
+
+
+def _phase_kernels(w):
+    out = {}
+    for py in (0, 1):
+        for px in (0, 1):
+            out[(py, px)] = {(a, c): sum(w[:, dy + 1, dx + 1, :] for dy in _LAND[(py, a)] for dx in _LAND[(px, c)])
+                             for a in _OFFS[py] for c in _OFFS[px]}
+    return out
+
+
+def test_upsample_then_convolve_is_four_coarse_2x2_convolutions():
+    rng = np.random.default_rng(5)
+    bsz, h, wd, ci, co = 2, 5, 7, 3, 4
+    x = rng.normal(size=(bsz, h, wd, ci))
+    w = rng.normal(size=(co, 3, 3, ci))
+    b = rng.normal(size=co)
+    want = unet.conv3(unet.up2(x), w, b)
+    xp = np.pad(x, ((0, 0), (1, 1), (1, 1), (0, 0)))
+    got = np.zeros_like(want)
+    for (py, px), kern in _phase_kernels(w).items():
+        # each phase's four kernels split the nine taps between them
+        assert np.allclose(sum(kern.values()), w.sum(axis=(1, 2)))
+        acc = np.zeros((bsz, h, wd, co))
+        for (a, c), k in kern.items():
+            acc += xp[:, 1 + a:1 + a + h, 1 + c:1 + c + wd, :] @ k.T
+        got[:, py::2, px::2, :] = acc + b
+    assert np.max(np.abs(got - want)) < 1e-12
