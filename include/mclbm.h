@@ -334,7 +334,7 @@ int mclbm_save(mclbm_lattice *lat, const char *path);
 int mclbm_load(mclbm_lattice *lat, const char *path);
 
 /* ------------------------------------------------------------------------
- * Learned warm start (spec extension of the quasi-static protocol of
+ * Learned warm start (an extension of the quasi-static protocol of
  * Sec. 4.2): a U-Net predicts the phase field of the next equilibrium.
  *
  * Network: levels L, base channels C0 (multiple of 32, at most 64),
