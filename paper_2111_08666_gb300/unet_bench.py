@@ -39,9 +39,13 @@ def main(argv=None) -> None:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--per-tap", action="store_true",
+                    help="weight gradients on the per-tap kernel instead of the shared-tap one")
     a = ap.parse_args(argv)
     b, h, w = a.batch, a.height, a.width
     net = mclbm.UNet(a.levels, a.base, max_batch=b, max_h=h, max_w=w)
+    if a.per_tap:
+        mclbm.mclbm_unet_set_shared_taps(net.h, 0)
     net.set_params(warmstart.init_params(a.levels, a.base, 0))
     rng = np.random.default_rng(0)
     x = torch.from_numpy(rng.normal(0, 1, (b, h, w, 4)).astype(np.float32)).cuda()
@@ -62,7 +66,8 @@ def main(argv=None) -> None:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / a.reps  # ms (the calls synchronise the network's stream)
 
-    out = dict(levels=a.levels, base=a.base, batch=b, height=h, width=w, forward_gflop=fl / 1e9)
+    out = dict(levels=a.levels, base=a.base, batch=b, height=h, width=w, forward_gflop=fl / 1e9,
+               wgrad="per-tap" if a.per_tap else "shared-tap")
     ms = timed(lambda: mclbm.mclbm_unet_infer(net.h, b, h, w, x, phi))
     out.update(infer_ms=ms, infer_tflops=fl / (ms * 1e-3) / 1e12)
     if not a.no_train:
