@@ -251,17 +251,20 @@ int mclbm_info(mclbm_lattice *lat, int64_t out[6]);
  *   f      [2][9][ny][nx] FP64 populations in device memory (the layout of
  *          mclbm_get_populations), owned by the caller
  *   solid  [ny][nx] uint8 in device memory, 1 = solid, owned by the caller
- *   g_coh  cohesion strength used in the boundary pressures (Eq. 14)
+ *   g_coh  the cohesion strength that enters the boundary pressures, as in
+ *          mclbm_diagnostics
  *   periodic_y  1 if rows wrap (affects which boundary nodes count as near
  *          a wall for P_in/P_out)
  *   out    [8] results as in mclbm_diagnostics, device or host memory
  *   cuda_stream  stream to run on (NULL: the legacy default stream)
  * The per-block partial sums live in a fixed array in the library's device
- * globals (74 KB per device, held until the process exits), which bounds the
+ * globals (64 KB per device, held until the process exits), which bounds the
  * lattice to at most 4194304 nodes; larger lattices are rejected with
- * MCLBM_ERR_ARG.  Allocates nothing.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress), so it should come
- * before any stream capture.  All calls share the array: calls that overlap
+ * MCLBM_ERR_ARG.  The caller guarantees the buffer sizes: f holds at least
+ * 18 * nx * ny doubles, solid nx * ny bytes and out 8 doubles (the library
+ * cannot check the extent of a raw pointer).  Allocates nothing.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so it should come before any stream capture.  All calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller.  With a device
  * output the call is asynchronous; with a host output it synchronises the
  * stream.

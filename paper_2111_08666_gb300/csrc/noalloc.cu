@@ -13,7 +13,7 @@
 // The array has room for NOALLOC_BLOCKS blocks of partial sums; each block
 // reduces NOALLOC_NODES_PER_BLOCK nodes, so lattices of up to
 // NOALLOC_MAX_NODES nodes are accepted and larger ones are rejected.  Every
-// device that loads the library holds the array (74 KB) until the process
+// device that loads the library holds the array (64 KB) until the process
 // exits.  All calls share it: calls that overlap on the GPU (on different
 // streams, or from different threads) race on it and must be serialised by
 // the caller.  Every call rewrites every partial it reads, so nothing left
@@ -33,7 +33,7 @@ constexpr int NOALLOC_NODES_PER_THREAD = 16;
 constexpr int NOALLOC_NODES_PER_BLOCK = NOALLOC_THREADS * NOALLOC_NODES_PER_THREAD;
 constexpr int NOALLOC_BLOCKS = 1024;
 constexpr long long NOALLOC_MAX_NODES = (long long)NOALLOC_BLOCKS * NOALLOC_NODES_PER_BLOCK;
-constexpr int NOALLOC_ACC = 9;
+constexpr int NOALLOC_ACC = 8;
 constexpr int NOALLOC_MAX_DEVICES = 64;
 
 // per-block partial sums, then the 8 results
@@ -54,7 +54,8 @@ __device__ __forceinline__ double noalloc_warp_sum(double v) {
 // Pass 1: block b reduces nodes [b * NODES_PER_BLOCK, (b+1) * NODES_PER_BLOCK).
 //   acc[0] mass1  acc[1] mass2  acc[2] fluid nodes  acc[3] water nodes
 //   acc[4] P_in sum  acc[5] P_in count  acc[6] P_out sum  acc[7] P_out count
-//   acc[8] nodes with a non-finite or negative density
+// (A non-finite density shows in the results themselves: the masses and
+// saturations it enters become NaN or infinite.)
 __global__ void __launch_bounds__(NOALLOC_THREADS)
     noalloc_partial_kernel(const double *f, const uint8_t *solid, int nx, int ny, double g_coh,
                            int periodic_y, double *scratch) {
@@ -78,7 +79,6 @@ __global__ void __launch_bounds__(NOALLOC_THREADS)
         acc[1] += r2;
         acc[2] += 1.0;
         acc[3] += (r2 > r1) ? 1.0 : 0.0;
-        if (!(r1 >= 0.0) || !(r2 >= 0.0) || !isfinite(r1) || !isfinite(r2)) acc[8] += 1.0;
         if (x == 0 || x == nx - 1) {
             // boundary pressure away from walls: no solid within 2 rows
             bool site = true;

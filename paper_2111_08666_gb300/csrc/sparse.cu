@@ -551,6 +551,14 @@ int sparse_prepare(Lattice &L, int STY) {
         const int x0 = (t % tiles_x) * STX, y0 = (t / tiles_x) * STY;
         std::vector<uint32_t> own, ring, sol;
         std::vector<uint16_t> smap((size_t)SFW * SFH, 0);
+        // Only what the tile's own nodes read is computed: the densities or
+        // virtual solid densities of their 8 neighbours (forces, Eqs. 12-15;
+        // the open-end mirror reads the opposite neighbour, also one of the
+        // 8), the fluid neighbours of those solid neighbours (Eq. 17), and
+        // the populations those densities pull.  Positions of the density
+        // frame: own (1), neighbour of an own node (2), density needed (4).
+        std::vector<uint8_t> mark((size_t)SN1, 0);
+        auto dpos = [&](int x, int y) { return (y - y0 + 2) * SDXW + (x - x0 + 2); };
         for (size_t i = 0; i < blk[t].size(); ++i) {
             const int n = blk[t][i];
             if (n < 0) continue;
@@ -558,36 +566,61 @@ int sparse_prepare(Lattice &L, int STY) {
             own.push_back((uint32_t)(x - x0) | (uint32_t)(y - y0) << 6 | (~fluid_mask(x, y) & 0xffu) << 12 |
                           set3(x) | (uint32_t)i << 22);
             smap[(size_t)(y - y0 + 3) * SFW + (x - x0 + 3)] = (uint16_t)(i * planes);
+            mark[(size_t)dpos(x, y)] |= 1;
+            for (int d = 1; d < 9; ++d) mark[(size_t)dpos(x + ex(d), y + ey(d))] |= 2;
         }
         for (int k = 0; k < SN1; ++k) {
             const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
-            const bool in_tile = dr >= 2 && dr < STY + 2 && dc >= 2 && dc < STX + 2 && x < nx && y < ny;
-            if (!in_tile && code_at(x, y) == GEO_FLUID)
-                ring.push_back((uint32_t)k | (~fluid_mask(x, y) & 0xffu) << 12 | set3(x));
-        }
-        for (int k = 0; k < SN1; ++k) {
-            const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
-            if (dr < 1 || dr > STY + 2 || dc < 1 || dc > STX + 2) continue;
+            if (!(mark[k] & 2)) continue;
             const int c = code_at(x, y);
-            if (c != GEO_FLUID) sol.push_back((uint32_t)k | (uint32_t)c << 12 | fluid_mask(x, y) << 20);
+            if (c == GEO_FLUID) {
+                mark[k] |= 4;
+                continue;
+            }
+            const uint32_t fm = fluid_mask(x, y);
+            sol.push_back((uint32_t)k | (uint32_t)c << 12 | fm << 20);
+            if (c == GEO_OUTSIDE) continue;  // zero: its neighbours are not read
+            for (int d = 1; d < 9; ++d)
+                if ((fm >> (d - 1)) & 1u) mark[(size_t)(k + ey(d) * SDXW + ex(d))] |= 4;
         }
-        // ring nodes to stage: fluid positions of the staged frame outside the tile
+        // the ring's densities, and the staged frame positions they and the
+        // own nodes pull from (fluid sources outside the tile's own block)
+        std::vector<uint8_t> pulled((size_t)SFW * SFH, 0);
+        auto mark_sources = [&](int x, int y) {
+            for (int d = 1; d < 9; ++d) {
+                const int sx = x - ex(d), sy = y - ey(d);
+                if (code_at(sx, sy) == GEO_FLUID) pulled[(size_t)(sy - y0 + 3) * SFW + (sx - x0 + 3)] = 1;
+            }
+        };
+        for (int k = 0; k < SN1; ++k) {
+            const int dr = k / SDXW, dc = k % SDXW, x = x0 - 2 + dc, y = y0 - 2 + dr;
+            if (mark[k] & 1) {
+                mark_sources(x, y);
+                continue;
+            }
+            if (!(mark[k] & 4)) continue;
+            ring.push_back((uint32_t)k | (~fluid_mask(x, y) & 0xffu) << 12 | set3(x));
+            mark_sources(x, y);
+        }
+        // ring nodes to stage: pulled fluid positions outside the own block
         std::vector<std::pair<int, int>> need;  // (slot, frame position)
         for (int r = 0; r < SFH; ++r)
             for (int c = 0; c < SFW; ++c) {
                 const int x = x0 - 3 + c, y = y0 - 3 + r;
                 const bool in_tile = x >= x0 && x < x0 + STX && y >= y0 && y < y0 + STY && x < nx && y < ny;
-                if (in_tile || code_at(x, y) != GEO_FLUID) continue;
+                if (in_tile || !pulled[(size_t)r * SFW + c]) continue;
                 const int gsl = src_of(x, y);
                 if (gsl < 0) return fail(MCLBM_ERR_STATE, "fluid-only layout: ring node without a slot");
                 need.push_back({gsl, r * SFW + c});
             }
         std::sort(need.begin(), need.end());
-        // ranges: the own block first, then runs of the ring's slots
+        // ranges: the own block first, then runs of the ring's slots.  Runs
+        // closer than `gap` slots are merged (the slots between are copied
+        // too); the gap grows until the record holds the tile's ranges.
         const long long own_len = (long long)blk[t].size();
         uint32_t *R = &recs[(size_t)t * REC_WORDS];
         int nr = 0;
-        long long bytes = 0;
+        long long bytes = 0, cursor = 0;
         auto add_range = [&](long long src, long long len, long long dst) {
             if (nr >= MAXR) return false;
             R[4 + 3 * nr] = (uint32_t)src;
@@ -597,23 +630,28 @@ int sparse_prepare(Lattice &L, int STY) {
             bytes += len * planes * (long long)L.store_bytes;
             return true;
         };
-        bool ok = own_len == 0 || add_range(start[t], own_len, 0);
-        long long cursor = own_len;
-        size_t i = 0;
-        while (ok && i < need.size()) {
-            const long long a = need[i].first / Q * Q;
-            size_t j = i;
-            while (j + 1 < need.size() && need[j + 1].first - need[j].first <= Q) ++j;
-            const long long b = (need[j].first / Q + 1) * Q;  // exclusive, 16-byte multiple
-            if (b > nfp || cursor + (b - a) > scap) {
-                ok = false;
-                break;
+        bool ok = false;
+        for (long long gap = Q; !ok && gap <= 4 * (long long)nfp; gap *= 2) {
+            nr = 0;
+            bytes = 0;
+            ok = own_len == 0 || add_range(start[t], own_len, 0);
+            cursor = own_len;
+            size_t i = 0;
+            while (ok && i < need.size()) {
+                const long long a = need[i].first / Q * Q;
+                size_t j = i;
+                while (j + 1 < need.size() && need[j + 1].first - need[j].first <= gap) ++j;
+                const long long b = (need[j].first / Q + 1) * Q;  // exclusive, 16-byte multiple
+                if (b > nfp || cursor + (b - a) > scap) {
+                    ok = false;
+                    break;
+                }
+                for (size_t k = i; k <= j; ++k)
+                    smap[(size_t)need[k].second] = (uint16_t)((cursor + need[k].first - a) * planes);
+                ok = add_range(a, b - a, cursor);
+                cursor += b - a;
+                i = j + 1;
             }
-            for (size_t k = i; k <= j; ++k)
-                smap[(size_t)need[k].second] = (uint16_t)((cursor + need[k].first - a) * planes);
-            ok = add_range(a, b - a, cursor);
-            cursor += b - a;
-            i = j + 1;
         }
         const long long words = HDR + (long long)own.size() + ring.size() + sol.size() + (smap.size() + 1) / 2;
         if (!ok || words > tabcap || own.size() > (size_t)STX * STY || cursor * planes > 65535)

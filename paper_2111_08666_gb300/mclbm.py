@@ -307,7 +307,14 @@ def mclbm_diagnostics_noalloc(f, solid, nx: int, ny: int, g_coh: float, periodic
                               out, stream=None) -> None:
     """Diagnostics of caller-owned device populations [2][9][ny][nx] and
     solid mask [ny][nx], without any allocation (see include/mclbm.h); out
-    is a [8] float64 buffer on the device or the host."""
+    is a [8] float64 buffer on the device or the host.  The buffer sizes are
+    checked here: the library reads 18 * nx * ny doubles of f and nx * ny
+    bytes of solid through raw pointers and cannot check them itself."""
+    n = int(nx) * int(ny)
+    for buf, need, name in ((f, 18 * n, "f"), (solid, n, "solid"), (out, 8, "out")):
+        have = buf.size if isinstance(buf, np.ndarray) else buf.numel()
+        if have < need:
+            raise ValueError(f"{name} holds {have} elements, needs at least {need}")
     _check(load().mclbm_diagnostics_noalloc(_addr(f, np.float64), _addr(solid, np.uint8),
                                             int(nx), int(ny), float(g_coh), int(periodic_y),
                                             _addr(out, np.float64), _stream_handle(stream)))

@@ -71,3 +71,15 @@ def test_unet_switches_reject_bad_arguments_without_a_device():
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_unet_set_shared_taps(None, 0)
     assert e.value.code == mclbm.MCLBM_ERR_ARG
+
+
+def test_noalloc_binding_rejects_short_buffers_before_the_library():
+    import numpy as np
+    nx, ny = 16, 8
+    f = np.zeros(18 * nx * ny, dtype=np.float64)
+    solid = np.zeros(nx * ny, dtype=np.uint8)
+    out = np.zeros(8, dtype=np.float64)
+    for args, name in (((f[:-1], solid, out), "f"), ((f, solid[:-1], out), "solid"),
+                       ((f, solid, out[:7]), "out")):
+        with pytest.raises(ValueError, match=name):
+            mclbm.mclbm_diagnostics_noalloc(args[0], args[1], nx, ny, 3.5, False, args[2])
