@@ -83,12 +83,16 @@ def workload(nx=2048, ny=1024, seed=99):
     return c
 
 
-def algorithmic_bytes(c, store_bytes: int) -> float:
-    """Per launch: each fluid node reads and writes its 2 x 9 populations
-    once; every node's 1-byte geometry code is read once."""
+PLANES = {"fp64": 18, "fp32": 18, "fp32dev": 20, "fp16dev": 20, "bf16dev": 20}
+
+
+def algorithmic_bytes(c, store_bytes: int, planes: int = 18) -> float:
+    """Per launch: each fluid node reads and writes its stored values once
+    (2 x 9 populations, plus the two reference densities of the deviation
+    storages); every node's 1-byte geometry code is read once."""
     n_fluid = int((c["solid"] == 0).sum())
     n_all = c["nx"] * c["ny"]
-    return 2 * 9 * 2 * store_bytes * n_fluid + n_all
+    return 2 * planes * store_bytes * n_fluid + n_all
 
 
 def measured_peaks() -> tuple[float, str]:
@@ -199,7 +203,7 @@ def run_gpu(args, rank, world):
     units, job_sec = replicas.aggregate(n_all * args.steps, sec)
     value = units / job_sec / 1e6
     per_launch = sec / args.steps
-    abytes = algorithmic_bytes(c, mclbm.STORE_BYTES[prec])
+    abytes = algorithmic_bytes(c, mclbm.STORE_BYTES[prec], PLANES[args.prec])
     peak, peak_kind = measured_peaks()
     achieved = abytes / per_launch / 1e9
     traffic = None
@@ -247,7 +251,10 @@ def run_gpu(args, rank, world):
 
     batched = None
     if args.batch_steps > 0:
-        batched = batched_section(args, stream)
+        batched = batched_section(args, stream, peak)
+    storages = None
+    if args.prec == "fp32" and args.storage_steps > 0:
+        storages = storage_section(args, stream, c, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -280,6 +287,7 @@ def run_gpu(args, rank, world):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "batched": batched,
+        "storages": storages,
         "diag": {k: (None if isinstance(v, float) and math.isnan(v) else v)
                  for k, v in diag.items()},
     }
@@ -288,14 +296,47 @@ def run_gpu(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
-def batched_section(args, stream) -> dict:
+def storage_section(args, stream, c, peak) -> dict:
+    """The same workload in the 16-bit deviation storages (FP16 and BF16
+    values, FP32 arithmetic): MLUPS and the fraction of the HBM roofline on
+    their own algorithmic bytes (20 stored values of 2 bytes per fluid node,
+    read and written, plus the geometry byte)."""
+    import torch
+    from paper_2111_08666_gb300 import mclbm
+    out = {}
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name in ("fp16dev", "bf16dev"):
+        p = mclbm.PRECISIONS[name]
+        lat = mclbm.Lattice(c["solid"], c["xi"], prec=p, nu1=c["nu1"], nu2=c["nu2"],
+                            rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream)
+        lat.init(c["rho1"], c["rho2"])
+        lat.step(20)
+        lat.sync()
+        start.record(stream)
+        lat.step(args.storage_steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        sec = start.elapsed_time(end) / 1e3 / args.storage_steps
+        ab = algorithmic_bytes(c, mclbm.STORE_BYTES[p], PLANES[name])
+        out[name] = {"mlups": round(c["nx"] * c["ny"] / sec / 1e6, 1), "launch_us": round(sec * 1e6, 3),
+                     "algorithmic_bytes_per_launch": ab,
+                     "achieved_gbs": round(ab / sec / 1e9, 1), "frac": round(ab / sec / 1e9 / peak, 4),
+                     "steps": args.storage_steps}
+        lat.close()
+    return out
+
+
+def batched_section(args, stream, peak) -> dict:
     """24 uneven cases (256x256 .. 1024x512, seeds 10..33, theta 30..150 deg,
     M = 1, 10, 50), FP32: one persistent launch per step under a CUDA graph
-    with the autotuned tile, against the same cases stepped one at a time."""
+    with the autotuned tile, against the same cases stepped one at a time.
+    The roofline fraction counts the algorithmic bytes of all cases (144 B
+    per fluid node and 1 B per node) per batched step."""
     import torch
     from paper_2111_08666_gb300 import mclbm
     cases = [media.config_batch(k) for k in range(24)]
     nodes = sum(c["nx"] * c["ny"] for c in cases)
+    abytes = sum(algorithmic_bytes(c, 4) for c in cases)
     k_steps = args.batch_steps
     b = mclbm.mclbm_batch_create(cases, mclbm.MCLBM_FP32, stream)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -339,6 +380,8 @@ def batched_section(args, stream) -> dict:
                         "M=1/10/50, FP32, drainage rho_in=1.005",
             "nodes": nodes, "steps": k_steps,
             "mlups_batched": round(nodes * k_steps / t_batch / 1e6, 1),
+            "algorithmic_bytes_per_step": abytes,
+            "frac": round(abytes / (t_batch / k_steps) / 1e9 / peak, 4),
             "mlups_one_at_a_time": round(nodes * k_steps / t_seq / 1e6, 1),
             "mlups_one_at_a_time_fluid_only": round(nodes * k_steps / t_fluid / 1e6, 1),
             "launches": int(launches),
@@ -421,6 +464,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-steps", type=int, default=400,
                     help="steps of the 24-case batched section (0: skip it)")
+    ap.add_argument("--storage-steps", type=int, default=2000,
+                    help="steps of each 16-bit deviation storage's timing (0: skip it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, world, _ = replicas.rank_info()

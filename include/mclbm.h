@@ -84,7 +84,17 @@ typedef enum {
     MCLBM_FLAG_KERNEL = 3,
     /* Tile of kernel 3: 0 (default) 32 x 16 nodes (32 x 12 for FP32_DEV),
      * two CTAs per SM; 1: 32 x 8 nodes, three CTAs per SM.  Same results. */
-    MCLBM_FLAG_TILE_SHAPE = 4
+    MCLBM_FLAG_TILE_SHAPE = 4,
+    /* Limit, in microseconds (1..10^7, default 10^6), of every wait of the
+     * staging kernels (2, 3 and 4) for their asynchronous copies.  A wait
+     * that runs out ends the launch and the next synchronising call returns
+     * MCLBM_ERR_TIMEOUT; the lattice state is then not valid until it is
+     * initialised again. */
+    MCLBM_FLAG_WAIT_LIMIT_US = 5,
+    /* Test hook, 0 by default: 1 makes kernel 4 issue no staging copies, so
+     * that its first wait runs out and the step reports MCLBM_ERR_TIMEOUT.
+     * It exercises the bounded-wait error path without a GPU fault. */
+    MCLBM_FLAG_TEST_NO_COPY = 6
 } mclbm_flag;
 
 typedef struct mclbm_lattice mclbm_lattice;
@@ -410,6 +420,21 @@ int mclbm_unet_train_step(mclbm_unet *u, int batch, int h, int w, const float *x
  * phases at G = 3.5, Sec. 3.1), phi clamped to [-1, 1]; then as
  * mclbm_init_densities. */
 int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi);
+
+/*
+ * Warm start in place (a quasi-static step of Sec. 4.2 started from a
+ * predicted equilibrium): at every fluid node whose predicted phase field
+ * phi_hat is on the other side of zero from the node's own phase (component
+ * 1's side is rho1 > rho2) and |phi_hat| > flip, the populations are reset
+ * to rest with the separated-phase densities of phi_hat, as in
+ * mclbm_init_from_phase; every other node keeps its populations, and the
+ * inlet/outlet records of Eqs. 26-27 are kept.
+ *   phi_hat  [ny][nx] float, host or device, owned by the caller
+ *   flip     in [0, 1)
+ *   changed  receives the number of nodes reset (may be NULL)
+ * The lattice must be initialised.  Synchronises the lattice's stream.
+ */
+int mclbm_blend_phase(mclbm_lattice *lat, const float *phi_hat, double flip, int64_t *changed);
 
 /* Kernel launches enqueued by this library since it was loaded (all
  * lattices); used to count the GPU work inside a timed region. */

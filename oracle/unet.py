@@ -20,6 +20,18 @@ Parameters, flat and in this order, each conv as weights [Co][3][3][Ci]
 (1x1 for the head: [1][C0]) followed by its bias [Co]: enc0a, enc0b, ...,
 enc(L-1)a, enc(L-1)b, dec(L-2)a, dec(L-2)b, ..., dec0a, dec0b, head.
 Tensors are NHWC.
+
+Storage model (optional).  The network is defined with BF16 storage: its
+input, its 3x3 weights and every activation it keeps (each conv output
+after ReLU, each pooled map) are bfloat16 values, and so is, in the
+backward pass, every gradient at a conv's pre-activation (after the ReLU
+mask), from which that conv's weight and input gradients are formed;
+biases, the head and all sums are wider.  ``forward(..., store=bf16_round)`` together with
+``store_weights`` evaluates exactly that network in FP64: the values are
+rounded where the storage format rounds them, so that the ReLU masks (a
+discrete outcome that a 2^-9 perturbation can flip) are decided on the same
+values as in a BF16 implementation.  With ``store=None`` every function is
+the plain FP64 network.
 """
 from __future__ import annotations
 
@@ -65,6 +77,29 @@ def pack(grads: dict, levels: int, base: int) -> np.ndarray:
     return np.concatenate(parts)
 
 
+def bf16_round(a):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even),
+    returned as float64.  Values are first rounded to float32, the type a
+    BF16 implementation converts from."""
+    u = np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32)).view(np.uint32)
+    u = u.astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def store_weights(theta, levels: int, base: int, rnd=bf16_round) -> np.ndarray:
+    """The parameter vector with every 3x3 weight rounded by ``rnd``; the
+    biases and the head (1x1) are kept."""
+    out = np.array(theta, np.float64, copy=True)
+    o = 0
+    for name, co, ci, k in layer_shapes(levels, base):
+        n = co * k * k * ci
+        if k == 3:
+            out[o:o + n] = rnd(out[o:o + n])
+        o += n + co
+    return out
+
+
 def conv3(x, w, b):
     """3x3 convolution, zero padding 1: y[p] = sum_{dy,dx} x[p+d] W[:,dy,dx,:]^T + b."""
     bsz, h, wd, _ = x.shape
@@ -108,28 +143,30 @@ def up2_backward(dy):
     return dy.reshape(b, h // 2, 2, w // 2, 2, c).sum(axis=(2, 4))
 
 
-def forward(theta, x, levels: int, base: int):
-    """Returns phi_hat [B][H][W] and the cache for backward."""
+def forward(theta, x, levels: int, base: int, store=None):
+    """Returns phi_hat [B][H][W] and the cache for backward.  ``store`` (see
+    the storage model above) rounds the input and every kept activation."""
+    keep = store if store is not None else (lambda a: a)
     p = unpack(theta, levels, base)
     cache = {}
-    e, h = [], x
+    e, h = [], keep(x)
     for l in range(levels):
         if l > 0:
-            h = pool2(e[-1])
+            h = keep(pool2(e[-1]))
         a_in = h
         za = conv3(a_in, *p[f"enc{l}a"])
-        ha = np.maximum(za, 0.0)
+        ha = keep(np.maximum(za, 0.0))
         zb = conv3(ha, *p[f"enc{l}b"])
-        hb = np.maximum(zb, 0.0)
+        hb = keep(np.maximum(zb, 0.0))
         cache[f"enc{l}"] = (a_in, za, ha, zb)
         e.append(hb)
     d = e[-1]
     for l in range(levels - 2, -1, -1):
         cat = np.concatenate([e[l], up2(d)], axis=3)
         za = conv3(cat, *p[f"dec{l}a"])
-        ha = np.maximum(za, 0.0)
+        ha = keep(np.maximum(za, 0.0))
         zb = conv3(ha, *p[f"dec{l}b"])
-        d = np.maximum(zb, 0.0)
+        d = keep(np.maximum(zb, 0.0))
         cache[f"dec{l}"] = (cat, za, ha, zb)
     hw, hb = p["head"]
     z = d @ hw[:, 0, 0, :].T + hb
@@ -145,7 +182,8 @@ def loss_and_grad_phi(phi, target, mask):
     return float((r * r).sum() / n), 2.0 * r / n
 
 
-def backward(theta, cache, dphi, levels: int, base: int) -> np.ndarray:
+def backward(theta, cache, dphi, levels: int, base: int, store=None) -> np.ndarray:
+    keep = store if store is not None else (lambda a: a)
     p = unpack(theta, levels, base)
     grads = {}
     d, phi = cache["head"]
@@ -157,10 +195,10 @@ def backward(theta, cache, dphi, levels: int, base: int) -> np.ndarray:
     de = [np.zeros_like(t) for t in e]
     for l in range(0, levels - 1):
         cat, za, ha, zb = cache[f"dec{l}"]
-        dzb = dd * (zb > 0)
+        dzb = keep(dd * (zb > 0))
         dha, gw, gb = conv3_backward(ha, p[f"dec{l}b"][0], dzb)
         grads[f"dec{l}b"] = (gw, gb)
-        dza = dha * (za > 0)
+        dza = keep(dha * (za > 0))
         dcat, gw, gb = conv3_backward(cat, p[f"dec{l}a"][0], dza)
         grads[f"dec{l}a"] = (gw, gb)
         c_skip = e[l].shape[3]
@@ -169,10 +207,10 @@ def backward(theta, cache, dphi, levels: int, base: int) -> np.ndarray:
     de[levels - 1] += dd
     for l in range(levels - 1, -1, -1):
         a_in, za, ha, zb = cache[f"enc{l}"]
-        dzb = de[l] * (zb > 0)
+        dzb = keep(de[l] * (zb > 0))
         dha, gw, gb = conv3_backward(ha, p[f"enc{l}b"][0], dzb)
         grads[f"enc{l}b"] = (gw, gb)
-        dza = dha * (za > 0)
+        dza = keep(dha * (za > 0))
         dx, gw, gb = conv3_backward(a_in, p[f"enc{l}a"][0], dza)
         grads[f"enc{l}a"] = (gw, gb)
         if l > 0:
@@ -180,7 +218,7 @@ def backward(theta, cache, dphi, levels: int, base: int) -> np.ndarray:
     return pack(grads, levels, base)
 
 
-def loss_and_gradient(theta, x, target, mask, levels: int, base: int):
-    phi, cache = forward(theta, x, levels, base)
+def loss_and_gradient(theta, x, target, mask, levels: int, base: int, store=None):
+    phi, cache = forward(theta, x, levels, base, store)
     loss, dphi = loss_and_grad_phi(phi, target, mask)
-    return loss, backward(theta, cache, dphi, levels, base), phi
+    return loss, backward(theta, cache, dphi, levels, base, store), phi

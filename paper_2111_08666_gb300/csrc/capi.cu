@@ -106,6 +106,7 @@ void release(Lattice *L) {
     cudaFree(L->diag_partial);
     cudaFree(L->diag_out);
     cudaFree(L->bad_flag);
+    cudaFree(L->blend_count);
     cudaFree(L->err);
     cudaFree(L->geo_pad);
     tma_release(*L);
@@ -371,6 +372,14 @@ int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
             if (value < 0) return fail(MCLBM_ERR_ARG, "diag_every must be >= 0");
             lat->diag_every = value;
             return MCLBM_OK;
+        case MCLBM_FLAG_WAIT_LIMIT_US:
+            if (value < 1 || value > 10000000)
+                return fail(MCLBM_ERR_ARG, "the wait limit must be 1..10000000 microseconds");
+            lat->wait_ns = (uint64_t)value * 1000ull;
+            return MCLBM_OK;
+        case MCLBM_FLAG_TEST_NO_COPY:
+            lat->test_no_copy = value ? 1 : 0;
+            return MCLBM_OK;
         default: return fail(MCLBM_ERR_ARG, "unknown flag " + std::to_string(flag));
     }
 }
@@ -533,6 +542,35 @@ int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi) {
     lat->pop_ghosts_stale = false;
     lat->initialised = true;
     lat->steps = 0;
+    return MCLBM_OK;
+}
+
+int mclbm_blend_phase(mclbm_lattice *lat, const float *phi_hat, double flip, int64_t *changed) {
+    if (int rc = check_lat(lat)) return rc;
+    if (!phi_hat) return fail(MCLBM_ERR_ARG, "phi_hat is NULL");
+    if (!(flip >= 0.0) || !(flip < 1.0)) return fail(MCLBM_ERR_ARG, "flip must be in [0, 1)");
+    if (int rc = make_current(*lat)) return rc;
+    if (int rc = check_ready(*lat)) return rc;
+    const size_t n = (size_t)lat->nx * lat->ny;
+    DeviceView vp;
+    if (int rc = view_in(*lat, phi_hat, n * sizeof(float), vp)) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!lat->blend_count) {
+        e = cudaMalloc((void **)&lat->blend_count, sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(blend counter)");
+    }
+    if (int rc = dense_current(*lat)) return rc;
+    e = cudaMemsetAsync(lat->blend_count, 0, sizeof(unsigned long long), lat->stream);
+    // rho_hi = 1, rho_lo = 0.027: the separated phases at G = 3.5 (Sec. 3.1)
+    if (e == cudaSuccess)
+        e = launch_blend_phase(*lat, static_cast<const float *>(vp.ptr), 1.0, 0.027, flip, lat->blend_count);
+    unsigned long long cnt = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&cnt, lat->blend_count, sizeof(cnt), cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "warm-start blend");
+    lat->sparse_state = 0;  // the dense buffers hold the state
+    if (changed) *changed = (int64_t)cnt;
     return MCLBM_OK;
 }
 

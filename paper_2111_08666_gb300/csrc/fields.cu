@@ -430,6 +430,44 @@ cudaError_t dispatch(const Lattice &L, F &&fn) {
     }
 }
 
+// Warm-start blend in place: at a fluid node whose predicted phase field
+// phi_hat lies on the other side of zero from the node's own phase
+// (rho1 > rho2 is component 1's side) and by more than `flip`, the node is
+// re-initialised at rest, f_i = w_i rho^sigma (Eq. 2 at u = 0), with the
+// separated-phase densities of phi_hat: rho1 = lo + (hi - lo)(1 + phi)/2,
+// rho2 = lo + (hi - lo)(1 - phi)/2, phi clamped to [-1, 1].  Every other
+// node keeps its populations, so the previous equilibrium survives
+// wherever no change of phase is predicted.  The number of replaced nodes
+// is added to *changed (one atomic per warp).
+template <class P>
+__global__ void blend_phase_kernel(Geometry g, Params p, typename P::store_t *f, const float *phi,
+                                   double hi, double lo, double flip, unsigned long long *changed) {
+    using R = typename P::real_t;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool change = false;
+    if (k < (long long)g.nx * g.ny) {
+        const int x = (int)(k % g.nx), y = (int)(k / g.nx);
+        if (is_fluid(g, x, y)) {
+            R r1, r2;
+            node_rho<P>(g, f, site_of(g, x, y), r1, r2);
+            const double ph = fmin(1.0, fmax(-1.0, (double)phi[k]));
+            change = ((ph > 0.0) != (r1 > r2)) && fabs(ph) > flip;
+            if (change) {
+                const R n1 = R(lo + (hi - lo) * (1.0 + ph) * 0.5), n2 = R(lo + (hi - lo) * (1.0 - ph) * 0.5);
+                R fs[2][9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    fs[0][i] = wgt<R>(i) * n1;
+                    fs[1][i] = wgt<R>(i) * n2;
+                }
+                pop_store_node<P>(g, p, f, x, y, fs, n1, n2);
+            }
+        }
+    }
+    const unsigned int votes = __ballot_sync(0xffffffffu, change);
+    if ((threadIdx.x & 31) == 0 && votes) atomicAdd(changed, (unsigned long long)__popc(votes));
+}
+
 }  // namespace
 
 int diag_blocks_for(const Lattice &L) {
@@ -455,6 +493,18 @@ cudaError_t launch_phase_densities(Lattice &L, const float *phi, double hi, doub
     phase_densities_kernel<<<blocks_for(n), BLK, 0, L.stream>>>(phi, n, hi, lo, r1, r2);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_blend_phase(Lattice &L, const float *phi, double hi, double lo, double flip,
+                               unsigned long long *changed) {
+    const Geometry g = geometry_of(L);
+    return dispatch(L, [&](auto tag) {
+        using P = decltype(tag);
+        blend_phase_kernel<P><<<blocks_for((long long)L.nx * L.ny), BLK, 0, L.stream>>>(
+            g, L.p, static_cast<typename P::store_t *>(L.f[L.cur]), phi, hi, lo, flip, changed);
+        count_launch();
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2) {

@@ -159,6 +159,8 @@ struct StepArgs {
                                // component 2's inlet f_{1,5,8} (Eq. 27), frozen at initialisation
     int *err;                  // device error word (bounded waits)
     int rows_per_cta;          // strip kernel: rows of one CTA
+    unsigned long long wait_ns = 1000000000ull;  // limit of every bounded wait of the staging kernels
+    int test_no_copy = 0;      // test hook: the fluid-only kernel issues no staging copies
 };
 
 // strip width (columns per CTA) of the row-sweeping kernel
@@ -194,7 +196,10 @@ struct Lattice {
     double *diag_out = nullptr;       // [8] device
     double *host_diag = nullptr;      // [8] pinned
     unsigned long long *bad_flag = nullptr;  // device: divergence count
+    unsigned long long *blend_count = nullptr;  // device: nodes replaced by the last blend
     int64_t diag_every = 0;
+    uint64_t wait_ns = 1000000000ull;  // bounded-wait limit of the staging kernels (1 s)
+    int test_no_copy = 0;      // MCLBM_FLAG_TEST_NO_COPY
     int64_t kernel = 0;        // 0 auto, 1 tile kernel, 2 strip kernel
     int64_t steps = 0;
     size_t device_bytes = 0;
@@ -268,6 +273,8 @@ cudaError_t launch_geo_ghosts(Lattice &L);
 cudaError_t launch_init_equilibrium(Lattice &L, const double *rho1, const double *rho2);
 cudaError_t launch_phase_densities(Lattice &L, const float *phi, double hi, double lo, double *r1,
                                    double *r2);
+cudaError_t launch_blend_phase(Lattice &L, const float *phi, double hi, double lo, double flip,
+                               unsigned long long *changed);
 cudaError_t launch_set_populations(Lattice &L, const double *f);
 cudaError_t launch_get_populations(Lattice &L, double *f);
 cudaError_t launch_diagnostics(Lattice &L);

@@ -66,16 +66,16 @@ struct SLayout {
     // of the density frame), then the staged slot of every frame position
     // (16 bits each)
     static constexpr int TABW = (HDR + SN1 + (SFW * SFH + 1) / 2 + 3) / 4 * 4;
-    static constexpr size_t stg_bytes = (size_t)SCAP * NPL * sizeof(S);  // [slot][plane]
-    static constexpr size_t out_off = (stg_bytes + 127) / 128 * 128;
-    static constexpr size_t out_bytes = (size_t)OCAP * NPL * sizeof(S);  // [slot][plane]
-    static constexpr size_t rho_off = (out_off + out_bytes + 127) / 128 * 128;
+    // two stages [slot][plane]: the tile being computed and the next one
+    // in flight; a stage's own block also receives the tile's output
+    static constexpr size_t stg_bytes = ((size_t)SCAP * NPL * sizeof(S) + 127) / 128 * 128;
+    static constexpr size_t rho_off = 2 * stg_bytes;
     static constexpr size_t rho_bytes = (size_t)2 * SN1 * sizeof(R);
     static constexpr size_t tab_off = (rho_off + rho_bytes + 127) / 128 * 128;  // two buffers
     static constexpr size_t tab_bytes = (size_t)2 * TABW * 4;
     static constexpr size_t rec_off = tab_off + tab_bytes;
     static constexpr size_t bar_off = (rec_off + REC_WORDS * 4 + 15) / 16 * 16;
-    static constexpr size_t total = bar_off + 8;
+    static constexpr size_t total = bar_off + 32;  // mbarriers full[2], done[2]
     static_assert(OCAP <= 1023, "own-block index is 10 bits");
     static_assert((TABW * 4) % 16 == 0 && (Q * NPL * sizeof(S)) % 16 == 0, "bulk copy granularity");
 };
@@ -111,51 +111,70 @@ struct SArgs {
     int first[N + 1];         // first work item of each lattice
     int ncases, total, tab_stride;
     // shared-memory layout, sized by the largest tile of the launch
-    uint32_t out_off, rho_off, tab_off, rec_off, bar_off;
+    uint32_t stage_bytes, rho_off, tab_off, rec_off, bar_off;
 };
 
-// offsets of the shared-memory regions for staged slots scap, own slots
-// ocap and table words tabw; returns the total bytes
+// offsets of the shared-memory regions for staged slots scap (per stage)
+// and table words tabw; returns the total bytes
 template <class P, int STY, int N>
-size_t smem_layout(int scap, int ocap, int tabw, SArgs<N> &s) {
-    constexpr int SFH = STY + 6, SN1 = SDXW * (STY + 4);
+size_t smem_layout(int scap, int tabw, SArgs<N> &s) {
+    constexpr int SN1 = SDXW * (STY + 4);
     using S = typename P::store_t;
     using R = typename P::real_t;
     auto up = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
-    const size_t stg = (size_t)scap * P::planes * sizeof(S);
-    s.out_off = (uint32_t)up(stg, 128);
-    s.rho_off = (uint32_t)up(s.out_off + (size_t)ocap * P::planes * sizeof(S), 128);
+    s.stage_bytes = (uint32_t)up((size_t)scap * P::planes * sizeof(S), 128);
+    s.rho_off = 2 * s.stage_bytes;
     s.tab_off = (uint32_t)up(s.rho_off + (size_t)2 * SN1 * sizeof(R), 128);
     s.rec_off = (uint32_t)(s.tab_off + (size_t)2 * tabw * 4);
     s.bar_off = (uint32_t)up(s.rec_off + REC_WORDS * 4, 16);
-    return s.bar_off + 8;
+    return s.bar_off + 32;  // mbarriers full[2], done[2]
 }
 
-__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-                 "r"(smem_u32(src)), "r"(bytes)
+// bulk store shared -> global with an L2 cache policy for the written lines
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes, uint64_t policy) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes), "l"(policy)
                  : "memory");
+}
+
+// named barrier `id` over `count` threads, and the same with an OR vote
+__device__ __forceinline__ void bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool bar_or(bool v, int id, int count) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
 }
 
 // CM: collision chosen at compile time (0 SRT of Eq. 1, 1 MRT) for a
 // single lattice, by each case's flag (2) in a batch
 template <class P, int STY, int N, int CM>
-__global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs<N> s) {
+__global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel(const __grid_constant__ SArgs<N> s) {
     using L = SLayout<P, STY>;
-    constexpr int SFH = L::SFH, SN1 = L::SN1;
+    constexpr int SN1 = L::SN1;
     using S = typename P::store_t;
     using R = typename P::real_t;
     constexpr int NT = STX * STY, NPL = L::NPL;
-    // the copy warp: issues the bulk copies and the output store, takes no
-    // part in phase B (it is the last warp, usually without a node in C)
-    constexpr int DW = NT / 32 - 1;
+    // NT compute threads, then one producer warp: it stages tiles into two
+    // stages ahead of the compute warps and stores their output, and meets
+    // them only on mbarriers (full[k]: stage k staged; done[k]: stage k's
+    // tile computed), never on their barriers (named barrier 1, NT threads)
+    constexpr int PW = NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
-    const S *stg = reinterpret_cast<const S *>(smem);
-    S *out = reinterpret_cast<S *>(smem + s.out_off);
+    auto stage = [&](int k) { return reinterpret_cast<S *>(smem + (size_t)k * s.stage_bytes); };
     R *rho = reinterpret_cast<R *>(smem + s.rho_off);
     uint32_t *tabs = reinterpret_cast<uint32_t *>(smem + s.tab_off);
     uint32_t *rec = reinterpret_cast<uint32_t *>(smem + s.rec_off);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + s.bar_off);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + s.bar_off);
+    uint64_t *done = full + 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     auto case_of = [&](int w) -> int {
         if constexpr (N == 1) {
@@ -167,70 +186,124 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
         }
     };
 
+    // L2 policies of the copy warp (made where used, so that no register
+    // holds them across the tile loop): the per-tile tables and copy records
+    // (read every step, about 6 % of a step's bytes) are kept in L2 across
+    // steps; the output block is not read again before the next step has
+    // streamed the whole lattice, so its lines go first.
     // copy warp: start the copy of tile w's record into shared memory
     auto fetch_record = [&](int w) {
         const int c = case_of(w);
         if (lane < REC_WORDS / 4) {
             const uint32_t *src = s.rec[c] + (size_t)(w - s.first[c]) * REC_WORDS + 4 * lane;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(rec + 4 * lane)), "l"(src)
+            asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                             smem_u32(rec + 4 * lane)),
+                         "l"(src), "l"(policy_evict_last())
                          : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // copy warp: stage tile w (record already in shared memory) into table buffer tb
-    auto issue = [&](int w, int tb) {
+    // copy warp: stage tile w (record already in shared memory) into stage
+    // and table buffer k, completing on mbarrier k
+    auto issue = [&](int w, int k) {
         const int c = case_of(w);
         const S *fin = static_cast<const S *>(s.fin[c]);
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
         const int nr = (int)rec[0];
         const uint32_t tbytes = 4u * (uint32_t)s.tab_words[c];
+        S *dst_stage = stage(k);
         fence_proxy_async();
         if (lane == 0) {
-            mbar_expect_tx(bar, rec[1] + tbytes);
-            bulk_g2s(tabs + tb * s.tab_stride, s.tab[c] + (size_t)(w - s.first[c]) * s.tab_words[c], tbytes,
-                     bar);
+            mbar_expect_tx(&full[k], rec[1] + tbytes);
+            bulk_g2s_hint(tabs + k * s.tab_stride, s.tab[c] + (size_t)(w - s.first[c]) * s.tab_words[c],
+                          tbytes, &full[k], policy_evict_last());
         }
         __syncwarp();
         for (int r = lane; r < nr; r += 32) {
             const uint32_t src = rec[4 + 3 * r], len = rec[5 + 3 * r], dst = rec[6 + 3 * r];
-            bulk_g2s(const_cast<S *>(stg) + (size_t)dst * NPL, fin + (size_t)src * NPL,
-                     len * (uint32_t)(NPL * sizeof(S)), bar);
+            bulk_g2s(dst_stage + (size_t)dst * NPL, fin + (size_t)src * NPL, len * (uint32_t)(NPL * sizeof(S)),
+                     &full[k]);
         }
         __syncwarp();
     };
 
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&done[0], NT / 32);
+        mbar_init(&done[1], NT / 32);
         fence_mbar_init();
     }
     __syncthreads();
     if ((int)blockIdx.x >= s.total) return;
-    if (warp == DW) {
-        fetch_record(blockIdx.x);
-        issue(blockIdx.x, 0);
-        if ((int)blockIdx.x + (int)gridDim.x < s.total) fetch_record(blockIdx.x + gridDim.x);
+    const int ntiles = (s.total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    // (the test hook stages nothing: the first tile's wait runs out)
+    const bool copies = !s.a[case_of(blockIdx.x)].test_no_copy;
+
+    if (warp == PW) {
+        // ---- producer: tile m of this CTA lives in stage m & 1 --------------------
+        if (!copies) return;
+        auto tile = [&](int m) { return (int)blockIdx.x + m * (int)gridDim.x; };
+        // wait until tile m has been computed, then store its output (the
+        // own block of its stage; length and start in table words 4 and 5)
+        auto store = [&](int m) -> bool {
+            const int km = m & 1, c = case_of(tile(m));
+            if (!mbar_wait(&done[km], (uint32_t)(m >> 1) & 1u, s.a[c].wait_ns)) return false;
+            const uint32_t *T = tabs + km * s.tab_stride;
+            const uint32_t own_len = T[4], start = T[5];
+            if (lane == 0 && own_len > 0)
+                bulk_s2g(static_cast<S *>(s.fout[c]) + (size_t)start * NPL, stage(km),
+                         own_len * (uint32_t)(NPL * sizeof(S)), policy_evict_first());
+            bulk_commit();
+            return true;
+        };
+        bool ok = true;
+        int issued = 0;
+        fetch_record(tile(0));
+        for (int m = 0; m < ntiles && ok; ++m) {
+            if (m >= 2) {
+                // stage m & 1 still holds tile m - 2: store it and wait until
+                // the store has read the stage
+                ok = store(m - 2);
+                if (!ok) break;
+                bulk_wait_read();
+            }
+            issue(tile(m), m & 1);
+            ++issued;
+            if (m + 1 < ntiles) fetch_record(tile(m + 1));
+        }
+        for (int m = ntiles > 2 ? ntiles - 2 : 0; m < ntiles && ok; ++m) ok = store(m);
+        bulk_wait_read();
+        if (!ok) {
+            // a wait ran out: report it, and give the copies in flight a
+            // bounded time to land before the shared memory is released
+            const StepArgs &a = s.a[case_of(blockIdx.x)];
+            const uint64_t drain = a.wait_ns < DRAIN_LIMIT_NS ? a.wait_ns : DRAIN_LIMIT_NS;
+            if (lane == 0) atomicExch(a.err, MCLBM_ERR_TIMEOUT);
+            for (int m = issued > 2 ? issued - 2 : 0; m < issued; ++m)
+                mbar_wait(&full[m & 1], (uint32_t)(m >> 1) & 1u, drain);
+        }
+        return;
     }
 
-    uint32_t parity = 0;
-    int tb = 0;
-    for (int w = blockIdx.x; w < s.total; w += gridDim.x) {
+    // ---- compute warps ----------------------------------------------------------
+    int n = 0;  // tiles done by this CTA; tile n lives in stage n & 1
+    for (int w = blockIdx.x; w < s.total; w += gridDim.x, ++n) {
         const int c = case_of(w);
         const int t = w - s.first[c];
         const StepArgs &a = s.a[c];
         const Geometry &g = a.g;
-        S *fout = static_cast<S *>(s.fout[c]);
         const int x0 = (t % s.tiles_x[c]) * STX, y0 = (t / s.tiles_x[c]) * STY;
-        const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
-        if (__syncthreads_or(bad)) {
-            if (tid == 0) {
-                atomicExch(a.err, MCLBM_ERR_TIMEOUT);
-                mbar_wait(bar, parity, DRAIN_LIMIT_NS);
-            }
-            if (warp == DW) bulk_wait_read();
+        const int st = n & 1;
+        const bool bad = !mbar_wait(&full[st], (uint32_t)(n >> 1) & 1u, a.wait_ns);
+        if (bar_or(bad, 1, NT)) {
+            // the producer finds the tile never computed and reports it
+            if (tid == 0) atomicExch(a.err, MCLBM_ERR_TIMEOUT);
             return;
         }
-        const uint32_t *T = tabs + tb * s.tab_stride;
+        const S *stg = stage(st);
+        const uint32_t *T = tabs + st * s.tab_stride;
         const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
         const uint32_t *E = T + HDR;
         // staged element offset (slot x planes) of every frame position (0
@@ -293,26 +366,13 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             rho[(ty + 2) * SDXW + tx + 2] = rho1;
             rho[SN1 + (ty + 2) * SDXW + tx + 2] = rho2;
         }
-        __syncthreads();
-        // the staged populations have been read.  The copy warp lets the
-        // others start C once the previous tile's output copy has read the
-        // output buffer (named barrier 1: it arrives, the others wait), then
-        // stages the next tile while they compute B and C.
-        // (When the copy warp owns tile nodes itself, all warps meet after B.)
-        const int wn = w + (int)gridDim.x;
-        const bool dw_busy = n_own > NT - 32;
-        if (warp == DW) {
-            bulk_wait_read();
-            if (!dw_busy) asm volatile("bar.arrive 1, %0;" ::"n"(NT) : "memory");
-            if (wn < s.total) {
-                issue(wn, tb ^ 1);
-                if (wn + (int)gridDim.x < s.total) fetch_record(wn + gridDim.x);
-            }
-        }
+        // the staged populations have been read: from here on the stage's
+        // own block receives the tile's output
+        bar_sync(1, NT);
 
         // ---- B: virtual solid densities on the 1-ring (zero outside) -----------
         const uint32_t *Es = E + n_own + n_ring;
-        for (int k = warp == DW ? n_sol : tid; k < n_sol; k += NT - 32) {
+        for (int k = tid; k < n_sol; k += NT) {
             const uint32_t e = Es[k];
             const int pos = (int)(e & 0xfffu);
             const int code = (int)((e >> 12) & 0xffu);
@@ -337,10 +397,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             rho[pos] = s1;
             rho[SN1 + pos] = s2;
         }
-        if (dw_busy)
-            __syncthreads();
-        else if (warp != DW)
-            asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+        bar_sync(1, NT);
 
         // ---- C: collision of the tile's fluid nodes --------------------------------
         if (have) {
@@ -375,7 +432,7 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
             R omega, ux, uy;
             node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
             collide<R, CM>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
-            S *o = out + bidx * NPL;
+            S *o = stage(st) + bidx * NPL;
             if constexpr (P::ref) {
                 const S h1 = from_real<S>(rho1), h2 = from_real<S>(rho2);
                 o[18] = h1;
@@ -394,20 +451,13 @@ __global__ void __launch_bounds__(STX *STY, STY == 8 ? 3 : 2) sparse_kernel(cons
                 }
             }
         }
+        // the output is in the stage: one arrival per warp hands it to the
+        // producer's store; the densities are reused by the next tile
         fence_proxy_async();
-        __syncthreads();
-        if (warp == DW) {
-            // the tile's block (length and start in table words 4 and 5), one
-            // bulk store
-            const uint32_t own_len = T[4], start = T[5];
-            if (lane == 0 && own_len > 0)
-                bulk_s2g(fout + (size_t)start * NPL, out, own_len * (uint32_t)(NPL * sizeof(S)));
-            bulk_commit();
-        }
-        parity ^= 1u;
-        tb ^= 1;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&done[st]);
+        bar_sync(1, NT);
     }
-    if (warp == DW) bulk_wait_read();
 }
 
 // dense <-> fluid-only conversion, one thread per (slot, plane)
@@ -782,18 +832,19 @@ cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t s
     }
     static SArgs<N> s;  // host staging of the parameter block
     std::memset(&s, 0, sizeof(s));
-    int scap = 16, ocap = 2, tabw = 4, total = 0;
+    int scap = 16, tabw = 4, total = 0;
     for (int c = 0; c < n; ++c) {
         Lattice &L = *cases[c];
         if (L.nfp <= 0 || L.sparse_ty != STY || L.sparse_state == 0) return cudaErrorInvalidValue;
         scap = std::max(scap, L.sscap);
-        ocap = std::max(ocap, L.socap);
         tabw = std::max(tabw, L.stab_words);
         s.a[c].g = L.geometry();
         s.a[c].p = L.p;
         s.a[c].p.round_fp32();
         s.a[c].d5 = L.d5;
         s.a[c].err = L.err;
+        s.a[c].wait_ns = L.wait_ns;
+        s.a[c].test_no_copy = L.test_no_copy;
         s.fin[c] = L.fs[L.scur];
         s.fout[c] = L.fs[1 - L.scur];
         s.tab[c] = L.stab;
@@ -807,7 +858,7 @@ cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t s
     s.ncases = n;
     s.total = total;
     s.tab_stride = tabw;
-    const size_t bytes = smem_layout<P, STY, N>(scap, ocap, tabw, s);
+    const size_t bytes = smem_layout<P, STY, N>(scap, tabw, s);
     if (bytes > Lay::total) return cudaErrorInvalidValue;
     // resident CTAs per SM for this size (cached per size)
     static size_t last_bytes = 0;
@@ -816,13 +867,14 @@ cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t s
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY, N, CM>, STX * STY, bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sparse_kernel<P, STY, N, CM>, STX * STY + 32, bytes);
         slots = (sms < 1 ? 1 : sms) * (per_sm < 1 ? 1 : per_sm);
         last_bytes = bytes;
     }
     if (slots_out) *slots_out = slots;
     const int g = grid > 0 ? std::min(grid, total) : std::min(slots, total);
-    sparse_kernel<P, STY, N, CM><<<g, STX * STY, bytes, stream>>>(s);
+    // STX * STY compute threads and the producer warp
+    sparse_kernel<P, STY, N, CM><<<g, STX * STY + 32, bytes, stream>>>(s);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)

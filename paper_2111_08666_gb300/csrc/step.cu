@@ -179,6 +179,7 @@ cudaError_t launch_step_tile(Lattice &L, int tile_cfg) {
     a.fout = L.f[1 - L.cur];
     a.d5 = L.d5;
     a.err = L.err;
+    a.wait_ns = L.wait_ns;
     a.rows_per_cta = 0;
     cudaError_t e;
     switch (L.prec) {

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(W) sweep_step_kernel(const StepArgs a) {
     const int K = (y_hi - y_lo) + 4;
     for (int k = 0; k < K; ++k) {
         while (waited <= k + 2 && waited < nraw) {
-            bad |= !mbar_wait(&bar[waited % NR], (waited / NR) & 1, WAIT_LIMIT_NS);
+            bad |= !mbar_wait(&bar[waited % NR], (waited / NR) & 1, a.wait_ns);
             ++waited;
         }
         // ---- A: densities of row qA over columns -2 .. W+1 -------------------
@@ -298,6 +298,7 @@ cudaError_t launch_step_sweep(Lattice &L) {
     a.fout = L.f[1 - L.cur];
     a.d5 = L.d5;
     a.err = L.err;
+    a.wait_ns = L.wait_ns;
     a.rows_per_cta = 16;
     cudaError_t e;
     switch (L.prec) {

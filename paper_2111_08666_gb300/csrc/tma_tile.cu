@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(TX *TY, 2) tma_tile_kernel(const __grid_consta
         const int t = w - b.first[c];
         const int x0 = (t % b.tiles_x[c]) * TX, y0 = (t / b.tiles_x[c]) * TY;
 
-        const bool bad = !mbar_wait(bar, parity, WAIT_LIMIT_NS);
+        const bool bad = !mbar_wait(bar, parity, a.wait_ns);
         if (__syncthreads_or(bad)) {
             if (tid == 0) {
                 atomicExch(a.err, MCLBM_ERR_TIMEOUT);
@@ -526,6 +526,7 @@ cudaError_t launch_args(Lattice *const *cases, int n, const CUtensorMap *maps, i
         a.fout = L.f[1 - L.cur];
         a.d5 = L.d5;
         a.err = L.err;
+        a.wait_ns = L.wait_ns;
         a.rows_per_cta = 0;
         const CUtensorMap *m = maps + MAPS_PER_CASE * c;
         b.tin[c] = m[2 * L.cur];               // read the current buffer

@@ -2,22 +2,22 @@
 the capillary-pressure / saturation curves, their hysteresis, the
 irreducible water and residual oil saturations.
 
-Each wettability runs on its own lattice (and CUDA stream) through the
-quasi-static protocol of ``drainage.py``: the inlet density of component 1
-rises level by level from equal pressures (drainage), then falls back to
-the outlet's (spontaneous imbibition), then the outlet density of component
-2 rises (forced imbibition).  A level ends when S_w by mass changes by less
-than ``tol`` over ``window`` steps, or after ``max_steps``.  The lattices
-advance in turns, so that their kernels overlap on the GPU.  All arithmetic
-runs in the CUDA library.
+The wettability states are the cases of one batch (``mclbm_batch_*``): one
+persistent launch per step advances all of them, under the batch's CUDA
+graph and autotuned step.  Each case follows the quasi-static protocol of
+``drainage.py`` on its own: the inlet density of component 1 rises level by
+level from equal pressures (drainage), then falls back to the outlet's
+(spontaneous imbibition), then the outlet density of component 2 rises
+(forced imbibition).  A level ends when S_w by mass changes by less than
+``tol`` over ``window`` steps, or after ``max_steps``; a case then moves to
+its next level through its batch view while the others continue.  All
+arithmetic runs in the CUDA library.
 """
 from __future__ import annotations
 
 import json
 import math
 import time
-
-import numpy as np
 
 from . import mclbm, media
 
@@ -32,13 +32,12 @@ def schedule(d_in: float, n_drain: int, n_spont: int, d_out: float, n_forced: in
 
 
 class Run:
-    def __init__(self, theta: float, levels, window: int, tol: float, max_steps: int):
-        c = media.config_block_hysteresis(theta)
-        self.theta, self.xi, self.levels = theta, c["xi_value"], levels
+    """One wettability state: a case of the batch, walked through the levels."""
+
+    def __init__(self, view, theta: float, xi: float, levels, window: int, tol: float,
+                 max_steps: int):
+        self.view, self.theta, self.xi, self.levels = view, theta, xi, levels
         self.window, self.tol, self.max_steps = window, tol, max_steps
-        self.lat = mclbm.Lattice(c["solid"], c["xi"], prec="fp32", nu1=c["nu1"], nu2=c["nu2"],
-                                 rho_in1=1.0, rho_out2=1.0)
-        self.lat.init(c["rho1"], c["rho2"])
         self.k = -1
         self.points = []
         self.next_level()
@@ -47,20 +46,19 @@ class Run:
         self.k += 1
         if self.k < len(self.levels):
             r_in, r_out, _ = self.levels[self.k]
-            self.lat.set_pressure_bc(r_in, r_out)
+            self.view.set_pressure_bc(r_in, r_out)
             self.steps = 0
-            self.prev = self.lat.diagnostics()["sw_mass"]
+            self.prev = self.view.diagnostics()["sw_mass"]
 
     @property
     def done(self):
         return self.k >= len(self.levels)
 
-    def advance(self):
-        self.lat.step(self.window)
-        self.steps += self.window
-
     def check(self):
-        d = self.lat.diagnostics()
+        """After the batch advanced one window: record the level if it has
+        converged (or hit the cap) and move on."""
+        self.steps += self.window
+        d = self.view.diagnostics()
         conv = abs(d["sw_mass"] - self.prev) < self.tol
         if conv or self.steps >= self.max_steps or not math.isfinite(d["sw_mass"]):
             r_in, r_out, phase = self.levels[self.k]
@@ -70,6 +68,30 @@ class Run:
             self.next_level()
         else:
             self.prev = d["sw_mass"]
+
+
+def sweep(thetas, levels, window: int = 1000, tol: float = 1e-6, max_steps: int = 60000,
+          stream=None):
+    """Run the protocol at every contact angle of ``thetas`` on the block
+    stand-in, all cases in one batch.  Returns (runs, batch steps, seconds)."""
+    cfgs = [media.config_block_hysteresis(float(t)) for t in thetas]
+    cases = [dict(solid=c["solid"], xi=c["xi"], rho1=c["rho1"], rho2=c["rho2"], nu1=c["nu1"],
+                  nu2=c["nu2"], rho_in1=1.0, rho_out2=1.0) for c in cfgs]
+    b = mclbm.mclbm_batch_create(cases, mclbm.MCLBM_FP32, stream)
+    try:
+        runs = [Run(mclbm.LatticeView(b, k, c["ny"], c["nx"], mclbm.MCLBM_FP32), c["theta"],
+                    c["xi_value"], levels, window, tol, max_steps) for k, c in enumerate(cfgs)]
+        t0 = time.perf_counter()
+        steps = 0
+        while not all(r.done for r in runs):
+            mclbm.mclbm_batch_step(b, window)
+            steps += window
+            for r in runs:
+                if not r.done:
+                    r.check()
+        return runs, steps, time.perf_counter() - t0
+    finally:
+        mclbm.mclbm_batch_destroy(b)
 
 
 def summarize(run: Run) -> dict:
@@ -101,21 +123,14 @@ def main(argv=None) -> None:
     ap.add_argument("--max-steps", type=int, default=60000)
     a = ap.parse_args(argv)
     levels = schedule(a.d_in, a.n_drain, a.n_spont, a.d_out, a.n_forced)
-    runs = [Run(float(t), levels, a.window, a.tol, a.max_steps) for t in a.thetas.split(",")]
-    t0 = time.perf_counter()
-    while not all(r.done for r in runs):
-        live = [r for r in runs if not r.done]
-        for r in live:
-            r.advance()
-        for r in live:
-            r.check()
-    sec = time.perf_counter() - t0
+    runs, steps, sec = sweep([float(t) for t in a.thetas.split(",")], levels, a.window, a.tol,
+                             a.max_steps)
     for r in runs:
         s = summarize(r)
+        s["batch_steps"] = steps
         s["seconds_all"] = sec
         s["points"] = r.points
         print(json.dumps(s), flush=True)
-        r.lat.close()
 
 
 if __name__ == "__main__":

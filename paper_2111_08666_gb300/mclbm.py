@@ -34,6 +34,8 @@ MCLBM_FLAG_VEL_SHIFT = 1
 MCLBM_FLAG_DIAG_EVERY = 2
 MCLBM_FLAG_KERNEL = 3
 MCLBM_FLAG_TILE_SHAPE = 4
+MCLBM_FLAG_WAIT_LIMIT_US = 5
+MCLBM_FLAG_TEST_NO_COPY = 6
 
 DIAG_FIELDS = ("mass1", "mass2", "sw_count", "sw_mass", "p_in", "p_out", "pc", "n_fluid")
 
@@ -104,6 +106,7 @@ _SIGS = {
     "mclbm_unet_train_step": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp,
                                         C.c_double, _P(C.c_double)]),
     "mclbm_init_from_phase": (C.c_int, [_vp, _vp]),
+    "mclbm_blend_phase": (C.c_int, [_vp, _vp, C.c_double, _P(_i64)]),
     "mclbm_save": (C.c_int, [_vp, C.c_char_p]),
     "mclbm_load": (C.c_int, [_vp, C.c_char_p]),
     "mclbm_launch_count": (_i64, []),
@@ -239,6 +242,14 @@ def mclbm_load(h, path) -> None:
 
 def mclbm_init_from_phase(h, phi) -> None:
     _check(load().mclbm_init_from_phase(h, _addr(phi, np.float32)))
+
+
+def mclbm_blend_phase(h, phi_hat, flip: float = 0.0) -> int:
+    """Warm start in place from a predicted phase field [ny][nx] (float32,
+    host or device); returns the number of nodes reset."""
+    n = C.c_int64(0)
+    _check(load().mclbm_blend_phase(h, _addr(phi_hat, np.float32), float(flip), C.byref(n)))
+    return int(n.value)
 
 
 def mclbm_set_populations(h, f) -> None:

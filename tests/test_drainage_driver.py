@@ -69,3 +69,34 @@ def test_drainage_curve_gpu_matches_oracle():
     # drainage: water saturation does not increase as P_c is raised
     sw = [p.sw_mass for p in cg.points]
     assert all(b <= a + 1e-9 for a, b in zip(sw, sw[1:]))
+
+
+@pytest.mark.gpu
+def test_imbibition_curve_gpu_matches_oracle():
+    """Imbibition (Sec. 4.2.2) from a drained state, FP64 on the GPU against
+    the oracle: the inlet density is lowered (spontaneous part) and then the
+    outlet density raised (forced part); every level's step count,
+    capillary pressure and saturations agree."""
+    import oracle
+    from paper_2111_08666_gb300 import mclbm
+    c = media.config_small_fp64()
+    xi = media.uniform_xi(c["solid"], -0.4)
+    kw = dict(nu1=(1.7 - 0.5) / 3, nu2=(0.62 - 0.5) / 3, rho_in1=1.0, rho_out2=1.0)
+    o = oracle.Oracle(c["solid"], xi, **kw)
+    o.init(c["rho1"], c["rho2"])
+    g = mclbm.Lattice(c["solid"], xi, prec="fp64", **kw)
+    g.init(c["rho1"], c["rho2"])
+    args = dict(window=200, tol=1e-6, max_steps=800)
+    for lat in (o, g):
+        drainage.drainage(lat, [1.01, 1.02], **args)
+    co = drainage.imbibition(o, [1.01, 1.0], [1.01, 1.02], 1.0, **args)
+    cg = drainage.imbibition(g, [1.01, 1.0], [1.01, 1.02], 1.0, **args)
+    assert len(cg.points) == len(co.points) == 4
+    for a, b in zip(cg.points, co.points):
+        assert (a.rho_in1, a.rho_out2) == (b.rho_in1, b.rho_out2)
+        assert a.steps == b.steps
+        assert a.pc == pytest.approx(b.pc, rel=1e-9, abs=1e-12)
+        assert a.sw_mass == pytest.approx(b.sw_mass, rel=1e-10)
+        assert a.sw_count == b.sw_count
+    # the forced part lowers P_c below the spontaneous part's
+    assert cg.points[-1].pc < cg.points[1].pc

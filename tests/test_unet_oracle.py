@@ -102,3 +102,39 @@ def test_upsample_then_convolve_is_four_coarse_2x2_convolutions():
             acc += xp[:, 1 + a:1 + a + h, 1 + c:1 + c + wd, :] @ k.T
         got[:, py::2, px::2, :] = acc + b
     assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_bf16_round_known_values():
+    """Round to nearest, ties to even, at 8 significant bits: exactly
+    representable values are kept; a value half an ulp above 1 (ulp 2^-7)
+    rounds down to the even 1, three halves up to 1 + 2^-6 ... and signs
+    and powers of two are preserved."""
+    r = unet.bf16_round
+    assert r(1.0) == 1.0 and r(-2.5) == -2.5 and r(0.0) == 0.0
+    assert r(1.0 + 2.0 ** -8) == 1.0                 # tie -> even (down)
+    assert r(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie -> even (up)
+    assert r(1.0 + 2.0 ** -8 + 2.0 ** -12) == 1.0 + 2.0 ** -7
+    assert r(3.0 * 2.0 ** -100) == 3.0 * 2.0 ** -100
+    x = np.random.default_rng(0).normal(0, 10, 1000)
+    rel = np.abs(r(x) - x) / np.abs(x)
+    assert rel.max() <= 2.0 ** -8 and np.all(np.abs(r(r(x)) - r(x)) == 0)
+
+
+def test_storage_model_is_the_plain_network_without_rounding():
+    """store=None and store=identity give the plain FP64 network; the BF16
+    model rounds the 3x3 weights only (biases and the head are kept)."""
+    levels, base = 2, 8
+    rng = np.random.default_rng(3)
+    theta = rng.normal(0, 0.3, unet.param_count(levels, base))
+    x = rng.normal(0, 1, (1, 8, 8, unet.IN_CHANNELS))
+    a, _ = unet.forward(theta, x, levels, base)
+    b, _ = unet.forward(theta, x, levels, base, store=lambda v: v)
+    assert np.array_equal(a, b)
+    q = unet.store_weights(theta, levels, base)
+    p, pq = unet.unpack(theta, levels, base), unet.unpack(q, levels, base)
+    for name, _, _, k in unet.layer_shapes(levels, base):
+        assert np.array_equal(pq[name][1], p[name][1])                    # biases kept
+        if k == 3:
+            assert np.array_equal(pq[name][0], unet.bf16_round(p[name][0]))
+        else:
+            assert np.array_equal(pq[name][0], p[name][0])                # the head kept
