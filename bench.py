@@ -69,6 +69,15 @@ def step_kernel(kernel: str, prec: str) -> str:
             "fluid": "sparse_kernel"}[kernel]
 
 
+def tile_label(kname: str, shape: int, prec: str) -> str:
+    """Tile of the step kernel that runs."""
+    if kname == "sparse_kernel":
+        return "32x12" if shape == 1 else "32x8"
+    if kname == "tma_tile_kernel":
+        return "32x8" if shape == 1 else ("32x12" if prec == "fp32dev" else "32x16")
+    return "32x16"
+
+
 def kernel_sha(name: str = "sparse_kernel") -> str:
     h = hashlib.sha256()
     for p in STEP_KERNELS[name]["sources"]:
@@ -272,6 +281,7 @@ def run_gpu(args, rank, world):
                                f"rho_in=1.005, rho_out=1)",
                    "nx": c["nx"], "ny": c["ny"], "porosity": round(c["porosity"], 4),
                    "storage": args.prec, "step_kernel": args.kernel, "tile_shape": args.tile_shape,
+                   "tile": tile_label(kname, args.tile_shape, args.prec),
                    "parallelism": f"replicas x{world}",
                    "l2": "working set 302 MB > 129 MB L2, no flush needed",
                    "mflups": round(value * (c["solid"] == 0).mean(), 1),
@@ -460,7 +470,8 @@ def main():
                     default="fp32")
     ap.add_argument("--kernel", choices=["auto", "tile", "strip", "tma", "fluid"], default="auto")
     ap.add_argument("--tile-shape", type=int, choices=[0, 1], default=0,
-                    help="tile of the TMA kernel: 0 = 32x16 (32x12 fp32dev), 1 = 32x8")
+                    help="tile shape: TMA kernel 0 = 32x16 (32x12 fp32dev), 1 = 32x8; "
+                         "fluid-only kernel 0 = 32x8, 1 = 32x12")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-steps", type=int, default=400,
                     help="steps of the 24-case batched section (0: skip it)")

@@ -82,8 +82,10 @@ typedef enum {
      * tile, staged with bulk copies (FP32, FP16 and BF16 deviation storage;
      * the dense buffers are rebuilt whenever a read-out needs them). */
     MCLBM_FLAG_KERNEL = 3,
-    /* Tile of kernel 3: 0 (default) 32 x 16 nodes (32 x 12 for FP32_DEV),
-     * two CTAs per SM; 1: 32 x 8 nodes, three CTAs per SM.  Same results. */
+    /* Tile shape, same results either way.  Kernel 3: 0 (default) 32 x 16
+     * nodes (32 x 12 for FP32_DEV), two CTAs per SM; 1: 32 x 8 nodes, three
+     * CTAs per SM.  Kernel 4: 0 (default) 32 x 8 nodes, three CTAs per SM
+     * where the staged tiles fit; 1: 32 x 12 nodes, two CTAs per SM. */
     MCLBM_FLAG_TILE_SHAPE = 4,
     /* Limit, in microseconds (1..10^7, default 10^6), of every wait of the
      * staging kernels (2, 3 and 4) for their asynchronous copies.  A wait

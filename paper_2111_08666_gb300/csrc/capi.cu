@@ -349,6 +349,10 @@ int mclbm_destroy(mclbm_lattice *lat) {
     return MCLBM_OK;
 }
 
+// Tile height of the fluid-only kernel: 32 x 8 by default (three CTAs per
+// SM: their warps fill each other's barrier waits), 32 x 12 for shape 1.
+static int sparse_height(const Lattice &L) { return L.tile_shape == 1 ? 12 : 8; }
+
 int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
     if (int rc = check_lat(lat)) return rc;
     switch (flag) {
@@ -703,7 +707,7 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
         // else the TMA tile kernel, else (FP64) the global-memory tile kernel
         which = tma_supported(*lat) ? 3 : 1;
         if (sparse_precision(lat->prec)) {
-            if (sparse_prepare(*lat, lat->tile_shape == 1 ? 8 : 12) == MCLBM_OK && lat->nfp > 0) which = 4;
+            if (sparse_prepare(*lat, sparse_height(*lat)) == MCLBM_OK && lat->nfp > 0) which = 4;
         }
     }
     if (which == 3 && !tma_supported(*lat))
@@ -713,7 +717,7 @@ int mclbm_step(mclbm_lattice *lat, int64_t nsteps) {
     if (which == 4) {
         if (!sparse_precision(lat->prec))
             return fail(MCLBM_ERR_ARG, "the fluid-only kernel is not available for this precision");
-        if (int rc = sparse_prepare(*lat, lat->tile_shape == 1 ? 8 : 12)) return rc;
+        if (int rc = sparse_prepare(*lat, sparse_height(*lat))) return rc;
         if (int rc = dense_to_sparse(*lat)) return rc;
     } else if (nsteps > 0) {
         if (int rc = dense_current(*lat)) return rc;

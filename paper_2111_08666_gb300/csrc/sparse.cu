@@ -40,7 +40,7 @@ namespace mclbm {
 
 namespace {
 
-constexpr int STX = 32;                  // tile width; height 12 (shape 0) or 8 (shape 1)
+constexpr int STX = 32;                  // tile width; height 8 (shape 0) or 12 (shape 1)
 constexpr int SFW = STX + 6;             // staged frame: tile + 3-node ring
 constexpr int SDXW = STX + 4;            // density frame: tile + 2-node ring
 constexpr int MAXR = 24;                 // ranges per tile (own block included)
@@ -70,7 +70,7 @@ struct SLayout {
     // in flight; a stage's own block also receives the tile's output
     static constexpr size_t stg_bytes = ((size_t)SCAP * NPL * sizeof(S) + 127) / 128 * 128;
     static constexpr size_t rho_off = 2 * stg_bytes;
-    static constexpr size_t rho_bytes = (size_t)2 * SN1 * sizeof(R);
+    static constexpr size_t rho_bytes = (size_t)4 * SN1 * sizeof(R);  // two buffers of (rho1, rho2) pairs
     static constexpr size_t tab_off = (rho_off + rho_bytes + 127) / 128 * 128;  // two buffers
     static constexpr size_t tab_bytes = (size_t)2 * TABW * 4;
     static constexpr size_t rec_off = tab_off + tab_bytes;
@@ -124,7 +124,7 @@ size_t smem_layout(int scap, int tabw, SArgs<N> &s) {
     auto up = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
     s.stage_bytes = (uint32_t)up((size_t)scap * P::planes * sizeof(S), 128);
     s.rho_off = 2 * s.stage_bytes;
-    s.tab_off = (uint32_t)up(s.rho_off + (size_t)2 * SN1 * sizeof(R), 128);
+    s.tab_off = (uint32_t)up(s.rho_off + (size_t)4 * SN1 * sizeof(R), 128);  // two density buffers
     s.rec_off = (uint32_t)(s.tab_off + (size_t)2 * tabw * 4);
     s.bar_off = (uint32_t)up(s.rec_off + REC_WORDS * 4, 16);
     return s.bar_off + 32;  // mbarriers full[2], done[2]
@@ -136,6 +136,29 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                  "r"(smem_u32(src)), "r"(bytes), "l"(policy)
                  : "memory");
 }
+
+// The two components of a stored value sit side by side in the fluid-only
+// layout (plane 2 i + comp for population i, 18 + comp for the reference
+// densities of the deviation storages), so that one 8-byte (FP32) or
+// 4-byte (16-bit) shared-memory access moves both.
+__device__ __forceinline__ float2 pair_load(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 pair_load(const __half *p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+__device__ __forceinline__ float2 pair_load(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+__device__ __forceinline__ void pair_store(float *p, float a, float b) {
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void pair_store(__half *p, float a, float b) {
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
+__device__ __forceinline__ void pair_store(__nv_bfloat16 *p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+// dense plane (comp * 9 + i, or 18 + comp) of fluid-only plane k
+__host__ __device__ __forceinline__ int dense_plane(int k) { return k < 18 ? (k & 1) * 9 + (k >> 1) : k; }
 
 // named barrier `id` over `count` threads, and the same with an OR vote
 __device__ __forceinline__ void bar_sync(int id, int count) {
@@ -170,7 +193,9 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
     constexpr int PW = NT / 32;
     extern __shared__ __align__(128) unsigned char smem[];
     auto stage = [&](int k) { return reinterpret_cast<S *>(smem + (size_t)k * s.stage_bytes); };
-    R *rho = reinterpret_cast<R *>(smem + s.rho_off);
+    static_assert(sizeof(R) == 4, "the fluid-only kernel computes in FP32");
+    // two density buffers of [SN1] (rho1, rho2) pairs
+    float2 *rho0 = reinterpret_cast<float2 *>(smem + s.rho_off);
     uint32_t *tabs = reinterpret_cast<uint32_t *>(smem + s.tab_off);
     uint32_t *rec = reinterpret_cast<uint32_t *>(smem + s.rec_off);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + s.bar_off);
@@ -288,92 +313,103 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
     }
 
     // ---- compute warps ----------------------------------------------------------
-    int n = 0;  // tiles done by this CTA; tile n lives in stage n & 1
-    for (int w = blockIdx.x; w < s.total; w += gridDim.x, ++n) {
-        const int c = case_of(w);
+    // Tile n lives in stage n & 1 and densities buffer n & 1.  Per tile:
+    //   X: collision (C) of tile n, then the pulls and densities (A) of
+    //      tile n + 1 -- the threads without a node in C take the ring pulls
+    //      of A, so that the two phases share one barrier;
+    //   B: virtual solid densities of tile n + 1.
+    // A thread keeps its own node's populations in registers from A to C.
+    auto tile_xy = [&](int w, int &c, int &x0, int &y0) {
+        c = case_of(w);
         const int t = w - s.first[c];
+        x0 = (t % s.tiles_x[c]) * STX;
+        y0 = (t / s.tiles_x[c]) * STY;
+    };
+    // A: pull + Set-3 + densities (Eq. 3) of tile w in stage k: the ring
+    // entries from the last thread down, the own node of thread tid
+    auto phase_a = [&](int w, int k, R f[2][9], R &rho1, R &rho2) {
+        int c, x0, y0;
+        tile_xy(w, c, x0, y0);
         const StepArgs &a = s.a[c];
-        const Geometry &g = a.g;
-        const int x0 = (t % s.tiles_x[c]) * STX, y0 = (t / s.tiles_x[c]) * STY;
-        const int st = n & 1;
-        const bool bad = !mbar_wait(&full[st], (uint32_t)(n >> 1) & 1u, a.wait_ns);
-        if (bar_or(bad, 1, NT)) {
-            // the producer finds the tile never computed and reports it
-            if (tid == 0) atomicExch(a.err, MCLBM_ERR_TIMEOUT);
-            return;
-        }
-        const S *stg = stage(st);
-        const uint32_t *T = tabs + st * s.tab_stride;
+        const S *stg = stage(k);
+        float2 *rho = rho0 + k * SN1;
+        const uint32_t *T = tabs + k * s.tab_stride;
         const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
         const uint32_t *E = T + HDR;
         // staged element offset (slot x planes) of every frame position (0
         // where nothing is staged)
         const uint16_t *slot_of = reinterpret_cast<const uint16_t *>(E + n_own + n_ring + n_sol);
-        const bool have = tid < n_own;
-        const uint32_t me = have ? E[tid] : 0u;
-        const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u), bidx = (int)(me >> 22);
-
-        // population (plane, comp) of the staged node at element offset off
+        // population (plane, comp) of the staged node at element offset
+        // off, and both components of a plane at once
         auto val = [&](int plane, int comp, int off, R wt) -> R {
-            R v = to_real(stg[off + comp * 9 + plane]);
+            R v = to_real(stg[off + 2 * plane + comp]);
             if constexpr (P::ref) v += wt * to_real(stg[off + 18 + comp]);
             return v;
         };
-        // f_i = f*_i(x - e_i), or the node's own f*_opp(i) where x - e_i is not
-        // fluid (half-way bounce-back), then the open-end treatment (Sec. 2.3)
-        auto pull = [&](int fpos, int ooff, uint32_t e, int x, int y, R f[2][9]) {
+        auto val2 = [&](int plane, int off, R wt, R &v0, R &v1) {
+            float2 v = pair_load(stg + off + 2 * plane);
+            if constexpr (P::ref) {
+                const float2 r = pair_load(stg + off + 18);
+                v.x += wt * r.x;
+                v.y += wt * r.y;
+            }
+            v0 = v.x;
+            v1 = v.y;
+        };
+        // f_i = f*_i(x - e_i), or the node's own f*_opp(i) where x - e_i is
+        // not fluid (half-way bounce-back), then the open-end treatment
+        // (Sec. 2.3)
+        auto pull = [&](int fpos, int ooff, uint32_t e, int x, int y, R g9[2][9]) {
             const uint32_t m = (e >> 12) & 0xffu;
-            f[0][0] = val(0, 0, ooff, wgt<R>(0));
-            f[1][0] = val(0, 1, ooff, wgt<R>(0));
+            val2(0, ooff, wgt<R>(0), g9[0][0], g9[1][0]);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const bool sb = (m >> (opp(i) - 1)) & 1u;
                 const int off = sb ? ooff : (int)slot_of[fpos - ey(i) * SFW - ex(i)];
                 const int pl = sb ? opp(i) : i;
-                f[0][i] = val(pl, 0, off, wgt<R>(i));
-                f[1][i] = val(pl, 1, off, wgt<R>(i));
+                val2(pl, off, wgt<R>(i), g9[0][i], g9[1][i]);
             }
             if (e & SET3)
-                apply_open_bc<R>(a, x, y, [&](int comp, int i) { return val(i, comp, ooff, wgt<R>(i)); }, f);
+                apply_open_bc<R>(a, x, y, [&](int comp, int i) { return val(i, comp, ooff, wgt<R>(i)); }, g9);
         };
-
-        // ---- A: densities of the ring's fluid nodes and of the tile's own ------
-        for (int k = tid - n_own + (tid < n_own ? NT : 0); k < n_ring; k += NT) {
-            const uint32_t e = E[n_own + k];
+        for (int kk = NT - 1 - tid; kk < n_ring; kk += NT) {
+            const uint32_t e = E[n_own + kk];
             const int pos = (int)(e & 0xfffu);
             const int dr = pos / SDXW, dc = pos - dr * SDXW;
             const int fpos = (dr + 1) * SFW + dc + 1;
-            R f[2][9];
-            pull(fpos, slot_of[fpos], e, x0 - 2 + dc, wrap(y0 - 2 + dr, g.ny), f);
+            R fr[2][9];
+            pull(fpos, slot_of[fpos], e, x0 - 2 + dc, wrap(y0 - 2 + dr, a.g.ny), fr);
             R r1 = 0, r2 = 0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                r1 += f[0][i];
-                r2 += f[1][i];
+                r1 += fr[0][i];
+                r2 += fr[1][i];
             }
-            rho[pos] = r1;
-            rho[SN1 + pos] = r2;
+            rho[pos] = make_float2(r1, r2);
         }
-        R f[2][9];
-        R rho1 = 0, rho2 = 0;
-        if (have) {
+        if (tid < n_own) {
+            const uint32_t me = E[tid];
+            const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u), bidx = (int)(me >> 22);
             pull((ty + 3) * SFW + tx + 3, bidx * NPL, me, x0 + tx, y0 + ty, f);
+            rho1 = 0;
+            rho2 = 0;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 rho1 += f[0][i];
                 rho2 += f[1][i];
             }
-            rho[(ty + 2) * SDXW + tx + 2] = rho1;
-            rho[SN1 + (ty + 2) * SDXW + tx + 2] = rho2;
+            rho[(ty + 2) * SDXW + tx + 2] = make_float2(rho1, rho2);
         }
-        // the staged populations have been read: from here on the stage's
-        // own block receives the tile's output
-        bar_sync(1, NT);
-
-        // ---- B: virtual solid densities on the 1-ring (zero outside) -----------
-        const uint32_t *Es = E + n_own + n_ring;
-        for (int k = tid; k < n_sol; k += NT) {
-            const uint32_t e = Es[k];
+    };
+    // B: virtual solid densities (Eqs. 16-17) on the 1-ring (zero outside)
+    auto phase_b = [&](int w, int k) {
+        const Geometry &g = s.a[case_of(w)].g;
+        float2 *rho = rho0 + k * SN1;
+        const uint32_t *T = tabs + k * s.tab_stride;
+        const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
+        const uint32_t *Es = T + HDR + n_own + n_ring;
+        for (int kk = tid; kk < n_sol; kk += NT) {
+            const uint32_t e = Es[kk];
             const int pos = (int)(e & 0xfffu);
             const int code = (int)((e >> 12) & 0xffu);
             const uint32_t fm = e >> 20;
@@ -383,8 +419,9 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
                 if ((fm >> (i - 1)) & 1u) {
                     const R w8 = wgt<R>(i);
                     const int q = pos + ey(i) * SDXW + ex(i);
-                    n1s += w8 * rho[q];
-                    n2s += w8 * rho[SN1 + q];
+                    const float2 r = rho[q];
+                    n1s += w8 * r.x;
+                    n2s += w8 * r.y;
                     den += w8;
                 }
             }
@@ -394,13 +431,19 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
                 s1 = chi_at<R>(g, 2 * code) * n1s * inv;
                 s2 = chi_at<R>(g, 2 * code + 1) * n2s * inv;
             }
-            rho[pos] = s1;
-            rho[SN1 + pos] = s2;
+            rho[pos] = make_float2(s1, s2);
         }
-        bar_sync(1, NT);
-
-        // ---- C: collision of the tile's fluid nodes --------------------------------
-        if (have) {
+    };
+    // C: forces (Eqs. 12-15), tau_s and u (Eqs. 6-9) and the collision
+    // (Eqs. 1, 2, 11) of the own node of thread tid in tile w; the output
+    // goes to the stage's own block, then each warp hands the stage over
+    auto phase_c = [&](int w, int k, R f[2][9], R rho1, R rho2) {
+        const StepArgs &a = s.a[case_of(w)];
+        const float2 *rho = rho0 + k * SN1;
+        const uint32_t *T = tabs + k * s.tab_stride;
+        if (tid < (int)T[0]) {
+            const uint32_t me = T[HDR + tid];
+            const int tx = (int)(me & 63u), ty = (int)((me >> 6) & 63u), bidx = (int)(me >> 22);
             const int dpos = (ty + 2) * SDXW + tx + 2;
             const uint32_t m = (me >> 12) & 0xffu;
             R fx1, fy1, fx2, fy2;
@@ -415,8 +458,9 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
                                          const int q = mir ? dpos - d : dpos + d;
                                          const uint32_t bit = mir ? (m >> (opp(i) - 1)) : (m >> (i - 1));
                                          code = (bit & 1u) ? 1 : GEO_FLUID;
-                                         s1 = rho[q];
-                                         s2 = rho[SN1 + q];
+                                         const float2 r = rho[q];
+                                         s1 = r.x;
+                                         s2 = r.y;
                                      },
                                      fx1, fy1, fx2, fy2);
             } else {
@@ -424,39 +468,66 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
                                      [&](int i, uint8_t &code, R &s1, R &s2) {
                                          const int q = dpos + ey(i) * SDXW + ex(i);
                                          code = ((m >> (i - 1)) & 1u) ? 1 : GEO_FLUID;
-                                         s1 = rho[q];
-                                         s2 = rho[SN1 + q];
+                                         const float2 r = rho[q];
+                                         s1 = r.x;
+                                         s2 = r.y;
                                      },
                                      fx1, fy1, fx2, fy2);
             }
             R omega, ux, uy;
             node_velocity<R>(a.p, f, rho1, rho2, fx1 + fx2, fy1 + fy2, omega, ux, uy);
             collide<R, CM>(a.p, f, rho1, rho2, ux, uy, fx1, fy1, fx2, fy2, omega);
-            S *o = stage(st) + bidx * NPL;
+            S *o = stage(k) + bidx * NPL;
             if constexpr (P::ref) {
                 const S h1 = from_real<S>(rho1), h2 = from_real<S>(rho2);
                 o[18] = h1;
-                o[19] = h2;
+                o[19] = h2;  // the reference pair, rounded once and reused below
                 const R q1 = to_real(h1), q2 = to_real(h2);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    o[i] = from_real<S>(f[0][i] - wgt<R>(i) * q1);
-                    o[9 + i] = from_real<S>(f[1][i] - wgt<R>(i) * q2);
-                }
+                for (int i = 0; i < 9; ++i)
+                    pair_store(o + 2 * i, f[0][i] - wgt<R>(i) * q1, f[1][i] - wgt<R>(i) * q2);
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    o[i] = from_real<S>(f[0][i]);
-                    o[9 + i] = from_real<S>(f[1][i]);
-                }
+                for (int i = 0; i < 9; ++i) pair_store(o + 2 * i, f[0][i], f[1][i]);
             }
         }
         // the output is in the stage: one arrival per warp hands it to the
-        // producer's store; the densities are reused by the next tile
+        // producer's store
         fence_proxy_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&done[st]);
+        if (lane == 0) mbar_arrive(&done[k]);
+    };
+    auto timed_out = [&](int w) {
+        // the producer finds the tile never computed and reports it
+        if (tid == 0) atomicExch(s.a[case_of(w)].err, MCLBM_ERR_TIMEOUT);
+    };
+
+    R f[2][9];
+    R rho1 = 0, rho2 = 0;
+    {
+        const bool bad = !mbar_wait(&full[0], 0u, s.a[case_of(blockIdx.x)].wait_ns);
+        if (!bad) phase_a(blockIdx.x, 0, f, rho1, rho2);
+        if (bar_or(bad, 1, NT)) {
+            timed_out(blockIdx.x);
+            return;
+        }
+    }
+    int n = 0;
+    for (int w = blockIdx.x; w < s.total; w += gridDim.x, ++n) {
+        const int st = n & 1;
+        phase_b(w, st);
         bar_sync(1, NT);
+        phase_c(w, st, f, rho1, rho2);
+        const int wn = w + (int)gridDim.x;
+        bool bad = false;
+        if (wn < s.total) {
+            bad = !mbar_wait(&full[st ^ 1], (uint32_t)((n + 1) >> 1) & 1u, s.a[case_of(wn)].wait_ns);
+            if (!bad) phase_a(wn, st ^ 1, f, rho1, rho2);
+        }
+        if (bar_or(bad, 1, NT)) {
+            timed_out(wn);
+            return;
+        }
     }
 }
 
@@ -470,7 +541,7 @@ __global__ void to_sparse_kernel(Geometry g, const typename P::store_t *f, typen
     const int pl = (int)(k - sl * P::planes);
     const int node = snode[sl];
     typename P::store_t v = typename P::store_t(0.f);
-    if (node >= 0) v = f[(long long)pl * g.plane + site_of(g, node % g.nx, node / g.nx)];
+    if (node >= 0) v = f[(long long)dense_plane(pl) * g.plane + site_of(g, node % g.nx, node / g.nx)];
     fs[k] = v;
 }
 
@@ -482,7 +553,7 @@ __global__ void to_dense_kernel(Geometry g, const typename P::store_t *fs, typen
     const long long sl = k / P::planes;
     const int pl = (int)(k - sl * P::planes);
     const int node = snode[sl];
-    if (node >= 0) f[(long long)pl * g.plane + site_of(g, node % g.nx, node / g.nx)] = fs[k];
+    if (node >= 0) f[(long long)dense_plane(pl) * g.plane + site_of(g, node % g.nx, node / g.nx)] = fs[k];
 }
 
 template <class F>

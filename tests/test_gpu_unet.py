@@ -16,11 +16,14 @@ only the weights and the input of the plain FP64 network already moves the
 first layer's weight gradient by ~8 % of its largest element, because ReLU
 masks flip on 2^-9 perturbations, so the masks must be decided on the same
 values on both sides.  Against the plain FP64 network each layer's gradient
-keeps its direction (cosine >= 0.99) and norm (10 %).  The input layer
-(enc0a), whose weight gradient multiplies the random network input with
-the gradient from the deepest point of the backward pass, is held to the
-direction and norm bars only: its element error against the storage-model
-reference measures 1.7-2.7 % of its largest element.
+keeps its direction (cosine >= 0.99) and norm (10 %).  Even against the
+storage-model reference a few isolated gradient elements move by single
+ReLU mask flips, where a pre-activation lies within FP32 rounding of zero
+(the order of the FP32 sums decides its sign); they weigh most on small
+images (8 x 512 pixels) and in the input layer.  Measured there: median
+element errors ~1e-5 of the layer max, 99th percentiles up to 1.7e-2,
+isolated elements up to 2.7e-2.  So the 2e-2 bar applies to every layer's
+99th percentile of element errors, and 5e-2 to its largest element.
 """
 import numpy as np
 import pytest
@@ -106,16 +109,15 @@ def test_gradient_matches_reference(levels, b, h, w, max_ctas, base):
             a, r, r0 = g[s].astype(np.float64), want_g[s], plain_g[s]
             if np.linalg.norm(r0) < 1e-12:
                 continue
-            elem = np.max(np.abs(a - r)) / np.max(np.abs(r))
-            if name == "enc0a":
-                print(f"enc0a {part}: element error {elem:.2e} of the layer max")
-            else:
-                worst = max(worst, elem)
-                assert elem < 2e-2, (name, part, elem)
+            err = np.abs(a - r) / np.max(np.abs(r))
+            elem, p99 = float(err.max()), float(np.percentile(err, 99))
+            worst = max(worst, p99)
+            assert p99 < 2e-2 and elem < 5e-2, (name, part, p99, elem)
             cos = a @ r0 / (np.linalg.norm(a) * np.linalg.norm(r0))
             assert cos > 0.99, (name, part, cos)
             assert abs(np.linalg.norm(a) / np.linalg.norm(r0) - 1) < 0.1, (name, part)
-    print(f"gradient L{levels} base {base} {b}x{h}x{w}: worst element error {worst:.2e} of the layer max")
+    print(f"gradient L{levels} base {base} {b}x{h}x{w}: worst 99th-percentile element error {worst:.2e} "
+          f"of the layer max")
     net.close()
 
 
