@@ -57,6 +57,13 @@ STEP_KERNELS = {
                      "ncu_bytes": None, "ncu_sha": None},
 }
 FLUID_ONLY_PRECISIONS = ("fp32", "fp16dev", "bf16dev")
+# The FP64 step (kernel 1) is bound by the FP64 pipe, not by HBM: FP64
+# floating-point operations per fluid-node update counted by ncu on the
+# workload below (DADD + DMUL + 2 DFMA thread instructions per launch over
+# the fluid nodes), and the GB300's FP64 FMA rate measured by a probe of
+# independent FMA chains (1.257 TFLOP/s; nominal 1.25).
+FP64_FLOPS_PER_FLUID_NODE = 367.0
+FP64_PEAK_GFLOPS = 1257.0
 
 
 def step_kernel(kernel: str, prec: str) -> str:
@@ -264,6 +271,9 @@ def run_gpu(args, rank, world):
     storages = None
     if args.prec == "fp32" and args.storage_steps > 0:
         storages = storage_section(args, stream, c, peak)
+    fp64 = None
+    if args.prec == "fp32" and args.fp64_steps > 0:
+        fp64 = fp64_section(args, stream, c)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,6 +308,7 @@ def run_gpu(args, rank, world):
         "cpu_baseline": cpu,
         "batched": batched,
         "storages": storages,
+        "fp64": fp64,
         "diag": {k: (None if isinstance(v, float) and math.isnan(v) else v)
                  for k, v in diag.items()},
     }
@@ -334,6 +345,33 @@ def storage_section(args, stream, c, peak) -> dict:
                      "steps": args.storage_steps}
         lat.close()
     return out
+
+
+def fp64_section(args, stream, c) -> dict:
+    """The same workload in FP64 storage and arithmetic (the parity path):
+    MLUPS and the fraction of the FP64 FMA rate its floating-point
+    operations reach (the FP64 pipe, not HBM, bounds this step)."""
+    import torch
+    from paper_2111_08666_gb300 import mclbm
+    lat = mclbm.Lattice(c["solid"], c["xi"], prec="fp64", nu1=c["nu1"], nu2=c["nu2"],
+                        rho_in1=c["rho_in1"], rho_out2=c["rho_out2"], stream=stream)
+    lat.init(c["rho1"], c["rho2"])
+    lat.step(3)
+    lat.sync()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    lat.step(args.fp64_steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    sec = start.elapsed_time(end) / 1e3 / args.fp64_steps
+    lat.close()
+    n_fluid = int((c["solid"] == 0).sum())
+    gflops = FP64_FLOPS_PER_FLUID_NODE * n_fluid / sec / 1e9
+    return {"mlups": round(c["nx"] * c["ny"] / sec / 1e6, 1), "launch_us": round(sec * 1e6, 1),
+            "roofline": {"bound": "alu", "achieved": round(gflops, 1), "peak": FP64_PEAK_GFLOPS,
+                         "unit": "GFLOP/s (FP64)", "frac": round(gflops / FP64_PEAK_GFLOPS, 4),
+                         "flops_per_fluid_node": FP64_FLOPS_PER_FLUID_NODE},
+            "steps": args.fp64_steps}
 
 
 def batched_section(args, stream, peak) -> dict:
@@ -477,6 +515,8 @@ def main():
                     help="steps of the 24-case batched section (0: skip it)")
     ap.add_argument("--storage-steps", type=int, default=2000,
                     help="steps of each 16-bit deviation storage's timing (0: skip it)")
+    ap.add_argument("--fp64-steps", type=int, default=100,
+                    help="steps of the FP64 step's timing (0: skip it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank, world, _ = replicas.rank_info()

@@ -97,6 +97,8 @@ def relax(step, saturation, window: int = 1000, tol: float = 1e-6, max_steps: in
         step(window)
         n += window
         cur = saturation()
+        if not np.isfinite(cur):
+            return n, cur, False
         if abs(cur - prev) < tol:
             return n, cur, True
         prev = cur
@@ -169,8 +171,8 @@ def train(net, x, t, m, epochs: int = 10, batch: int = 16, lr: float = 1e-3, see
 
 
 def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, window: int = 1000,
-                    tol: float = 1e-6, max_steps: int = 200000, flip: float = 0.0, stream=None,
-                    warm: bool = True):
+                    tol: float = 1e-6, max_steps: int = 200000, flip: float = 0.0, gate: int = 0,
+                    stream=None, warm: bool = True):
     """Quasi-static primary drainage of one lattice (Sec. 4.2.1), run as two
     independent P_c-S_w curves from the same relaxed start:
 
@@ -181,19 +183,37 @@ def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, win
           the nodes predicted to change phase are reset to the predicted
           phase, every other node keeps its populations), then relaxes.
 
-    The warm wall time of a level counts everything the warm start adds:
-    the phase read-out, the network input, the inference and the blend.
+    The blend is applied only where the network predicts a real invasion:
+    at least ``gate`` fluid nodes whose predicted phase lies on the other
+    side of zero (by more than ``flip``); a smaller predicted change leaves
+    the level to the cold continuation (resetting a few nodes to rest costs
+    more relaxation, by the pressure waves it sends, than it saves).  The
+    warm wall time of a level counts everything the warm start adds: the
+    phase read-out, the network input, the inference and the blend.
+
     A level ends when |S_w(t) - S_w(t - window)| < tol (S_w by mass) or
-    after max_steps.  ``warm=False`` runs the cold curve only.  Returns one
-    record per level."""
+    after max_steps; the library's divergence check runs every window, and
+    a curve that diverges stops there (its record says so).  ``warm=False``
+    runs the cold curve only.  Returns one record per level."""
     import time
 
     def make():
         lat = mclbm.Lattice(case["solid"], case["xi"], prec="fp32", nu1=case["nu1"],
                             nu2=case["nu2"], rho_in1=case["rho_in1"], rho_out2=case["rho_out2"],
                             stream=stream)
+        mclbm.mclbm_set_flag(lat.h, mclbm.MCLBM_FLAG_DIAG_EVERY, window)
         lat.init(case["rho1"], case["rho2"])
         return lat
+
+    def relax_checked(lat):
+        try:
+            n, s_end, ok = relax(lat.step, lambda: sw(lat), window, tol, max_steps)
+            lat.sync()  # reports the library's divergence check
+            return n, s_end, ok, not np.isfinite(s_end)
+        except mclbm.MclbmError as e:
+            if e.code != mclbm.MCLBM_ERR_DIVERGED:
+                raise
+            return None, float("nan"), False, True
 
     def sw(l):
         return l.diagnostics()["sw_mass"]
@@ -203,28 +223,39 @@ def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, win
         branches["warm"] = make()
     # the common start: both relax at the initial boundary densities (the
     # kernels are deterministic, so the two states are identical)
-    start = {}
-    for name, lat in branches.items():
-        start[name] = relax(lat.step, lambda: sw(lat), window, tol, max_steps)
+    for name, lat in list(branches.items()):
+        if relax_checked(lat)[3]:
+            raise RuntimeError("the lattice diverged at the initial boundary densities")
+    fluid = case["solid"] == 0
     out = []
     for lev in range(1, levels + 1):
         rho_in = case["rho_in1"] + lev * d_rho
         rec = dict(level=lev, rho_in1=rho_in)
-        for name, lat in branches.items():
+        for name, lat in list(branches.items()):
             sw0 = sw(lat)
             t0 = time.perf_counter()
             lat.set_pressure_bc(rho_in, case["rho_out2"])
             if name == "warm":
-                x = network_input(case["solid"], case["xi"], lat.phase(), d_rho * DP_SCALE)[None]
+                phase = lat.phase()
+                x = network_input(case["solid"], case["xi"], phase, d_rho * DP_SCALE)[None]
                 phi = net.infer(x)[0]
-                rec["nodes_changed"] = mclbm.mclbm_blend_phase(lat.h, phi, flip)
+                p = np.clip(phi, -1.0, 1.0)
+                predicted = int((fluid & ((p > 0) != (phase > 0)) & (np.abs(p) > flip)).sum())
+                rec["nodes_predicted"] = predicted
+                rec["nodes_changed"] = mclbm.mclbm_blend_phase(lat.h, phi, flip) if predicted >= gate else 0
                 rec["sec_predict"] = time.perf_counter() - t0
-            n, s_end, ok = relax(lat.step, lambda: sw(lat), window, tol, max_steps)
-            d = lat.diagnostics()
+            n, s_end, ok, diverged = relax_checked(lat)
             rec.update({f"steps_{name}": n, f"sw_{name}": s_end, f"converged_{name}": ok,
-                        f"sec_{name}": time.perf_counter() - t0, f"pc_{name}": d["pc"],
+                        f"diverged_{name}": diverged, f"sec_{name}": time.perf_counter() - t0,
                         f"sw_before_{name}": sw0})
+            if diverged:
+                lat.close()
+                del branches[name]
+            else:
+                rec[f"pc_{name}"] = lat.diagnostics()["pc"]
         out.append(rec)
+        if not branches:
+            break
     for lat in branches.values():
         lat.close()
     return out
@@ -250,6 +281,8 @@ def main(argv=None) -> None:
     ap.add_argument("--d-rho", type=float, default=0.005)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--flip", type=float, default=0.0)
+    ap.add_argument("--gate", type=int, default=1000,
+                    help="predicted flipped nodes below which a level is left to the cold continuation")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
@@ -265,17 +298,20 @@ def main(argv=None) -> None:
     net.close()
     case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
     rec = drainage_curves(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
-                          max_steps=a.max_steps, flip=a.flip)
+                          max_steps=a.max_steps, flip=a.flip, gate=a.gate)
+    both = [r for r in rec if r.get("steps_cold") and r.get("steps_warm")]
     summary = dict(train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
                    loss=hist,
                    pair_steps_mean=float(st.mean()),
-                   steps_cold=int(sum(r["steps_cold"] for r in rec)),
-                   steps_warm=int(sum(r["steps_warm"] for r in rec)),
-                   sec_cold=float(sum(r["sec_cold"] for r in rec)),
-                   sec_warm=float(sum(r["sec_warm"] for r in rec)),
-                   levels_unconverged_cold=int(sum(not r["converged_cold"] for r in rec)),
-                   levels_unconverged_warm=int(sum(not r["converged_warm"] for r in rec)),
-                   max_abs_dsw=float(max(abs(r["sw_cold"] - r["sw_warm"]) for r in rec)),
+                   levels_compared=len(both),
+                   steps_cold=int(sum(r["steps_cold"] for r in both)),
+                   steps_warm=int(sum(r["steps_warm"] for r in both)),
+                   sec_cold=float(sum(r["sec_cold"] for r in both)),
+                   sec_warm=float(sum(r["sec_warm"] for r in both)),
+                   levels_unconverged_cold=int(sum(not r["converged_cold"] for r in both)),
+                   levels_unconverged_warm=int(sum(not r["converged_warm"] for r in both)),
+                   diverged=[(r["level"], k) for r in rec for k in ("cold", "warm") if r.get(f"diverged_{k}")],
+                   max_abs_dsw=float(max(abs(r["sw_cold"] - r["sw_warm"]) for r in both)) if both else None,
                    levels=rec)
     print(json.dumps(summary))
     big.close()
