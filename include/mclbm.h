@@ -428,10 +428,8 @@ int mclbm_init_from_phase(mclbm_lattice *lat, const float *phi);
  * predicted equilibrium): at every fluid node whose predicted phase field
  * phi_hat is on the other side of zero from the node's own phase (component
  * 1's side is rho1 > rho2) and |phi_hat| > flip, the populations are reset
- * to rest with the densities of the phase the node joins: the mean (rho1,
- * rho2) of its fluid neighbours already in that phase, or, where it has
- * none, the separated-phase densities of phi_hat as in
- * mclbm_init_from_phase.  Every other node keeps its populations, and the
+ * to rest with the separated-phase densities of phi_hat, as in
+ * mclbm_init_from_phase; every other node keeps its populations, and the
  * inlet/outlet records of Eqs. 26-27 are kept.
  *   phi_hat  [ny][nx] float, host or device, owned by the caller
  *   flip     in [0, 1)

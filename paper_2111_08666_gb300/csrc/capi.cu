@@ -573,9 +573,7 @@ int mclbm_blend_phase(mclbm_lattice *lat, const float *phi_hat, double flip, int
         e = cudaMemcpyAsync(&cnt, lat->blend_count, sizeof(cnt), cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "warm-start blend");
-    lat->cur = 1 - lat->cur;        // the blended state is in the other buffer
-    lat->pop_ghosts_stale = true;   // its ghost images are rebuilt before use
-    lat->sparse_state = 0;          // the dense buffers hold the state
+    lat->sparse_state = 0;  // the dense buffers hold the state
     if (changed) *changed = (int64_t)cnt;
     return MCLBM_OK;
 }

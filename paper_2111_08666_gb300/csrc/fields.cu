@@ -430,66 +430,37 @@ cudaError_t dispatch(const Lattice &L, F &&fn) {
     }
 }
 
-// Warm-start blend: at a fluid node whose predicted phase field phi_hat
-// lies on the other side of zero from the node's own phase (rho1 > rho2 is
-// component 1's side) and by more than `flip`, the node is re-initialised
-// at rest, f_i = w_i rho^sigma (Eq. 2 at u = 0), with the densities of the
-// phase it joins: the mean (rho1, rho2) of its fluid neighbours already in
-// that phase (the local, pressure-compressed equilibrium values), or, with
-// no such neighbour, the separated-phase densities of phi_hat:
-// rho1 = lo + (hi - lo)(1 + phi)/2, rho2 = lo + (hi - lo)(1 - phi)/2, phi
-// clamped to [-1, 1].  Every other fluid node keeps its stored values.  The
-// kernel reads the state in fcur and writes fnext, so that the neighbours
-// it reads are never the values it writes; the number of replaced nodes is
-// added to *changed (one atomic per warp).  Ghost images are not written
-// (the caller marks them stale).
+// Warm-start blend in place: at a fluid node whose predicted phase field
+// phi_hat lies on the other side of zero from the node's own phase
+// (rho1 > rho2 is component 1's side) and by more than `flip`, the node is
+// re-initialised at rest, f_i = w_i rho^sigma (Eq. 2 at u = 0), with the
+// separated-phase densities of phi_hat: rho1 = lo + (hi - lo)(1 + phi)/2,
+// rho2 = lo + (hi - lo)(1 - phi)/2, phi clamped to [-1, 1].  Every other
+// node keeps its populations, so the previous equilibrium survives
+// wherever no change of phase is predicted.  The number of replaced nodes
+// is added to *changed (one atomic per warp).
 template <class P>
-__global__ void blend_phase_kernel(Geometry g, Params p, const typename P::store_t *fcur,
-                                   typename P::store_t *fnext, const float *phi, double hi, double lo,
-                                   double flip, unsigned long long *changed) {
+__global__ void blend_phase_kernel(Geometry g, Params p, typename P::store_t *f, const float *phi,
+                                   double hi, double lo, double flip, unsigned long long *changed) {
     using R = typename P::real_t;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool change = false;
     if (k < (long long)g.nx * g.ny) {
         const int x = (int)(k % g.nx), y = (int)(k / g.nx);
         if (is_fluid(g, x, y)) {
-            const long long site = site_of(g, x, y);
             R r1, r2;
-            node_rho<P>(g, fcur, site, r1, r2);
+            node_rho<P>(g, f, site_of(g, x, y), r1, r2);
             const double ph = fmin(1.0, fmax(-1.0, (double)phi[k]));
-            const bool oil = ph > 0.0;
-            change = (oil != (r1 > r2)) && fabs(ph) > flip;
+            change = ((ph > 0.0) != (r1 > r2)) && fabs(ph) > flip;
             if (change) {
-                R m1 = 0, m2 = 0;
-                int cnt = 0;
-                for (int i = 1; i < 9; ++i) {
-                    const int xn = x + ex(i), yn = y + ey(i);
-                    if (geo_at(g, p, xn, yn) != GEO_FLUID) continue;
-                    const int xw = pmod(xn, g.nx), yw = pmod(yn, g.ny);
-                    R n1, n2;
-                    node_rho<P>(g, fcur, site_of(g, xw, yw), n1, n2);
-                    if ((n1 > n2) != oil) continue;
-                    m1 += n1;
-                    m2 += n2;
-                    ++cnt;
-                }
-                R n1, n2;
-                if (cnt > 0) {
-                    n1 = m1 / R(cnt);
-                    n2 = m2 / R(cnt);
-                } else {
-                    n1 = R(lo + (hi - lo) * (1.0 + ph) * 0.5);
-                    n2 = R(lo + (hi - lo) * (1.0 - ph) * 0.5);
-                }
+                const R n1 = R(lo + (hi - lo) * (1.0 + ph) * 0.5), n2 = R(lo + (hi - lo) * (1.0 - ph) * 0.5);
                 R fs[2][9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     fs[0][i] = wgt<R>(i) * n1;
                     fs[1][i] = wgt<R>(i) * n2;
                 }
-                pop_store_site<P>(fnext, g.plane, site, fs, n1, n2);
-            } else {
-                for (int pl = 0; pl < P::planes; ++pl) fnext[pl * g.plane + site] = fcur[pl * g.plane + site];
+                pop_store_node<P>(g, p, f, x, y, fs, n1, n2);
             }
         }
     }
@@ -530,8 +501,7 @@ cudaError_t launch_blend_phase(Lattice &L, const float *phi, double hi, double l
     return dispatch(L, [&](auto tag) {
         using P = decltype(tag);
         blend_phase_kernel<P><<<blocks_for((long long)L.nx * L.ny), BLK, 0, L.stream>>>(
-            g, L.p, static_cast<const typename P::store_t *>(L.f[L.cur]),
-            static_cast<typename P::store_t *>(L.f[1 - L.cur]), phi, hi, lo, flip, changed);
+            g, L.p, static_cast<typename P::store_t *>(L.f[L.cur]), phi, hi, lo, flip, changed);
         count_launch();
         return cudaGetLastError();
     });

@@ -281,8 +281,9 @@ def main(argv=None) -> None:
     ap.add_argument("--d-rho", type=float, default=0.005)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--flip", type=float, default=0.0)
-    ap.add_argument("--gate", type=int, default=1000,
-                    help="predicted flipped nodes below which a level is left to the cold continuation")
+    ap.add_argument("--gates", type=str, default="1000",
+                    help="comma list of gates: predicted flipped nodes below which a level is left to "
+                         "the cold continuation (one evaluation per gate, the same trained network)")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
@@ -297,23 +298,25 @@ def main(argv=None) -> None:
     big.set_params(net.params())
     net.close()
     case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
-    rec = drainage_curves(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
-                          max_steps=a.max_steps, flip=a.flip, gate=a.gate)
-    both = [r for r in rec if r.get("steps_cold") and r.get("steps_warm")]
-    summary = dict(train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
-                   loss=hist,
-                   pair_steps_mean=float(st.mean()),
-                   levels_compared=len(both),
-                   steps_cold=int(sum(r["steps_cold"] for r in both)),
-                   steps_warm=int(sum(r["steps_warm"] for r in both)),
-                   sec_cold=float(sum(r["sec_cold"] for r in both)),
-                   sec_warm=float(sum(r["sec_warm"] for r in both)),
-                   levels_unconverged_cold=int(sum(not r["converged_cold"] for r in both)),
-                   levels_unconverged_warm=int(sum(not r["converged_warm"] for r in both)),
-                   diverged=[(r["level"], k) for r in rec for k in ("cold", "warm") if r.get(f"diverged_{k}")],
-                   max_abs_dsw=float(max(abs(r["sw_cold"] - r["sw_warm"]) for r in both)) if both else None,
-                   levels=rec)
-    print(json.dumps(summary))
+    for gate in [int(g) for g in a.gates.split(",")]:
+        rec = drainage_curves(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
+                              max_steps=a.max_steps, flip=a.flip, gate=gate)
+        both = [r for r in rec if r.get("steps_cold") and r.get("steps_warm")]
+        summary = dict(gate=gate, train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
+                       loss=hist,
+                       pair_steps_mean=float(st.mean()),
+                       levels_compared=len(both),
+                       steps_cold=int(sum(r["steps_cold"] for r in both)),
+                       steps_warm=int(sum(r["steps_warm"] for r in both)),
+                       sec_cold=float(sum(r["sec_cold"] for r in both)),
+                       sec_warm=float(sum(r["sec_warm"] for r in both)),
+                       levels_unconverged_cold=int(sum(not r["converged_cold"] for r in both)),
+                       levels_unconverged_warm=int(sum(not r["converged_warm"] for r in both)),
+                       diverged=[(r["level"], k) for r in rec for k in ("cold", "warm")
+                                 if r.get(f"diverged_{k}")],
+                       max_abs_dsw=float(max(abs(r["sw_cold"] - r["sw_warm"]) for r in both)) if both else None,
+                       levels=rec)
+        print(json.dumps(summary), flush=True)
     big.close()
 
 

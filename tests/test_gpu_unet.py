@@ -201,10 +201,8 @@ def test_init_from_phase_sets_the_densities():
 def test_blend_phase_resets_only_predicted_flips(prec):
     """mclbm_blend_phase: fluid nodes whose predicted phase field is on the
     other side of zero (and beyond the flip margin) are reset to rest with
-    the mean densities of their fluid neighbours already in the phase they
-    join (the nominal phase densities of the prediction where there is
-    none); every other node keeps its populations exactly; the count of
-    reset nodes is returned."""
+    the predicted phase densities; every other node keeps its populations
+    exactly; the count of reset nodes is returned."""
     nx, ny = 40, 20
     solid = np.zeros((ny, nx), np.uint8)
     solid[0] = solid[-1] = 1
@@ -213,43 +211,31 @@ def test_blend_phase_resets_only_predicted_flips(prec):
     fluid = solid == 0
     rho1 = np.where(rng.random((ny, nx)) < 0.5, 1.0, 0.027) * fluid
     rho2 = np.where(rho1 > 0.5, 0.027, 1.0) * fluid
-    rho1[14:17, 27:32] = np.where(fluid[14:17, 27:32], 0.027, 0)    # a water pocket ...
-    rho2[14:17, 27:32] = np.where(fluid[14:17, 27:32], 1.0, 0)
     lat = mclbm.Lattice(solid, None, prec=prec, nu1=0.1, nu2=0.1)
     lat.init(rho1, rho2)
     lat.step(7)
     f0 = lat.populations()
     r = f0.sum(axis=1)
     phi_hat = np.where(r[0] > r[1], 0.9, -0.9).astype(np.float32)     # no change predicted ...
-    flips = [(3, 4), (5, 30), (17, 2), (9, 20), (15, 29)]              # ... except here (the last
-    for y, x in flips:                                                  # one inside the pocket)
-        phi_hat[y, x] = -phi_hat[y, x] * 1.5                           # (clamped)
+    flips = [(3, 4), (5, 30), (17, 2), (9, 20)]
+    for y, x in flips:
+        phi_hat[y, x] = -phi_hat[y, x] * 1.5                          # ... except here (clamped)
     phi_hat[6, 6] = -np.sign(phi_hat[6, 6]) * 0.05                    # within the flip margin
     phi_hat[10, 16] = -phi_hat[10, 16]                                 # a solid node: ignored
     n = mclbm.mclbm_blend_phase(lat.h, phi_hat, 0.1)
     assert n == len(flips)
     f1 = lat.populations()
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-    tol = {"fp64": 1e-14, "fp32": 2e-7, "fp16dev": 2e-3}[prec]
     changed = np.zeros((ny, nx), bool)
-    used_nominal = False
     for y, x in flips:
         changed[y, x] = True
-        oil = phi_hat[y, x] > 0
-        nb = [((y + dy) % ny, (x + dx) % nx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if dy or dx]
-        same = [q for q in nb if fluid[q] and (r[0][q] > r[1][q]) == oil]
-        if same:
-            want1 = np.mean([r[0][q] for q in same])
-            want2 = np.mean([r[1][q] for q in same])
-        else:
-            used_nominal = True
-            p = float(np.clip(phi_hat[y, x], -1, 1))
-            want1 = warmstart.RHO_LO + (warmstart.RHO_HI - warmstart.RHO_LO) * (1 + p) / 2
-            want2 = warmstart.RHO_LO + (warmstart.RHO_HI - warmstart.RHO_LO) * (1 - p) / 2
+        p = float(np.clip(phi_hat[y, x], -1, 1))
+        want1 = warmstart.RHO_LO + (warmstart.RHO_HI - warmstart.RHO_LO) * (1 + p) / 2
+        want2 = warmstart.RHO_LO + (warmstart.RHO_HI - warmstart.RHO_LO) * (1 - p) / 2
+        tol = {"fp64": 1e-15, "fp32": 1e-7, "fp16dev": 2e-3}[prec]
         assert np.allclose(f1[0, :, y, x], w * want1, rtol=tol, atol=tol)
         assert np.allclose(f1[1, :, y, x], w * want2, rtol=tol, atol=tol)
-    assert used_nominal                                   # the pocket node has no oil neighbour
     assert np.array_equal(f1[:, :, ~changed], f0[:, :, ~changed])
-    lat.step(3)                                           # and it steps on
+    lat.step(3)                                                        # and it steps on
     assert np.isfinite(lat.populations()).all()
     lat.close()
