@@ -94,7 +94,7 @@ void drop_graph(mclbm_batch &b) {
 // trial steps are ordinary steps of the simulation.  Returns steps used.
 int autotune(mclbm_batch &b, int64_t budget, int *rc) {
     *rc = MCLBM_OK;
-    const int reps = 2;
+    const int reps = 4;  // timed steps per candidate (2 picked unevenly from run to run)
     if (budget < (int64_t)NCAND * (reps + 1)) {
         b.cand = 0;
         return 0;

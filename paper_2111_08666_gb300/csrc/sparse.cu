@@ -201,12 +201,17 @@ __global__ void __launch_bounds__(STX *STY + 32, STY == 8 ? 3 : 2) sparse_kernel
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + s.bar_off);
     uint64_t *done = full + 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // the case of work item w; a thread's queries mostly move forward (its
+    // tiles are w = blockIdx.x + m * gridDim.x), so the search starts at the
+    // case of its previous query
+    int c_hint = 0;
     auto case_of = [&](int w) -> int {
         if constexpr (N == 1) {
             return 0;
         } else {
-            int c = 0;
+            int c = w >= s.first[c_hint] ? c_hint : 0;
             while (c + 1 < s.ncases && w >= s.first[c + 1]) ++c;
+            c_hint = c;
             return c;
         }
     };

@@ -3,7 +3,7 @@ quasi-static drainage protocol, Sec. 4.2.1): a network briefly trained on
 LBM equilibria of small media cuts the relaxation steps of a drainage curve
 on an unseen medium against the cold-started curve, reaching the same
 saturations (|dS_w| <= 0.005 per level); the same network untrained does
-not (more steps, or other saturations).  Everything runs through the C ABI:
+not (more steps, other saturations, or a curve that diverges).  Everything runs through the C ABI:
 training pairs from the batched LBM, training and inference on the
 tensor-core U-Net, the blend in the library."""
 import numpy as np
@@ -23,7 +23,10 @@ def _curves(params, case):
     rec = warmstart.drainage_curves(net, case, levels=LEVELS, d_rho=D_RHO, max_steps=100000,
                                     **RELAX)
     net.close()
+    assert len(rec) == LEVELS and not any(r.get("diverged_cold") for r in rec)
     cold = sum(r["steps_cold"] for r in rec)
+    if any(r.get("diverged_warm") for r in rec):   # a curve that diverges gains nothing
+        return cold, float("inf"), float("inf"), rec
     warm = sum(r["steps_warm"] for r in rec)
     dsw = max(abs(r["sw_cold"] - r["sw_warm"]) for r in rec)
     return cold, warm, dsw, rec
