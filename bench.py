@@ -81,7 +81,7 @@ def step_kernel(kernel: str, prec: str) -> str:
 def tile_label(kname: str, shape: int, prec: str) -> str:
     """Tile of the step kernel that runs."""
     if kname == "sparse_kernel":
-        return "32x12" if shape == 1 else "32x8"
+        return "16-row bands, width <= 32, <= 384 fluid" if shape == 1 else "12-row bands, width <= 32, <= 256 fluid"
     if kname == "tma_tile_kernel":
         return "32x8" if shape == 1 else ("32x12" if prec == "fp32dev" else "32x16")
     return "32x16"
@@ -435,7 +435,7 @@ def batched_section(args, stream, peak) -> dict:
             "mlups_one_at_a_time": round(nodes * k_steps / t_seq / 1e6, 1),
             "mlups_one_at_a_time_fluid_only": round(nodes * k_steps / t_fluid / 1e6, 1),
             "launches": int(launches),
-            "step": ["tile 32x16", "tile 32x8", "fluid-only 32x12", "fluid-only 32x8"][info["shape"]],
+            "step": ["tile 32x16", "tile 32x8", "fluid-only 12-row bands", "fluid-only 16-row bands"][info["shape"]],
             "grid": "persistent" if info["grid"] == 0 else "one CTA per tile",
             "tuner_ms_per_step": [round(x, 4) for x in tuning]}
 
@@ -511,7 +511,7 @@ def main():
     ap.add_argument("--kernel", choices=["auto", "tile", "strip", "tma", "fluid"], default="auto")
     ap.add_argument("--tile-shape", type=int, choices=[0, 1], default=0,
                     help="tile shape: TMA kernel 0 = 32x16 (32x12 fp32dev), 1 = 32x8; "
-                         "fluid-only kernel 0 = 32x8, 1 = 32x12")
+                         "fluid-only kernel 0 = 12-row bands, 1 = 16-row bands")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-steps", type=int, default=400,
                     help="steps of the 24-case batched section (0: skip it)")

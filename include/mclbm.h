@@ -84,8 +84,10 @@ typedef enum {
     MCLBM_FLAG_KERNEL = 3,
     /* Tile shape, same results either way.  Kernel 3: 0 (default) 32 x 16
      * nodes (32 x 12 for FP32_DEV), two CTAs per SM; 1: 32 x 8 nodes, three
-     * CTAs per SM.  Kernel 4: 0 (default) 32 x 8 nodes, three CTAs per SM
-     * where the staged tiles fit; 1: 32 x 12 nodes, two CTAs per SM. */
+     * CTAs per SM.  Kernel 4: bands of 12 rows (0, default; 256 compute
+     * threads, three CTAs per SM) or 16 rows (1; 384 threads, two CTAs per
+     * SM), cut into tiles of at most 32 columns and at most one fluid node
+     * per compute thread (narrower where the staged tile would not fit). */
     MCLBM_FLAG_TILE_SHAPE = 4,
     /* Limit, in microseconds (1..10^7, default 10^6), of every wait of the
      * staging kernels (2, 3 and 4) for their asynchronous copies.  A wait
@@ -327,8 +329,8 @@ int mclbm_batch_lattice(mclbm_batch *b, int k, mclbm_lattice **view);
 int mclbm_batch_step(mclbm_batch *b, int64_t nsteps);
 
 /* out[0] cases, out[1] total nodes, out[2] chosen step (0: tile kernel
- * 32 x 16 or 32 x 12, 1: tile kernel 32 x 8, 2: fluid-only kernel 32 x 12,
- * 3: fluid-only kernel 32 x 8; -1 not yet chosen), out[3] grid (0: one CTA
+ * 32 x 16 or 32 x 12, 1: tile kernel 32 x 8, 2: fluid-only kernel, 12-row
+ * bands, 3: fluid-only kernel, 16-row bands; -1 not yet chosen), out[3] grid (0: one CTA
  * per resident slot, persistent; -1: one CTA per tile), out[4] steps per
  * graph replay, out[5] steps taken, out[6] resident CTA slots of the tile
  * kernel (0 for the fluid-only kernel), out[7] 1 if a graph is captured. */
@@ -336,9 +338,31 @@ int mclbm_batch_info(mclbm_batch *b, int64_t out[8]);
 
 /* Milliseconds per step the tuner measured for its 6 candidates: the tile
  * kernel at shape 0 persistent, shape 0 one CTA per tile, shape 1
- * persistent, shape 1 one CTA per tile; the fluid-only kernel at 32 x 12
- * and 32 x 8 (persistent).  -1 for a candidate not available. */
+ * persistent, shape 1 one CTA per tile; the fluid-only kernel with bands of
+ * 12 and of 16 rows (persistent).  -1 for a candidate not available. */
 int mclbm_batch_tuning(mclbm_batch *b, double ms_per_step[6]);
+
+/* Host only, no GPU needed: build the fluid-only layout of kernel 4 (its
+ * tiles, slot blocks, work tables and copy records; Sec. 2.1 fixes what a
+ * tile reads: pulls with half-way bounce-back, the 8-neighbour stencils of
+ * Eqs. 12-15 and the weighted virtual densities of Eqs. 16-17) for a
+ * geometry and check every invariant the step kernel relies on against it.
+ * codes: (ny + 6) rows of nx + 6 bytes, row y + 3 and column x + 3 holding
+ * the code of node (x, y) for x in [-3, nx + 3), y in [-3, ny + 3): 0
+ * fluid, 255 outside the lattice, any other value a solid class (the ghost
+ * rows and columns as the boundary mode makes them: copies of the opposite
+ * edge where periodic).  Caller-owned, read only.  tile_shape as
+ * MCLBM_FLAG_TILE_SHAPE; open_x marks the x ends open (Sec. 2.3).
+ * out[0] tiles, out[1] fluid slots (padded), out[2] largest staged set
+ * (slots), out[3] table words per tile, out[4] build attempts (a tile whose
+ * padded copy ranges overflow the stage is narrowed and the layout
+ * rebuilt), out[5] largest own block (slots), out[6] shared memory per CTA
+ * (bytes), out[7] 0 if every check holds, 1 + the first failing tile, or
+ * -1 if the blocks do not hold every fluid node exactly once.  Returns
+ * MCLBM_ERR_ARG for a bad argument or a precision kernel 4 does not serve,
+ * MCLBM_ERR_STATE if no tiling fits the staging capacity. */
+int mclbm_fluid_layout_check(int nx, int ny, const uint8_t *codes, mclbm_precision prec, int tile_shape,
+                             int open_x, int64_t out[8]);
 
 /* Checkpoint: write the current state (populations as stored, the outlet
  * record of Eq. 26, the parameters and the step count) to a file, and read

@@ -21,7 +21,7 @@ struct mclbm_batch {
     std::vector<unsigned char> maps[2];  // tensor descriptors per tile shape
     // chosen step (-1: not tuned yet): 0-3 the dense tile kernel (tile shape
     // 0 or 1, persistent or one CTA per tile), 4-5 the fluid-only kernel
-    // (tile 32x12 or 32x8, persistent)
+    // (bands of 12 or 16 rows, persistent)
     int cand = -1;
     double tune_ms[NCAND] = {0, 0, 0, 0, 0, 0};
     cudaGraphExec_t graph = nullptr;
@@ -49,7 +49,7 @@ int grid_of_cand(int cand) { return !fluid_cand(cand) && cand % 2 ? 1 << 30 : 0;
 int ensure_layout(mclbm_batch &b, int cand) {
     for (auto *L : b.cases) {
         if (fluid_cand(cand)) {
-            if (int rc = sparse_prepare(*L, shape_of_cand(cand) == 1 ? 8 : 12)) return rc;
+            if (int rc = sparse_prepare(*L, shape_of_cand(cand) == 1 ? 16 : 12)) return rc;
             if (L->nfp <= 0) return fail(MCLBM_ERR_STATE, "fluid-only layout unavailable for a case");
             if (int rc = dense_to_sparse(*L)) return rc;
         } else {

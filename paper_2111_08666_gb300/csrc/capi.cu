@@ -349,9 +349,10 @@ int mclbm_destroy(mclbm_lattice *lat) {
     return MCLBM_OK;
 }
 
-// Tile height of the fluid-only kernel: 32 x 8 by default (three CTAs per
-// SM: their warps fill each other's barrier waits), 32 x 12 for shape 1.
-static int sparse_height(const Lattice &L) { return L.tile_shape == 1 ? 12 : 8; }
+// Band height of the fluid-only kernel: 12 rows by default (256 compute
+// threads, three CTAs per SM: their warps fill each other's barrier waits),
+// 16 rows for shape 1 (384 compute threads, two CTAs per SM).
+static int sparse_height(const Lattice &L) { return L.tile_shape == 1 ? 16 : 12; }
 
 int mclbm_set_flag(mclbm_lattice *lat, int flag, int64_t value) {
     if (int rc = check_lat(lat)) return rc;
@@ -871,6 +872,18 @@ int mclbm_info(mclbm_lattice *lat, int64_t out[6]) {
     out[4] = lat->steps;
     out[5] = (int64_t)lat->device_bytes;
     return MCLBM_OK;
+}
+
+int mclbm_fluid_layout_check(int nx, int ny, const uint8_t *codes, mclbm_precision prec, int tile_shape,
+                             int open_x, int64_t out[8]) {
+    if (nx < 1 || ny < 1 || (int64_t)nx * ny > (1LL << 30)) return fail(MCLBM_ERR_ARG, "lattice size out of range");
+    if (!codes || !out) return fail(MCLBM_ERR_ARG, "codes or out is NULL");
+    if (tile_shape != 0 && tile_shape != 1) return fail(MCLBM_ERR_ARG, "tile_shape must be 0 or 1");
+    try {
+        return sparse_layout_check(nx, ny, codes, prec, tile_shape, open_x != 0, out);
+    } catch (const std::bad_alloc &) {
+        return fail(MCLBM_ERR_NOMEM, "host memory for the layout check");
+    }
 }
 
 }  // extern "C"

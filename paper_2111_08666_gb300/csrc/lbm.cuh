@@ -225,7 +225,9 @@ struct Lattice {
     uint32_t *stab = nullptr;          // per-tile tables of kernel 4
     int stab_words = 0;                // words per tile table (stride and copy size)
     int socap = 0, sscap = 0;          // largest own block and staged set of any tile
-    int sparse_ty = 0;                 // tile height of the layout
+    int sparse_ty = 0;                 // band height of the layout (12 or 16)
+    int stiles = 0;                    // tiles of the layout
+    int sparse_fail_key = -1;          // (boundary mode, band height) that could not be tiled
     uint32_t *scopy = nullptr;         // per-tile copy records of kernel 4
     int *snode = nullptr;              // [nfp]: lattice node y * nx + x of each slot, -1 padding
     uint64_t version = 0;      // bumped whenever a parameter changes
@@ -254,7 +256,11 @@ int tma_prepare(Lattice &L);      // builds the TMA descriptors; MCLBM_OK or err
 int tma_build_tables(Lattice &L); // work tables for the current boundary mode (synchronises)
 // fluid-only step (sparse.cu)
 bool sparse_precision(mclbm_precision p);
-int sparse_prepare(Lattice &L, int tile_height);  // layout and tables (tile 32 x 12 or 32 x 8)
+int sparse_prepare(Lattice &L, int band_height);  // layout and tables (bands of 12 or 16 rows)
+// host only: build and check the layout of a geometry given as codes over
+// [-3, nx + 3) x [-3, ny + 3) (capi: mclbm_fluid_layout_check)
+int sparse_layout_check(int nx, int ny, const uint8_t *codes, mclbm_precision prec, int tile_shape, bool open_x,
+                        int64_t out[8]);
 cudaError_t launch_step_sparse(Lattice &L);
 // one launch over several lattices (fluid-only state current, same tile height)
 cudaError_t launch_step_sparse_batch(Lattice *const *cases, int n, int grid, cudaStream_t stream);

@@ -107,6 +107,7 @@ _SIGS = {
                                         C.c_double, _P(C.c_double)]),
     "mclbm_init_from_phase": (C.c_int, [_vp, _vp]),
     "mclbm_blend_phase": (C.c_int, [_vp, _vp, C.c_double, _P(_i64)]),
+    "mclbm_fluid_layout_check": (C.c_int, [C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp]),
     "mclbm_save": (C.c_int, [_vp, C.c_char_p]),
     "mclbm_load": (C.c_int, [_vp, C.c_char_p]),
     "mclbm_launch_count": (_i64, []),
@@ -384,6 +385,20 @@ def mclbm_batch_tuning(b) -> list[float]:
     out = np.zeros(6)
     _check(load().mclbm_batch_tuning(b, out.ctypes.data))
     return out.tolist()
+
+
+def mclbm_fluid_layout_check(codes, prec: str = "fp32", tile_shape: int = 0, open_x: bool = False) -> dict:
+    """Build and check the fluid-only layout on the host (no GPU) for
+    geometry codes of shape (ny + 6, nx + 6) (see include/mclbm.h)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    if codes.ndim != 2 or codes.shape[0] < 7 or codes.shape[1] < 7:
+        raise ValueError("codes must be a (ny + 6, nx + 6) array")
+    ny, nx = codes.shape[0] - 6, codes.shape[1] - 6
+    out = np.zeros(8, dtype=np.int64)
+    _check(load().mclbm_fluid_layout_check(nx, ny, codes.ctypes.data, PRECISIONS[prec], int(tile_shape),
+                                           int(open_x), out.ctypes.data))
+    keys = ("tiles", "slots", "max_stage", "table_words", "attempts", "max_own", "smem_bytes", "check")
+    return dict(zip(keys, out.tolist()))
 
 
 def mclbm_launch_count() -> int:

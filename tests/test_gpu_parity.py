@@ -516,6 +516,40 @@ def test_fluid_only_kernel_ragged_lattice(prec, periodic_y, open_x, tile_shape):
     assert np.max(np.abs(fa - fb)) <= AGREE[prec][1] * np.max(np.abs(fa))
 
 
+@pytest.mark.parametrize("tile_shape", [0, 1])
+@pytest.mark.parametrize("periodic_y,open_x", [(True, False), (False, True)])
+def test_fluid_only_kernel_speckle_medium_fp32(periodic_y, open_x, tile_shape):
+    """Isolated solid nodes scattered at random (30 %) leave fluid ring nodes
+    whose fluid neighbours are neither own nor ring nodes: the tile must
+    still stage the ring node's own populations, which its bounce-back and
+    Set-3 treatment read.  Kernel 4 against the oracle on a lattice off every
+    tile multiple."""
+    nx, ny = 97, 50
+    rng = np.random.default_rng(5)
+    solid = (rng.random((ny, nx)) < 0.3).astype(np.uint8)
+    if not periodic_y:
+        solid[0] = solid[-1] = 1
+    if open_x:
+        solid[:, :2] = 0
+        solid[:, -2:] = 0
+        if not periodic_y:
+            solid[0] = solid[-1] = 1
+    xi = media.uniform_xi(solid, -0.3)
+    kw = dict(nu1=nu_of_tau(1.7), nu2=nu_of_tau(0.62), periodic_y=periodic_y)
+    if open_x:
+        rho1, rho2 = media.drainage_densities(solid)
+        kw.update(rho_in1=1.01, rho_out2=1.0)
+    else:
+        rho1, rho2 = media.droplet_densities(nx, ny, 48, 25, 12, solid=solid)
+    o = oracle.Oracle(solid, xi, **kw)
+    o.init(rho1, rho2)
+    g = mclbm.Lattice(solid, xi, prec="fp32", kernel=4, tile_shape=tile_shape, **kw)
+    g.init(rho1, rho2)
+    o.step(200)
+    g.step(200)
+    assert rel_err(g.populations(), o.f) < 2e-5
+
+
 def test_fluid_only_readouts_and_kernel_switches():
     """Read-outs between fluid-only steps convert the layouts without loss,
     and switching kernels mid-run continues the same trajectory."""
