@@ -50,7 +50,7 @@ _COMMON = ["paper_2111_08666_gb300/csrc/async_copy.cuh",
            "paper_2111_08666_gb300/csrc/lbm.cuh"]
 STEP_KERNELS = {
     "sparse_kernel": {"sources": ["paper_2111_08666_gb300/csrc/sparse.cu"] + _COMMON,
-                      "ncu_bytes": 185097011, "ncu_sha": "33be6e76ef99ee45"},
+                      "ncu_bytes": 183913882, "ncu_sha": "b415d8461a5080da"},
     "tma_tile_kernel": {"sources": ["paper_2111_08666_gb300/csrc/tma_tile.cu"] + _COMMON,
                         "ncu_bytes": 268262144, "ncu_sha": "127f58da57dc516e"},
     "fused_step_kernel": {"sources": ["paper_2111_08666_gb300/csrc/step.cu"] + _COMMON,

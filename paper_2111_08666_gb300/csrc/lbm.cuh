@@ -98,7 +98,12 @@ struct Params {
     float nu1_f = 0, nu2_f = 0, g_coh_f = 0, g_ads_f = 0, gx_f = 0, gy_f = 0;
     float rho_in1_f = 0, rho_out2_f = 0, rho_in2_f = 0, rho_out1_f = 0;
     float s_e_f = 0, s_eps_f = 0, s_q_f = 0;
+    // G_ads / G_coh (0 where G_coh = 0), for the fluid-only step, which
+    // stores the virtual solid densities scaled by it so that its force
+    // stencil has one coupling for all 8 neighbours
+    float ads_over_coh_f = 0;
     void round_fp32() {
+        ads_over_coh_f = g_coh != 0 ? (float)(g_ads / g_coh) : 0.f;
         nu1_f = (float)nu1;
         nu2_f = (float)nu2;
         g_coh_f = (float)g_coh;

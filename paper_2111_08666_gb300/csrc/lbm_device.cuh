@@ -293,20 +293,27 @@ __device__ __forceinline__ void collide_pair(R f[2][9], R rho1, R rho2, R ux, R 
     const R gx1 = pref * fx1, gy1 = pref * fy1, gx2 = pref * fx2, gy2 = pref * fy2;
     const R ub = R(1) - R(1.5) * (ux * ux + uy * uy);
     const R v1 = R(3) * (ux * gx1 + uy * gy1), v2 = R(3) * (ux * gx2 + uy * gy2);
-    const R v1a = wgt<R>(1) * v1, v1d = wgt<R>(5) * v1, v2a = wgt<R>(1) * v2, v2d = wgt<R>(5) * v2;
     R r1 = 0, r2 = 0;
+    // the directions in opposite pairs (i, opp(i)): e_opp . u = -e_i . u, so
+    // E_i and E_opp share the even part w (ub + 4.5 (e.u)^2) and differ in
+    // the sign of 3 w e.u, and the sources in the sign of their e.F term
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
+    for (int k = 0; k < 4; ++k) {
+        const int i = k < 2 ? k + 1 : k + 3, j = opp(i);
         const R w = wgt<R>(i);
         const R eu = edot<R>(i, ux, uy);
-        const R e = w * (ub + eu * (R(3) + R(4.5) * eu));
-        const R a = w * (R(3) + R(9) * eu);
-        const R s1 = a * edot<R>(i, gx1, gy1) - (i >= 5 ? v1d : v1a);
-        const R s2 = a * edot<R>(i, gx2, gy2) - (i >= 5 ? v2d : v2a);
-        f[0][i] = keep * f[0][i] + (q1 * e + s1);
-        f[1][i] = keep * f[1][i] + (q2 * e + s2);
-        r1 += f[0][i];
-        r2 += f[1][i];
+        const R even = w * (ub + R(4.5) * eu * eu), odd = (R(3) * w) * eu;
+        const R ai = w * R(3) + (R(9) * w) * eu, aj = w * R(3) - (R(9) * w) * eu;
+        const R g1 = edot<R>(i, gx1, gy1), g2 = edot<R>(i, gx2, gy2);
+        const R wv1 = w * v1, wv2 = w * v2;
+        const R s1i = ai * g1 - wv1, s1j = -(aj * g1) - wv1;
+        const R s2i = ai * g2 - wv2, s2j = -(aj * g2) - wv2;
+        f[0][i] = keep * f[0][i] + (q1 * (even + odd) + s1i);
+        f[0][j] = keep * f[0][j] + (q1 * (even - odd) + s1j);
+        f[1][i] = keep * f[1][i] + (q2 * (even + odd) + s2i);
+        f[1][j] = keep * f[1][j] + (q2 * (even - odd) + s2j);
+        r1 += f[0][i] + f[0][j];
+        r2 += f[1][i] + f[1][j];
     }
     f[0][0] = rho1 - r1;
     f[1][0] = rho2 - r2;

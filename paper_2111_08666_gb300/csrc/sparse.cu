@@ -428,9 +428,13 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
             rho[(ty + 2) * SDXW + tx + 2] = make_float2(rho1, rho2);
         }
     };
-    // B: virtual solid densities (Eqs. 16-17) on the 1-ring (zero outside)
+    // B: virtual solid densities (Eqs. 16-17) on the 1-ring (zero outside),
+    // times G_ads / G_coh where G_coh != 0: the force stencil of phase C
+    // then weights every neighbour by G_coh w_i
     auto phase_b = [&](int w, int k) {
-        const Geometry &g = s.a[case_of(w)].g;
+        const StepArgs &a = s.a[case_of(w)];
+        const Geometry &g = a.g;
+        const R scale = a.p.g_coh_f != 0.f ? R(a.p.ads_over_coh_f) : R(1);
         float2 *rho = rho0 + k * SN1;
         const uint32_t *T = tabs + k * s.tab_stride;
         const int n_own = (int)T[0], n_ring = (int)T[1], n_sol = (int)T[2];
@@ -454,7 +458,7 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
             }
             R s1 = 0, s2 = 0;
             if (den > R(0) && code != GEO_OUTSIDE) {
-                const R inv = R(1) / den;
+                const R inv = scale / den;
                 s1 = chi_at<R>(g, 2 * code) * n1s * inv;
                 s2 = chi_at<R>(g, 2 * code + 1) * n2s * inv;
             }
@@ -474,7 +478,38 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
             const int dpos = (ty + 2) * SDXW + tx + 2;
             const uint32_t m = (me >> 12) & 0xffu;
             R fx1, fy1, fx2, fy2;
-            if (me & SET3) {
+            // Eqs. 12-15 with one coupling: F^s = -rho^s G_coh sum_i w_i
+            // psi'^sb(x + e_i) e_i + rho^s g, psi' the density of a fluid
+            // neighbour or the scaled virtual density of a solid one; the
+            // axis and diagonal differences of the 8 neighbours
+            auto uniform_force = [&](auto nb) {
+                float2 v[9];
+#pragma unroll
+                for (int i = 1; i < 9; ++i) v[i] = nb(i);
+                const R gca = R(a.p.g_coh_f) * wgt<R>(1), gcd = R(a.p.g_coh_f) * wgt<R>(5);
+                const R px = (v[5].x + v[8].x) - (v[6].x + v[7].x), py = (v[5].x + v[6].x) - (v[7].x + v[8].x);
+                const R qx = (v[5].y + v[8].y) - (v[6].y + v[7].y), qy = (v[5].y + v[6].y) - (v[7].y + v[8].y);
+                const R sx1 = gca * (v[1].y - v[3].y) + gcd * qx, sy1 = gca * (v[2].y - v[4].y) + gcd * qy;
+                const R sx2 = gca * (v[1].x - v[3].x) + gcd * px, sy2 = gca * (v[2].x - v[4].x) + gcd * py;
+                fx1 = rho1 * (R(a.p.gx_f) - sx1);
+                fy1 = rho1 * (R(a.p.gy_f) - sy1);
+                fx2 = rho2 * (R(a.p.gx_f) - sx2);
+                fy2 = rho2 * (R(a.p.gy_f) - sy2);
+            };
+            if (a.p.g_coh_f != 0.f) {
+                if (me & SET3) {
+                    // Sec. 2.1: a neighbour beyond an open end is replaced by
+                    // the one in the opposite direction
+                    const bool mir_in = me & IN_BIT, mir_out = me & OUT_BIT;
+                    uniform_force([&](int i) {
+                        const bool mir = (mir_in && ex(i) < 0) || (mir_out && ex(i) > 0);
+                        const int d = ey(i) * SDXW + ex(i);
+                        return rho[mir ? dpos - d : dpos + d];
+                    });
+                } else {
+                    uniform_force([&](int i) { return rho[dpos + ey(i) * SDXW + ex(i)]; });
+                }
+            } else if (me & SET3) {
                 // Sec. 2.1: a neighbour beyond an open end is replaced by the
                 // one in the opposite direction
                 const bool mir_in = me & IN_BIT, mir_out = me & OUT_BIT;

@@ -4,9 +4,10 @@ buffers, the tile loop), and of every case of the 24-lattice batch.
 
 Workload: the 1024x512 heterogeneous lognormal disk medium of seed 1
 (porosity 0.6, water-wet theta = 50 deg, viscosity ratio 10) under driven
-primary drainage, rho_in1 = 1.005 and rho_out2 = 1 (Set-3).  With 304
-resident CTAs the fluid-only kernel walks about 4.5 tiles of 32 x 12 per
-CTA, the dense tile kernel about 3.4 of 32 x 16.
+primary drainage, rho_in1 = 1.005 and rho_out2 = 1 (Set-3).  The fluid-only kernel cuts
+the lattice into 1460 tiles (12-row bands, at most 256 fluid nodes each)
+and walks about 3.2 of them per CTA with 456 resident CTAs, the dense tile
+kernel about 3.4 tiles of 32 x 16 per CTA.
 
 The oracle runs once per module: the densities and diagnostics after 200,
 1000, 2000, ..., 10000 steps.
