@@ -102,9 +102,15 @@ def summarize(run: Run) -> dict:
     # 0.05 (the critical oil saturation Sec. 4.2.1 reports is 0.053)
     thr = next((p["pc"] for p in dr if p["sw_count"] < 0.95), None)
     spont_end = [p for p in im if p["phase"] == "spontaneous"]
+    forced = [p for p in im if p["phase"] == "forced"]
+    # residual oil: at the highest water saturation forced imbibition reaches
+    # (a curve that loses water again at higher outlet pressure has passed its
+    # residual state); the last level's saturation is reported beside it
+    sw_best = max((p["sw_count"] for p in forced), default=im[-1]["sw_count"] if im else None)
     return dict(theta=run.theta, xi=run.xi, pc_threshold=thr, sw_irreducible=dr[-1]["sw_count"],
                 sw_at_pc0=spont_end[-1]["sw_count"] if spont_end else None,
-                so_residual=1.0 - im[-1]["sw_count"] if im else None,
+                so_residual=1.0 - sw_best if sw_best is not None else None,
+                sw_forced_last=forced[-1]["sw_count"] if forced else None,
                 levels=len(pts), unconverged=sum(not p["converged"] for p in pts),
                 steps=sum(p["steps"] for p in pts))
 
