@@ -287,6 +287,13 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
         __syncwarp();
     };
 
+    // A single-lattice launch follows the previous step programmatically:
+    // the next step's grid may start as soon as the hardware allows, its
+    // CTAs set up and fetch their first copy record (static) while this one
+    // drains, and wait for the previous grid before touching the populations
+    // (griddepcontrol.wait: that grid complete, its writes visible).
+    // Without that launch attribute both instructions are no-ops.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -320,6 +327,7 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
         bool ok = true;
         int issued = 0;
         fetch_record(tile(0));
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         for (int m = 0; m < ntiles && ok; ++m) {
             if (m >= 2) {
                 // stage m & 1 still holds tile m - 2: store it and wait until
@@ -566,6 +574,7 @@ __global__ void __launch_bounds__(threads_for(STY) + 32, ctas_for(STY)) sparse_k
 
     R f[2][9];
     R rho1 = 0, rho2 = 0;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     {
         const bool bad = !mbar_wait(&full[0], 0u, s.a[case_of(blockIdx.x)].wait_ns);
         if (!bad) phase_a(blockIdx.x, 0, f, rho1, rho2);
@@ -1357,10 +1366,28 @@ cudaError_t launch_sparse(Lattice *const *cases, int n, int grid, cudaStream_t s
     }
     if (slots_out) *slots_out = slots;
     const int g = grid > 0 ? std::min(grid, total) : std::min(slots, total);
-    // NT compute threads and the producer warp
-    sparse_kernel<P, STY, N, CM><<<g, Lay::NT + 32, bytes, stream>>>(s);
+    cudaError_t e;
+    if (N == 1) {
+        // one lattice: programmatic dependent launch (the kernel orders its
+        // accesses with griddepcontrol), so that this step's grid starts
+        // while the previous one drains
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)g);
+        cfg.blockDim = dim3(Lay::NT + 32);  // NT compute threads and the producer warp
+        cfg.dynamicSmemBytes = bytes;
+        cfg.stream = stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, sparse_kernel<P, STY, N, CM>, s);
+    } else {
+        // NT compute threads and the producer warp
+        sparse_kernel<P, STY, N, CM><<<g, Lay::NT + 32, bytes, stream>>>(s);
+        e = cudaGetLastError();
+    }
     count_launch();
-    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         for (int c = 0; c < n; ++c) {
             cases[c]->scur = 1 - cases[c]->scur;
