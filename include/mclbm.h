@@ -206,7 +206,11 @@ int mclbm_get_populations(mclbm_lattice *lat, double *f);
  * with half-way bounce-back, Set-3 boundaries, moments (Eqs. 3-5), virtual
  * solid densities (Eqs. 16-17), forces (Eqs. 12-15 with the boundary-column
  * mirror of Sec. 2.1), system relaxation time and velocity (Eqs. 6-9), and
- * the forced BGK collision (Eqs. 1, 2, 11).  Asynchronous.
+ * the forced BGK collision (Eqs. 1, 2, 11).  Asynchronous.  The fluid-only
+ * kernel (4) launches each step as a programmatic dependent of the work
+ * before it on the stream: its grid may start early, but it reads nothing
+ * that earlier work writes (and writes nothing) until that work has
+ * completed, so stream order holds for the caller's own kernels too.
  */
 int mclbm_step(mclbm_lattice *lat, int64_t nsteps);
 
