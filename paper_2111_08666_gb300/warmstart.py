@@ -172,7 +172,7 @@ def train(net, x, t, m, epochs: int = 10, batch: int = 16, lr: float = 1e-3, see
 
 def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, window: int = 1000,
                     tol: float = 1e-6, max_steps: int = 200000, flip: float = 0.0, gate: int = 0,
-                    stream=None, warm: bool = True):
+                    stream=None, warm: bool = True, mrt: bool = False):
     """Quasi-static primary drainage of one lattice (Sec. 4.2.1), run as two
     independent P_c-S_w curves from the same relaxed start:
 
@@ -194,7 +194,9 @@ def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, win
     A level ends when |S_w(t) - S_w(t - window)| < tol (S_w by mass) or
     after max_steps; the library's divergence check runs every window, and
     a curve that diverges stops there (its record says so).  ``warm=False``
-    runs the cold curve only.  Returns one record per level."""
+    runs the cold curve only; ``mrt`` steps both curves with the MRT
+    collision (energy rates tied to 1/tau_s, heat-flux rate 1.9) instead of
+    the SRT of Eq. 1.  Returns one record per level."""
     import time
 
     def make():
@@ -202,6 +204,8 @@ def drainage_curves(net, case: dict, levels: int = 20, d_rho: float = 0.005, win
                             nu2=case["nu2"], rho_in1=case["rho_in1"], rho_out2=case["rho_out2"],
                             stream=stream)
         mclbm.mclbm_set_flag(lat.h, mclbm.MCLBM_FLAG_DIAG_EVERY, window)
+        if mrt:
+            lat.set_mrt(True, 0.0, 0.0, 1.9)
         lat.init(case["rho1"], case["rho2"])
         return lat
 
@@ -284,6 +288,8 @@ def main(argv=None) -> None:
     ap.add_argument("--gates", type=str, default="1000",
                     help="comma list of gates: predicted flipped nodes below which a level is left to "
                          "the cold continuation (one evaluation per gate, the same trained network)")
+    ap.add_argument("--mrt", action="store_true",
+                    help="step both evaluation curves with the MRT collision (training pairs stay SRT)")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     x, t, m, st = drainage_pairs(range(1000, 1000 + a.train_media), levels=a.train_levels,
@@ -300,9 +306,9 @@ def main(argv=None) -> None:
     case = media.config_paper_scale(a.eval_nx, a.eval_ny, 99)
     for gate in [int(g) for g in a.gates.split(",")]:
         rec = drainage_curves(big, case, levels=a.eval_levels, d_rho=a.d_rho, tol=a.tol,
-                              max_steps=a.max_steps, flip=a.flip, gate=gate)
+                              max_steps=a.max_steps, flip=a.flip, gate=gate, mrt=a.mrt)
         both = [r for r in rec if r.get("steps_cold") and r.get("steps_warm")]
-        summary = dict(gate=gate, train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
+        summary = dict(gate=gate, mrt=a.mrt, train_pairs=int(x.shape[0]), data_sec=t_data, train_sec=t_train,
                        loss=hist,
                        pair_steps_mean=float(st.mean()),
                        levels_compared=len(both),
