@@ -371,8 +371,8 @@ int mclbm_fluid_layout_check(int nx, int ny, const uint8_t *codes, mclbm_precisi
 /* Checkpoint: write the current state (populations as stored, the outlet
  * record of Eq. 26, the parameters and the step count) to a file, and read
  * it back into a lattice of the same size and precision; the restored run
- * continues bit for bit.  The file is raw device bytes of this build
- * (same machine byte order). */
+ * continues bit for bit.  The file holds raw device bytes in this library
+ * version's layout (same machine byte order). */
 int mclbm_save(mclbm_lattice *lat, const char *path);
 int mclbm_load(mclbm_lattice *lat, const char *path);
 
