@@ -124,3 +124,48 @@ def test_layout_check_rejects_bad_arguments():
         mclbm.mclbm_fluid_layout_check(codes, "fp32", 2)
     with pytest.raises(ValueError):
         mclbm.mclbm_fluid_layout_check(np.zeros((5, 5), np.uint8))
+
+
+def _random_geometry(rng):
+    """A ragged lattice with one of three solid patterns: speckle (isolated
+    solids), blobs (clustered solids) or stripes with gaps, at a random
+    porosity, with or without walls."""
+    ny, nx = int(rng.integers(5, 70)), int(rng.integers(5, 140))
+    kind = rng.integers(3)
+    phi = rng.uniform(0.2, 0.95)
+    if kind == 0:
+        solid = (rng.random((ny, nx)) > phi).astype(np.uint8)
+    elif kind == 1:
+        solid = np.zeros((ny, nx), np.uint8)
+        yy, xx = np.mgrid[0:ny, 0:nx]
+        for _ in range(int(rng.integers(1, 12))):
+            cy, cx, r = rng.uniform(0, ny), rng.uniform(0, nx), rng.uniform(1, 8)
+            solid[(yy - cy) ** 2 + (xx - cx) ** 2 < r * r] = 1
+    else:
+        solid = np.zeros((ny, nx), np.uint8)
+        for x in range(int(rng.integers(0, 4)), nx, int(rng.integers(3, 9))):
+            solid[:, x] = 1
+            solid[rng.integers(0, ny):, x] = 0
+    walls = bool(rng.integers(2)) and ny > 4
+    if walls:
+        solid[:2] = 1
+        solid[-2:] = 1
+    return solid, dict(periodic_y=not walls, open_x=bool(rng.integers(2)))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_layout_of_random_geometries(seed):
+    """Seeded random geometries (sizes, patterns, porosities, boundary
+    modes, both band heights and both storage widths): every invariant of
+    the self-check holds and every fluid node sits in one block."""
+    rng = np.random.default_rng(1000 + seed)
+    solid, kw = _random_geometry(rng)
+    shape = int(rng.integers(2))
+    prec = ("fp32", "fp16dev")[int(rng.integers(2))]
+    codes = codes_of(solid, periodic_x=not kw["open_x"], periodic_y=kw["periodic_y"])
+    r = mclbm.mclbm_fluid_layout_check(codes, prec, shape, kw["open_x"])
+    assert r["check"] == 0, (seed, solid.shape, kw, shape, prec, r)
+    fluid = int((solid == 0).sum())
+    assert r["slots"] >= fluid
+    assert r["max_own"] <= NT[shape] + 9
+    assert r["smem_bytes"] <= SMEM_BUDGET[shape]
